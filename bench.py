@@ -1,0 +1,387 @@
+"""Benchmark: tiled Hogbom CLEAN with feedback on one GB300.
+
+One step = one whole deconvolution of the 4096 x 4096 workload (8192^2 PSF,
+500 synthetic point sources, 4 x 4 tiles, feedback every K = 50 minor
+iterations per tile, gain 0.1, 50000 iterations, threshold 0 so the work is
+fixed) through the C ABI: set-up, every round's minor loops and feedback,
+the round closes.  Inputs are resident in HBM when the timed region starts.
+
+Prints one JSON line: minor iterations per second (whole job), plus
+  roofline      the dominant kernel's algorithmic bytes / CUDA-event time,
+                against the measured HBM copy bandwidth
+  cpu_baseline  the CPU oracle on the host cores, on the first round of the
+                same workload (a bounded sample)
+  e2e           the same metric through clean_deconvolve_host with host
+                buffers (host<->device copies inside the timed region)
+  clocks        SM clocks and throttle reasons sampled during the timed region
+
+--impl reference times the CPU oracle instead (one round of the same
+workload per step) and prints the same kind of line with "impl": "reference".
+Multi-GPU (torchrun): every rank deconvolves its own image (replicas, weak
+scaling); there is no data-path collective.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "CLEAN minor iterations/s (4096^2, 4x4 tiles, feedback every K)"
+UNIT = "iters/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="tiled-4096")
+    ap.add_argument("--K", type=int, default=50, help="feedback interval")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--untiled-iters", type=int, default=2000,
+                    help="iterations of the untiled whole-GPU comparison run (0: skip)")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) taken while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def build_inputs(args):
+    w = synth.workload(args.workload, feedback_interval=args.K)
+    data = w.build(threshold=0.0)
+    return w, data
+
+
+def minor_bytes_per_run(w) -> int:
+    """Algorithmic bytes of all minor iterations of one run: each iteration of
+    tile t reads its M_t residual pixels and the M_t-pixel PSF window and
+    writes M_t residual pixels (12 M_t bytes)."""
+    ty, tx = w.tiles
+    T = ty * tx
+    M = [((i + 1) * w.n // ty - i * w.n // ty) * ((j + 1) * w.n // tx - j * w.n // tx)
+         for i in range(ty) for j in range(tx)]
+    per_tile = [w.niter // T + (1 if t < w.niter % T else 0) for t in range(T)]
+    return int(sum(12 * m * k for m, k in zip(M, per_tile)))
+
+
+def feedback_updates_per_run(w) -> int:
+    """Pixel-component updates of all feedbacks of one run (threshold 0, every
+    tile spends its budget): each component updates every pixel outside its
+    own tile once."""
+    ty, tx = w.tiles
+    T = ty * tx
+    N2 = w.n * w.n
+    M = [((i + 1) * w.n // ty - i * w.n // ty) * ((j + 1) * w.n // tx - j * w.n // tx)
+         for i in range(ty) for j in range(tx)]
+    per_tile = [w.niter // T + (1 if t < w.niter % T else 0) for t in range(T)]
+    return int(sum((N2 - m) * k for m, k in zip(M, per_tile))) if w.feedback_interval > 0 else 0
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def cpu_baseline(w, data):
+    """The oracle as it stands, single-threaded, on the first round of the
+    workload (every tile's first K iterations and that round's feedback)."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    r = oracle.clean_f32(data["dirty"], data["psf"], w.gain, w.niter, 0.0, w.tiles,
+                         w.feedback_interval, max_rounds=1)
+    dt = time.perf_counter() - t0
+    return {"value": r.n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first round of {w.name}: {r.n} minor iterations + their feedback, "
+                      f"{dt:.1f} s single-threaded C (float32, -O2)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    w, data = build_inputs(args)
+    import oracle
+    oracle.build()
+    times, n = [], 0
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        r = oracle.clean_f32(data["dirty"], data["psf"], w.gain, w.niter, 0.0, w.tiles,
+                             w.feedback_interval, max_rounds=1)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+            n += r.n
+    total = sum(times)
+    value = n / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config_dict(w),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"each step: first round of {w.name} "
+                                       f"({n // args.steps} minor iterations + feedback)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_dict(w):
+    return {"workload": w.name, "image": f"{w.n}x{w.n}", "psf": f"{w.psf_n}x{w.psf_n}",
+            "tiles": f"{w.tiles[0]}x{w.tiles[1]}", "feedback_interval": w.feedback_interval,
+            "niter": w.niter, "gain": w.gain, "threshold": 0.0, "sources": w.n_sources,
+            "l2": "inputs larger than L2 (PSF 256 MiB) and a 512 MiB write between steps"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+
+    import paper_2501_01461_gb300 as cg
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    cg.lib()
+
+    w, data = build_inputs(args)
+    psf, dirty = data["psf"], data["dirty"]
+    d_psf = torch.from_numpy(psf).cuda()
+    d_dirty = torch.from_numpy(dirty).cuda()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    plan = cg.Plan(d_psf, w.n, w.n, gain=w.gain, niter=w.niter, threshold=0.0,
+                   tiles=w.tiles, feedback_interval=w.feedback_interval)
+    for _ in range(args.warmup):
+        plan.run(d_dirty)
+    torch.cuda.synchronize()
+    plan.debug_set(cg.DEBUG_TIMING, 1)
+    launches0 = plan.stats()["kernel_launches"]
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))           # evicts L2 (outside the timed events)
+        ev[i][0].record(stream)
+        plan.run(d_dirty)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    st = plan.stats()
+    gpu_launches = st["kernel_launches"] - launches0
+    n_comp = plan.n_components()
+    total_ms = float(sum(step_ms))
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * n_comp * args.steps / (total_ms / 1e3)
+
+    # ---- roofline of the dominant kernel ----
+    peaks, peak_src = measured_peaks()
+    minor_avg = st["minor_ms"] / max(st["minor_launches"], 1)
+    fb_avg = st["feedback_ms"] / max(st["feedback_launches"], 1)
+    rounds_per_run = st["minor_launches"] / args.steps
+    minor_b = minor_bytes_per_run(w) / rounds_per_run           # per launch
+    fb_upd = feedback_updates_per_run(w) / rounds_per_run       # per launch
+    minor_gbs = minor_b / (minor_avg / 1e3) / 1e9
+    fb_gbs = (4.0 * fb_upd + 8.0 * w.n * w.n) / (fb_avg / 1e3) / 1e9
+    dominant = "minor" if st["minor_ms"] >= st["feedback_ms"] else "feedback"
+    if dominant == "minor":
+        roof = {"kernel": "minor_kernel", "bound": "hbm", "achieved": minor_gbs,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": minor_gbs / peaks["hbm_gbs"],
+                "traffic": None}
+    else:
+        roof = {"kernel": "feedback_kernel", "bound": "hbm", "achieved": fb_gbs,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": fb_gbs / peaks["hbm_gbs"],
+                "traffic": None}
+    roof["peak_source"] = f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"
+    kernels = {
+        "minor_kernel": {"ms_per_step": st["minor_ms"] / args.steps,
+                         "launches_per_step": rounds_per_run,
+                         "algorithmic_GBps": minor_gbs,
+                         "bytes_per_launch": minor_b},
+        "feedback_kernel": {"ms_per_step": st["feedback_ms"] / args.steps,
+                            "launches_per_step": st["feedback_launches"] / args.steps,
+                            "updates_per_s": fb_upd / (fb_avg / 1e3),
+                            "algorithmic_GBps": fb_gbs},
+    }
+
+    # ---- end to end through host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        h_dirty = torch.from_numpy(dirty).pin_memory()
+        h_psf = torch.from_numpy(psf).pin_memory()
+        h_res = torch.empty_like(h_dirty).pin_memory()
+        h_mod = torch.empty_like(h_dirty).pin_memory()
+        h_comp = torch.empty((w.niter, 4), dtype=torch.int32).pin_memory()
+        hp = cg.Plan(None, w.n, w.n, gain=w.gain, niter=w.niter, threshold=0.0,
+                     tiles=w.tiles, feedback_interval=w.feedback_interval, psf_shape=psf.shape)
+
+        def host_step():
+            import ctypes
+            n = ctypes.c_int64(0)
+            rc = cg.lib().clean_deconvolve_host(
+                hp.handle, ctypes.c_void_p(h_dirty.data_ptr()), ctypes.c_void_p(h_psf.data_ptr()),
+                ctypes.c_void_p(h_res.data_ptr()), ctypes.c_void_p(h_mod.data_ptr()),
+                ctypes.c_void_p(h_comp.data_ptr()), w.niter, ctypes.byref(n),
+                ctypes.c_void_p(stream.cuda_stream))
+            if rc:
+                raise cg.CleanError(rc, "clean_deconvolve_host")
+            return n.value
+        for _ in range(max(1, args.warmup)):
+            host_step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ne = 0
+        for _ in range(args.steps):
+            ne += host_step()
+        te = time.perf_counter() - t0
+        hp.close()
+        e2e = {"value": world * ne / te, "unit": UNIT,
+               "h2d_bytes_per_step": int(dirty.nbytes + psf.nbytes),
+               "d2h_bytes_per_step": int(2 * dirty.nbytes + 16 * w.niter)}
+
+    # ---- untiled whole-GPU Hogbom on the same image (rate on a prefix) ----
+    untiled = None
+    if args.untiled_iters > 0:
+        up = cg.Plan(d_psf, w.n, w.n, gain=w.gain, niter=args.untiled_iters, threshold=0.0,
+                     mode=cg.UNTILED_GRID)
+        up.run(d_dirty)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        up.run(d_dirty)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ums = a.elapsed_time(b)
+        untiled = {"iters": args.untiled_iters, "ms": ums,
+                   "iters_per_s": args.untiled_iters / (ums / 1e3),
+                   "px_iter_per_s": args.untiled_iters * w.n * w.n / (ums / 1e3)}
+        up.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(w, data)
+        cpu["cores"] = 1
+
+    if rank == 0:
+        ty, tx = w.tiles
+        px_iter = sum(((i + 1) * w.n // ty - i * w.n // ty) * ((j + 1) * w.n // tx - j * w.n // tx)
+                      for i in range(ty) for j in range(tx)) / (ty * tx)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (VLA-like Y array PSF, seeded point-source sky)",
+            "config": config_dict(w),
+            "px_iter_per_s": value * px_iter,
+            "feedback_px_comp_per_s": world * feedback_updates_per_run(w) * args.steps / (total_ms / 1e3),
+            "roofline": roof, "kernels": kernels,
+            "cpu_baseline": cpu, "e2e": e2e, "untiled_gpu": untiled,
+            "vs_untiled_gpu": (value / untiled["iters_per_s"]) if untiled else None,
+            "gpu_launches": int(gpu_launches),
+            "clocks": clocks, "wall_s_timed": wall,
+            "plan": {k: st[k] for k in ("group_ctas", "group_sync", "resident", "sm_count")},
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

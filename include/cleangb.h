@@ -1,0 +1,245 @@
+/*
+ * cleangb -- tiled Hogbom CLEAN with feedback on one GB300 GPU.
+ *
+ * C ABI of libcleangb.so.  Method: Wright, Adamek & Armour, "Distribution of
+ * the Hogbom CLEAN Algorithm Using Tiled Images with Feedback" (arXiv
+ * 2501.01461).
+ *
+ *   Section 3, first equation:  a minor iteration finds the peak pixel of the
+ *       residual and records a component (position, peak x gain).
+ *   Section 3, second equation: the residual loses gain x peak x PSF, the
+ *       PSF centred on the peak.
+ *   Section 2, Fig. 1: the image is split into tiles that are deconvolved in
+ *       parallel.
+ *   Section 3, Figs. 2-3: at regular intervals every tile's new components,
+ *       placed on a full-size image and convolved with the full PSF
+ *       ("cross-coupling"), are subtracted from the other tiles (feedback).
+ *
+ * Readings fixed by this library where the paper is silent:
+ *   - the peak is the largest |residual| (its signed value becomes the
+ *     component); among equal |residual| the lowest row-major index wins;
+ *   - PSF centre = (psf_ny / 2, psf_nx / 2); residual pixels whose PSF index
+ *     falls outside the PSF array are left unchanged;
+ *   - tile (i, j) of a Ty x Tx grid covers rows [floor(i ny / Ty),
+ *     floor((i + 1) ny / Ty)) and columns likewise; tile index t = i Tx + j;
+ *   - niter is the total budget: tile t may run floor(niter / T) iterations,
+ *     plus one for t < niter mod T (T = Ty Tx);
+ *   - a tile stops while |peak| <= threshold; it is checked again after each
+ *     feedback;
+ *   - the feedback interval K counts minor iterations per tile; a round is up
+ *     to K iterations in every tile, then one feedback; K = 0 means no
+ *     feedback (independent tiles, Fig. 1(b)); the last round executed always
+ *     ends with its feedback;
+ *   - feedback applies, to each pixel, the other tiles' components of the
+ *     round in list order (tile index, then iteration), each as a rounded
+ *     float32 multiply followed by a rounded float32 subtract;
+ *   - all arithmetic is float32 with separately rounded multiplies and
+ *     subtracts (no fused multiply-add), so results are bit-reproducible.
+ *
+ * Conventions
+ *   - Images are row-major float32.  Device pointers ("d_") are CUDA global
+ *     memory owned by the caller; host pointers ("h_") are ordinary (ideally
+ *     pinned) host memory.  No call keeps a caller pointer after it returns,
+ *     except the PSF borrowed by clean_plan (see there).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls are stream-ordered; they synchronise the stream only
+ *     where stated (to read a status word or a count back).
+ *   - Every call returns a clean_status.  After CLEAN_ERR_CUDA or
+ *     CLEAN_ERR_TIMEOUT a plan is poisoned: every later call on it returns
+ *     the same code.  No call aborts the process.
+ */
+#ifndef CLEANGB_H
+#define CLEANGB_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define CLEAN_API __attribute__((visibility("default")))
+#else
+#define CLEAN_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CLEAN_OK = 0,
+  CLEAN_ERR_INVALID_ARG = 1, /* bad parameter or pointer; PSF peak not at centre */
+  CLEAN_ERR_NONFINITE = 2,   /* NaN or Inf in the dirty image or the PSF */
+  CLEAN_ERR_OOM = 3,         /* device allocation failed */
+  CLEAN_ERR_CUDA = 4,        /* a CUDA call failed (plan poisoned) */
+  CLEAN_ERR_TIMEOUT = 5,     /* a bounded device wait expired (plan poisoned) */
+  CLEAN_ERR_UNSUPPORTED = 6  /* valid request this build cannot serve */
+} clean_status;
+
+/* feedback_mode */
+enum { CLEAN_FB_GATHER = 0, CLEAN_FB_FFT = 1, CLEAN_FB_AUTO = 2 };
+/* mode */
+enum { CLEAN_TILED = 0, CLEAN_UNTILED_GRID = 1 };
+/* group_sync */
+enum { CLEAN_SYNC_AUTO = 0, CLEAN_SYNC_CLUSTER = 1, CLEAN_SYNC_GRID = 2 };
+
+/* One CLEAN component: pixel (y, x), flux gain x peak (Jy), and the tile
+ * that found it.  16 bytes. */
+typedef struct {
+  int32_t y, x;
+  float flux;
+  int32_t tile;
+} clean_component;
+
+/* The problem as the paper states it (dirty image size, PSF, gain,
+ * iteration count, threshold, tile grid, feedback interval) plus execution
+ * choices.  Fill with clean_params_default() first. */
+typedef struct {
+  int32_t ny, nx;            /* dirty image rows, columns (>= 1, ny*nx < 2^31) */
+  int32_t psf_ny, psf_nx;    /* PSF rows, columns (>= 1); centre (psf_ny/2, psf_nx/2) */
+  float gain;                /* loop gain, 0 < gain <= 1 */
+  float threshold;           /* stop a tile while |peak| <= threshold (>= 0) */
+  int64_t niter;             /* total minor iterations over all tiles (>= 0) */
+  int32_t tiles_y, tiles_x;  /* tile grid, 1 .. min(64, ny) and 1 .. min(64, nx) */
+  int32_t feedback_interval; /* K >= 0 minor iterations per tile between feedbacks */
+  int32_t feedback_mode;     /* CLEAN_FB_GATHER (exact) | CLEAN_FB_FFT | CLEAN_FB_AUTO */
+  int32_t mode;              /* CLEAN_TILED | CLEAN_UNTILED_GRID (needs a 1 x 1 grid) */
+  int32_t group_ctas;        /* CTAs per tile in the minor loop; 0 = choose */
+  int32_t group_sync;        /* CLEAN_SYNC_*: cluster barrier or bounded grid barrier */
+  int32_t reserved[5];       /* must be 0 */
+} clean_params;
+
+typedef struct clean_plan_s* clean_plan_t;
+
+/* Counters of a plan's current run (host struct, filled by clean_stats). */
+typedef struct {
+  int64_t n_components;   /* components in the list */
+  int64_t rounds;         /* rounds that produced at least one component */
+  int64_t rounds_launched;/* rounds launched, including no-op rounds */
+  int32_t group_ctas;     /* CTAs per tile chosen for the minor loop */
+  int32_t group_sync;     /* CLEAN_SYNC_CLUSTER or CLEAN_SYNC_GRID */
+  int32_t resident;       /* 1 if each CTA keeps its residual rows in shared memory */
+  int32_t feedback_mode;  /* the feedback path in use */
+  int32_t sm_count;       /* SMs of the device */
+  int32_t reserved;
+  int64_t kernel_launches;   /* kernels this plan has launched in total */
+  int64_t minor_launches;    /* minor-loop launches timed (CLEAN_DEBUG_TIMING) */
+  int64_t feedback_launches; /* feedback launches timed (CLEAN_DEBUG_TIMING) */
+  double minor_ms;           /* summed CUDA-event time of the timed minor launches */
+  double feedback_ms;        /* summed CUDA-event time of the timed feedback launches */
+} clean_stats_t;
+
+/* Fills *p with defaults: gain 0.1, threshold 0, 1 x 1 tiles, K 0, gather
+ * feedback, tiled mode, automatic group choice.  Sizes and niter are 0 and
+ * must be set.  Returns CLEAN_ERR_INVALID_ARG for p == NULL. */
+CLEAN_API int clean_params_default(clean_params* p);
+
+/* Checks *p without touching the GPU.  CLEAN_OK or CLEAN_ERR_INVALID_ARG. */
+CLEAN_API int clean_params_check(const clean_params* p);
+
+/* Creates a plan: validates *p (before any CUDA call), then allocates the
+ * plan's device state on the current device: residual and model images
+ * (4 ny nx bytes each), the component list (16 niter bytes), per-round and
+ * per-tile scratch.  d_psf (psf_ny x psf_nx float32, device) is BORROWED:
+ * the caller keeps it alive and unchanged until clean_destroy or the next
+ * clean_set_psf.  d_psf == NULL makes the plan allocate its own PSF buffer,
+ * to be filled by clean_set_psf or clean_deconvolve_host.  A supplied PSF is
+ * checked on the device (finite, |P| <= P[centre] everywhere); this call
+ * synchronises `stream` for that check.
+ * Returns CLEAN_OK, CLEAN_ERR_INVALID_ARG, CLEAN_ERR_NONFINITE, CLEAN_ERR_OOM
+ * or CLEAN_ERR_CUDA; *out is NULL on failure. */
+CLEAN_API int clean_plan(clean_plan_t* out, const clean_params* p, const float* d_psf,
+               void* stream);
+
+/* Replaces the PSF.  on_host = 0: `psf` is a device pointer and is borrowed
+ * as in clean_plan (only for plans created with a device PSF).  on_host = 1:
+ * `psf` is host memory copied into the plan's own PSF buffer (only for plans
+ * created with d_psf == NULL).  Validates and synchronises like clean_plan. */
+CLEAN_API int clean_set_psf(clean_plan_t plan, const float* psf, int32_t on_host,
+                  void* stream);
+
+/* Runs CLEAN.  d_dirty != NULL starts a new run from that dirty image
+ * (device, ny x nx, read only; copied to the residual): the component list,
+ * model and budgets are reset.  d_dirty == NULL continues the current run
+ * (applying any pending feedback from clean_step first).  Executes up to
+ * max_rounds rounds (-1 = until no tile is active: every tile has spent its
+ * budget or has |peak| <= threshold), each round being up to K minor
+ * iterations per tile followed by one feedback.  Synchronises `stream`
+ * between batches of rounds to read the device status (a few bytes).
+ * Returns CLEAN_OK, CLEAN_ERR_NONFINITE (dirty image not finite; nothing is
+ * computed), CLEAN_ERR_INVALID_ARG, CLEAN_ERR_CUDA or CLEAN_ERR_TIMEOUT. */
+CLEAN_API int clean_run(clean_plan_t plan, const float* d_dirty, int32_t max_rounds,
+              void* stream);
+
+/* One round of minor loops WITHOUT its feedback (Section 3: the tiles are
+ * deconvolved separately between synchronising feedback steps).  The round's
+ * components stay pending until clean_feedback (or the next clean_run /
+ * clean_step, which apply them first).  Does not synchronise. */
+CLEAN_API int clean_step(clean_plan_t plan, void* stream);
+
+/* Applies the pending feedback (Section 3, Figs. 2-3): each component found
+ * since the last feedback is subtracted, convolved with the full PSF, from
+ * every tile but its own.  No-op if nothing is pending.  Does not
+ * synchronise. */
+CLEAN_API int clean_feedback(clean_plan_t plan, void* stream);
+
+/* Restored image = model convolved with an elliptical Gaussian clean beam
+ * (FWHM bmaj_px, bmin_px pixels; major axis at bpa_rad from +x toward +y;
+ * peak 1; offsets (dy, dx) with dy^2 + dx^2 <= r^2, r = floor(5 sigma_major))
+ * plus the residual, into d_out (device, ny x nx float32).  The paper
+ * compares "reconstructed" images (Section 4, Fig. 4) without defining them;
+ * this is the usual Hogbom restoration.  Does not synchronise. */
+CLEAN_API int clean_restore(clean_plan_t plan, float bmaj_px, float bmin_px,
+                  float bpa_rad, float* d_out, void* stream);
+
+/* Copies the current residual and model (device, ny x nx float32 each) and
+ * the component list (device, list order) out of the plan; any output may
+ * be NULL.  comps_cap bounds the components written.  n_comps (host, may be
+ * NULL) receives the list length; reading it synchronises `stream`. */
+CLEAN_API int clean_get(clean_plan_t plan, float* d_residual_out, float* d_model_out,
+              clean_component* d_comps_out, int64_t comps_cap,
+              int64_t* n_comps, void* stream);
+
+/* Host copy of the list offset at which each recorded round starts (the
+ * list is round-major, tile index, then iteration).  Writes up to cap
+ * offsets; *n_rounds receives the number of rounds.  Synchronises. */
+CLEAN_API int clean_get_rounds(clean_plan_t plan, int64_t* h_offsets, int64_t cap,
+                     int64_t* n_rounds, void* stream);
+
+/* One whole deconvolution with host buffers: copies h_dirty (and h_psf if
+ * not NULL; the plan must own its PSF then) to the device, runs to
+ * completion, copies residual, model and components back.  Outputs may be
+ * NULL.  Synchronises `stream` before returning. */
+CLEAN_API int clean_deconvolve_host(clean_plan_t plan, const float* h_dirty,
+                          const float* h_psf, float* h_residual,
+                          float* h_model, clean_component* h_comps,
+                          int64_t comps_cap, int64_t* n_comps, void* stream);
+
+/* Fills *out (host) with the plan's counters.  Synchronises. */
+CLEAN_API int clean_stats(clean_plan_t plan, clean_stats_t* out, void* stream);
+
+/* Frees everything the plan owns (not the borrowed PSF).  NULL is a no-op.
+ * Synchronises the device's work that uses the plan. */
+CLEAN_API void clean_destroy(clean_plan_t plan);
+
+/* Static string for a status code. */
+CLEAN_API const char* clean_strerror(int status);
+
+/* Test hooks.  clean_debug_set(plan, what, value):
+ *   CLEAN_DEBUG_SPIN_LIMIT_NS  bound (ns) of every grid-barrier wait
+ *                              (default 2e9); a wait that exceeds it sets
+ *                              CLEAN_ERR_TIMEOUT and the kernel returns
+ *   CLEAN_DEBUG_FORCE_TIMEOUT  1: the first grid-barrier wait waits for an
+ *                              arrival that never comes (it must expire)
+ *   CLEAN_DEBUG_TIMING         1: bracket every minor-loop and feedback launch
+ *                              with CUDA events on its stream and sum their
+ *                              durations into clean_stats (0: off, resets)
+ * clean_debug_alloc_limit(bytes): host-side cap on the bytes a plan may
+ * allocate (-1 = none); a plan over it fails with CLEAN_ERR_OOM before
+ * allocating. */
+enum { CLEAN_DEBUG_SPIN_LIMIT_NS = 1, CLEAN_DEBUG_FORCE_TIMEOUT = 2, CLEAN_DEBUG_TIMING = 3 };
+CLEAN_API int clean_debug_set(clean_plan_t plan, int32_t what, int64_t value);
+CLEAN_API void clean_debug_alloc_limit(int64_t bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CLEANGB_H */

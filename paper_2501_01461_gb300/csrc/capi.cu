@@ -1,0 +1,670 @@
+// C ABI of libcleangb.so (declared in include/cleangb.h): plan state,
+// argument checks, the round loop and the status conventions.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "cleangb_internal.cuh"
+
+using namespace cleangb;
+
+namespace {
+
+std::atomic<int64_t> g_alloc_limit{-1};
+
+constexpr int64_t kResidentMaxBytes = 200 * 1024;  // residual rows per CTA in smem
+constexpr int kMaxBeamRadius = 64;
+constexpr int64_t kDefaultSpinNs = 2000000000ll;
+
+}  // namespace
+
+struct clean_plan_s {
+  clean_params p{};
+  int device = 0;
+  int sm_count = 0;
+  PlanDev d{};
+  MinorCfg mc{};
+  float* psf_own = nullptr;
+  bool psf_set = false;
+  int psf_status = CLEAN_OK;
+  int poisoned = CLEAN_OK;
+  bool started = false;
+  bool pending = false;
+  int parity = 0;
+  int64_t rounds_launched = 0;
+  DevState* h_st = nullptr;
+  float* beam_buf = nullptr;
+  std::vector<void*> allocs;
+  // launch accounting and optional per-launch CUDA-event timing
+  int64_t kernel_launches = 0;
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;  // pairs: [2i] start, [2i+1] stop
+  std::vector<int> ev_kind;          // 0 minor, 1 feedback, per used pair
+  int64_t minor_launches = 0, feedback_launches = 0;
+  double minor_ms = 0.0, feedback_ms = 0.0;
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+int poison(clean_plan_s* pl, int code) {
+  if (pl->poisoned == CLEAN_OK) pl->poisoned = code;
+  return pl->poisoned;
+}
+
+int cuda_fail(clean_plan_s* pl, cudaError_t e) {
+  (void)e;
+  cudaGetLastError();
+  return poison(pl, CLEAN_ERR_CUDA);
+}
+
+bool finite_pos(float v) { return std::isfinite(v); }
+
+int max_extent(int n, int parts) {
+  int m = 0;
+  for (int i = 0; i < parts; ++i)
+    m = std::max(m, (int)(((int64_t)(i + 1) * n) / parts - ((int64_t)i * n) / parts));
+  return m;
+}
+
+// Event pair for one timed launch (created on first use, reused after).
+int timed_begin(clean_plan_s* pl, int kind, cudaStream_t s) {
+  if (!pl->timing) return -1;
+  const size_t i = pl->ev_kind.size();
+  while (pl->ev_pool.size() < 2 * (i + 1)) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      return -1;
+    }
+    pl->ev_pool.push_back(e);
+  }
+  pl->ev_kind.push_back(kind);
+  cudaEventRecord(pl->ev_pool[2 * i], s);
+  return (int)i;
+}
+
+void timed_end(clean_plan_s* pl, int i, cudaStream_t s) {
+  if (i >= 0) cudaEventRecord(pl->ev_pool[2 * i + 1], s);
+}
+
+// Folds the durations of completed timed launches into the totals (called
+// after a synchronisation).
+void timed_collect(clean_plan_s* pl) {
+  for (size_t i = 0; i < pl->ev_kind.size(); ++i) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, pl->ev_pool[2 * i], pl->ev_pool[2 * i + 1]) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    if (pl->ev_kind[i] == 0) {
+      pl->minor_ms += ms;
+      ++pl->minor_launches;
+    } else {
+      pl->feedback_ms += ms;
+      ++pl->feedback_launches;
+    }
+  }
+  pl->ev_kind.clear();
+}
+
+// Reads the device control block into the pinned mirror (synchronises).
+int read_state(clean_plan_s* pl, cudaStream_t s) {
+  cudaError_t e = cudaMemcpyAsync(pl->h_st, pl->d.st, sizeof(DevState),
+                                  cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(pl, e);
+  timed_collect(pl);
+  if (pl->h_st->status & ST_TIMEOUT) return poison(pl, CLEAN_ERR_TIMEOUT);
+  return CLEAN_OK;
+}
+
+int check_psf(clean_plan_s* pl, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(pl->d.st, 0, sizeof(DevState), s);
+  if (e == cudaSuccess) e = launch_validate_psf(pl->d, s);
+  ++pl->kernel_launches;
+  if (e != cudaSuccess) return cuda_fail(pl, e);
+  int rc = read_state(pl, s);
+  if (rc != CLEAN_OK) return rc;
+  const int bits = pl->h_st->status;
+  pl->psf_set = true;
+  pl->psf_status = (bits & ST_NONFINITE_PSF)   ? CLEAN_ERR_NONFINITE
+                   : (bits & ST_PSF_OFFCENTRE) ? CLEAN_ERR_INVALID_ARG
+                                               : CLEAN_OK;
+  pl->started = false;  // a run's state refers to the old PSF
+  return pl->psf_status;
+}
+
+int launch_round_feedback(clean_plan_s* pl, cudaStream_t s) {
+  const int apply = (pl->d.K > 0 && pl->d.T > 1) ? 1 : 0;
+  const int ev = timed_begin(pl, 1, s);
+  cudaError_t e = launch_feedback(pl->d, pl->parity, apply, s);
+  timed_end(pl, ev, s);
+  ++pl->kernel_launches;
+  if (e != cudaSuccess) return cuda_fail(pl, e);
+  pl->parity ^= 1;
+  pl->pending = false;
+  ++pl->rounds_launched;
+  return CLEAN_OK;
+}
+
+int launch_round_minor(clean_plan_s* pl, cudaStream_t s) {
+  const int ev = timed_begin(pl, 0, s);
+  cudaError_t e = launch_minor(pl->d, pl->mc, pl->parity, s);
+  timed_end(pl, ev, s);
+  ++pl->kernel_launches;
+  if (e != cudaSuccess) return cuda_fail(pl, e);
+  pl->pending = true;
+  return CLEAN_OK;
+}
+
+int start_run(clean_plan_s* pl, const float* d_dirty, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(pl->d.peak, 0, sizeof(uint64_t) * 2 * pl->d.T, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(pl->d.st, 0, sizeof(DevState), s);
+  if (e == cudaSuccess) e = launch_init(pl->d, d_dirty, pl->p.niter, s);
+  ++pl->kernel_launches;
+  if (e != cudaSuccess) return cuda_fail(pl, e);
+  pl->started = true;
+  pl->pending = false;
+  pl->parity = 0;
+  pl->rounds_launched = 0;
+  return CLEAN_OK;
+}
+
+int common_checks(clean_plan_s* pl) {
+  if (!pl) return CLEAN_ERR_INVALID_ARG;
+  if (pl->poisoned != CLEAN_OK) return pl->poisoned;
+  if (!pl->psf_set) return CLEAN_ERR_INVALID_ARG;
+  if (pl->psf_status != CLEAN_OK) return pl->psf_status;
+  return CLEAN_OK;
+}
+
+int run_rounds(clean_plan_s* pl, int32_t max_rounds, cudaStream_t s) {
+  int rc;
+  if (pl->pending && (rc = launch_round_feedback(pl, s)) != CLEAN_OK) return rc;
+  if ((rc = read_state(pl, s)) != CLEAN_OK) return rc;
+  if (pl->h_st->status & ST_NONFINITE_DIRTY) {
+    pl->started = false;
+    return CLEAN_ERR_NONFINITE;
+  }
+  int64_t done = 0;
+  while (max_rounds < 0 || done < max_rounds) {
+    if (!pl->h_st->active) break;
+    int64_t chunk = 1;
+    if (pl->d.K > 0) chunk = (pl->h_st->max_budget + pl->d.K - 1) / pl->d.K;
+    chunk = std::max<int64_t>(chunk, 1);
+    if (max_rounds >= 0) chunk = std::min<int64_t>(chunk, max_rounds - done);
+    for (int64_t i = 0; i < chunk; ++i) {
+      if ((rc = launch_round_minor(pl, s)) != CLEAN_OK) return rc;
+      if ((rc = launch_round_feedback(pl, s)) != CLEAN_OK) return rc;
+    }
+    done += chunk;
+    if ((rc = read_state(pl, s)) != CLEAN_OK) return rc;
+  }
+  return CLEAN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int clean_params_default(clean_params* p) {
+  if (!p) return CLEAN_ERR_INVALID_ARG;
+  std::memset(p, 0, sizeof(*p));
+  p->gain = 0.1f;
+  p->threshold = 0.f;
+  p->tiles_y = p->tiles_x = 1;
+  p->feedback_interval = 0;
+  p->feedback_mode = CLEAN_FB_GATHER;
+  p->mode = CLEAN_TILED;
+  p->group_ctas = 0;
+  p->group_sync = CLEAN_SYNC_AUTO;
+  return CLEAN_OK;
+}
+
+int clean_params_check(const clean_params* p) {
+  if (!p) return CLEAN_ERR_INVALID_ARG;
+  if (p->ny < 1 || p->nx < 1 || p->psf_ny < 1 || p->psf_nx < 1) return CLEAN_ERR_INVALID_ARG;
+  if ((int64_t)p->ny * p->nx >= 0x7fffffffll) return CLEAN_ERR_INVALID_ARG;
+  if ((int64_t)p->psf_ny * p->psf_nx >= 0x7fffffffll) return CLEAN_ERR_INVALID_ARG;
+  if (!finite_pos(p->gain) || !(p->gain > 0.f) || !(p->gain <= 1.f)) return CLEAN_ERR_INVALID_ARG;
+  if (!finite_pos(p->threshold) || !(p->threshold >= 0.f)) return CLEAN_ERR_INVALID_ARG;
+  if (p->niter < 0 || p->niter > (int64_t)1 << 40) return CLEAN_ERR_INVALID_ARG;
+  if (p->tiles_y < 1 || p->tiles_x < 1 || p->tiles_y > 64 || p->tiles_x > 64 ||
+      p->tiles_y > p->ny || p->tiles_x > p->nx)
+    return CLEAN_ERR_INVALID_ARG;
+  if (p->feedback_interval < 0) return CLEAN_ERR_INVALID_ARG;
+  if (p->feedback_mode != CLEAN_FB_GATHER && p->feedback_mode != CLEAN_FB_FFT &&
+      p->feedback_mode != CLEAN_FB_AUTO)
+    return CLEAN_ERR_INVALID_ARG;
+  if (p->mode != CLEAN_TILED && p->mode != CLEAN_UNTILED_GRID) return CLEAN_ERR_INVALID_ARG;
+  if (p->mode == CLEAN_UNTILED_GRID && (p->tiles_y != 1 || p->tiles_x != 1))
+    return CLEAN_ERR_INVALID_ARG;
+  if (p->group_ctas < 0 || p->group_ctas > 1024) return CLEAN_ERR_INVALID_ARG;
+  if (p->group_sync != CLEAN_SYNC_AUTO && p->group_sync != CLEAN_SYNC_CLUSTER &&
+      p->group_sync != CLEAN_SYNC_GRID)
+    return CLEAN_ERR_INVALID_ARG;
+  if (p->group_sync == CLEAN_SYNC_CLUSTER && p->group_ctas > 16) return CLEAN_ERR_INVALID_ARG;
+  for (int i = 0; i < 5; ++i)
+    if (p->reserved[i] != 0) return CLEAN_ERR_INVALID_ARG;
+  return CLEAN_OK;
+}
+
+void clean_debug_alloc_limit(int64_t bytes) { g_alloc_limit.store(bytes); }
+
+void clean_destroy(clean_plan_t pl) {
+  if (!pl) return;
+  {
+    DeviceGuard g(pl->device);
+    cudaDeviceSynchronize();
+    for (void* a : pl->allocs) cudaFree(a);
+    for (cudaEvent_t e : pl->ev_pool) cudaEventDestroy(e);
+    if (pl->h_st) cudaFreeHost(pl->h_st);
+    cudaGetLastError();
+  }
+  delete pl;
+}
+
+int clean_plan(clean_plan_t* out, const clean_params* p, const float* d_psf, void* stream) {
+  if (!out) return CLEAN_ERR_INVALID_ARG;
+  *out = nullptr;
+  int rc = clean_params_check(p);
+  if (rc != CLEAN_OK) return rc;
+  if (p->feedback_mode == CLEAN_FB_FFT) return CLEAN_ERR_UNSUPPORTED;
+
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return CLEAN_ERR_CUDA;
+  }
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      sms < 1) {
+    cudaGetLastError();
+    return CLEAN_ERR_CUDA;
+  }
+  clean_plan_s* pl = new (std::nothrow) clean_plan_s();
+  if (!pl) return CLEAN_ERR_OOM;
+  pl->p = *p;
+  pl->device = dev;
+  pl->sm_count = sms;
+  cudaStream_t s = as_stream(stream);
+
+  const int T = p->tiles_y * p->tiles_x;
+  const int maxH = max_extent(p->ny, p->tiles_y);
+  const int maxW = max_extent(p->nx, p->tiles_x);
+  const int threads = minor_threads();
+
+  // ---- minor-loop group: G CTAs per tile, cluster or grid barrier ----
+  MinorCfg& mc = pl->mc;
+  mc.threads = threads;
+  mc.spin_limit_ns = kDefaultSpinNs;
+  mc.force_timeout = 0;
+  int sync = p->group_sync;
+  int G = p->group_ctas;
+  if (p->mode == CLEAN_UNTILED_GRID) {
+    sync = CLEAN_SYNC_GRID;
+    if (G == 0) G = sms;
+  } else {
+    const int per = std::max(1, sms / T);
+    if (sync == CLEAN_SYNC_AUTO) sync = (per > 16) ? CLEAN_SYNC_GRID : CLEAN_SYNC_CLUSTER;
+    if (G == 0) {
+      if (sync == CLEAN_SYNC_GRID) {
+        G = per;
+      } else {
+        G = 1;
+        while (G * 2 <= std::min(per, 16)) G *= 2;
+      }
+    }
+  }
+  G = std::max(1, std::min(G, maxH));
+  auto slab_bytes = [&](int g) { return (int64_t)((maxH + g - 1) / g) * maxW * 4; };
+  mc.sync = sync;
+  mc.G = G;
+  mc.resident = slab_bytes(G) <= kResidentMaxBytes ? 1 : 0;
+  mc.smem = mc.resident ? (int)slab_bytes(G) : 0;
+  if (sync == CLEAN_SYNC_CLUSTER) {
+    while (minor_max_cluster_ctas(mc.G, mc.resident, mc.smem, threads) < 1) {
+      if (p->group_ctas != 0 || mc.G == 1) {
+        delete pl;
+        return mc.G == 1 ? CLEAN_ERR_CUDA : CLEAN_ERR_INVALID_ARG;
+      }
+      mc.G /= 2;
+      mc.resident = slab_bytes(mc.G) <= kResidentMaxBytes ? 1 : 0;
+      mc.smem = mc.resident ? (int)slab_bytes(mc.G) : 0;
+    }
+  }
+  if (minor_prepare(mc) != cudaSuccess) {
+    cudaGetLastError();
+    delete pl;
+    return CLEAN_ERR_CUDA;
+  }
+  if (sync == CLEAN_SYNC_GRID && (int64_t)T * mc.G > sms) {
+    // a grid-synchronised launch needs every CTA resident (one per SM)
+    delete pl;
+    return CLEAN_ERR_INVALID_ARG;
+  }
+
+  // ---- device state ----
+  const int64_t npix = (int64_t)p->ny * p->nx;
+  const int64_t per_tile_max = p->niter / T + (p->niter % T ? 1 : 0);
+  int64_t cap_round = p->feedback_interval > 0
+                          ? std::min<int64_t>(p->feedback_interval, per_tile_max)
+                          : per_tile_max;
+  cap_round = std::max<int64_t>(cap_round, 1);
+  if (cap_round * T > 0x7fffffffll) {
+    delete pl;
+    return CLEAN_ERR_INVALID_ARG;
+  }
+  const int64_t list_cap = std::max<int64_t>(p->niter, 1);
+  struct Req {
+    void** dst;
+    size_t bytes;
+  };
+  const int beam_n = (2 * kMaxBeamRadius + 1) * (2 * kMaxBeamRadius + 1);
+  std::vector<Req> req = {
+      {(void**)&pl->d.R, sizeof(float) * (size_t)npix},
+      {(void**)&pl->d.model, sizeof(float) * (size_t)npix},
+      {(void**)&pl->d.budget, sizeof(int64_t) * (size_t)T},
+      {(void**)&pl->d.peak, sizeof(uint64_t) * 2 * (size_t)T},
+      {(void**)&pl->d.rcount, sizeof(int32_t) * (size_t)T},
+      {(void**)&pl->d.rcomps, sizeof(clean_component) * (size_t)(cap_round * T)},
+      {(void**)&pl->d.list, sizeof(clean_component) * (size_t)list_cap},
+      {(void**)&pl->d.round_off, sizeof(int64_t) * (size_t)(list_cap + 1)},
+      {(void**)&pl->d.gkeys, sizeof(uint64_t) * 2 * (size_t)T * (size_t)mc.G},
+      {(void**)&pl->d.gbar, sizeof(uint32_t) * (size_t)T},
+      {(void**)&pl->d.st, sizeof(DevState)},
+      {(void**)&pl->beam_buf, sizeof(float) * (size_t)beam_n},
+  };
+  if (!d_psf) req.push_back({(void**)&pl->psf_own, sizeof(float) * (size_t)p->psf_ny * p->psf_nx});
+  size_t total = 0;
+  for (auto& r : req) total += r.bytes;
+  const int64_t lim = g_alloc_limit.load();
+  if (lim >= 0 && (int64_t)total > lim) {
+    delete pl;
+    return CLEAN_ERR_OOM;
+  }
+  for (auto& r : req) {
+    void* ptr = nullptr;
+    if (cudaMalloc(&ptr, r.bytes) != cudaSuccess) {
+      cudaGetLastError();
+      clean_destroy(pl);
+      return CLEAN_ERR_OOM;
+    }
+    pl->allocs.push_back(ptr);
+    *r.dst = ptr;
+  }
+  if (cudaMallocHost((void**)&pl->h_st, sizeof(DevState)) != cudaSuccess) {
+    cudaGetLastError();
+    clean_destroy(pl);
+    return CLEAN_ERR_OOM;
+  }
+  std::memset(pl->h_st, 0, sizeof(DevState));
+
+  PlanDev& d = pl->d;
+  d.P = d_psf ? d_psf : pl->psf_own;
+  d.ny = p->ny;
+  d.nx = p->nx;
+  d.pny = p->psf_ny;
+  d.pnx = p->psf_nx;
+  d.cy = p->psf_ny / 2;
+  d.cx = p->psf_nx / 2;
+  d.ty = p->tiles_y;
+  d.tx = p->tiles_x;
+  d.T = T;
+  d.gain = p->gain;
+  d.thr = p->threshold;
+  d.K = p->feedback_interval;
+  d.cap_round = (int32_t)cap_round;
+
+  if (cudaMemsetAsync(d.gbar, 0, sizeof(uint32_t) * T, s) != cudaSuccess ||
+      cudaMemsetAsync(d.st, 0, sizeof(DevState), s) != cudaSuccess) {
+    cudaGetLastError();
+    clean_destroy(pl);
+    return CLEAN_ERR_CUDA;
+  }
+  if (d_psf) {
+    rc = check_psf(pl, s);
+    if (rc != CLEAN_OK) {
+      clean_destroy(pl);
+      return rc;
+    }
+  }
+  *out = pl;
+  return CLEAN_OK;
+}
+
+int clean_set_psf(clean_plan_t pl, const float* psf, int32_t on_host, void* stream) {
+  if (!pl || !psf) return CLEAN_ERR_INVALID_ARG;
+  if (pl->poisoned != CLEAN_OK) return pl->poisoned;
+  DeviceGuard g(pl->device);
+  cudaStream_t s = as_stream(stream);
+  if (on_host) {
+    if (!pl->psf_own) return CLEAN_ERR_INVALID_ARG;
+    cudaError_t e = cudaMemcpyAsync(pl->psf_own, psf,
+                                    sizeof(float) * (size_t)pl->d.pny * pl->d.pnx,
+                                    cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(pl, e);
+  } else {
+    if (pl->psf_own) return CLEAN_ERR_INVALID_ARG;
+    pl->d.P = psf;
+  }
+  return check_psf(pl, s);
+}
+
+int clean_run(clean_plan_t pl, const float* d_dirty, int32_t max_rounds, void* stream) {
+  int rc = common_checks(pl);
+  if (rc != CLEAN_OK) return rc;
+  if (max_rounds < -1) return CLEAN_ERR_INVALID_ARG;
+  DeviceGuard g(pl->device);
+  cudaStream_t s = as_stream(stream);
+  if (d_dirty) {
+    if ((rc = start_run(pl, d_dirty, s)) != CLEAN_OK) return rc;
+  } else if (!pl->started) {
+    return CLEAN_ERR_INVALID_ARG;
+  }
+  return run_rounds(pl, max_rounds, s);
+}
+
+int clean_step(clean_plan_t pl, void* stream) {
+  int rc = common_checks(pl);
+  if (rc != CLEAN_OK) return rc;
+  if (!pl->started) return CLEAN_ERR_INVALID_ARG;
+  DeviceGuard g(pl->device);
+  cudaStream_t s = as_stream(stream);
+  if (pl->pending && (rc = launch_round_feedback(pl, s)) != CLEAN_OK) return rc;
+  return launch_round_minor(pl, s);
+}
+
+int clean_feedback(clean_plan_t pl, void* stream) {
+  int rc = common_checks(pl);
+  if (rc != CLEAN_OK) return rc;
+  if (!pl->started) return CLEAN_ERR_INVALID_ARG;
+  if (!pl->pending) return CLEAN_OK;
+  DeviceGuard g(pl->device);
+  return launch_round_feedback(pl, as_stream(stream));
+}
+
+int clean_restore(clean_plan_t pl, float bmaj, float bmin, float bpa, float* d_out,
+                  void* stream) {
+  int rc = common_checks(pl);
+  if (rc != CLEAN_OK) return rc;
+  if (!pl->started || !d_out) return CLEAN_ERR_INVALID_ARG;
+  if (!std::isfinite(bmaj) || !std::isfinite(bmin) || !std::isfinite(bpa) || !(bmin > 0.f) ||
+      !(bmaj >= bmin))
+    return CLEAN_ERR_INVALID_ARG;
+  const double smaj = (double)bmaj / (2.0 * std::sqrt(2.0 * std::log(2.0)));
+  const int r = (int)std::floor(5.0 * smaj);
+  if (r > kMaxBeamRadius) return CLEAN_ERR_UNSUPPORTED;
+  DeviceGuard g(pl->device);
+  cudaError_t e = launch_restore_with(pl->d, bmaj, bmin, bpa, pl->beam_buf, r, d_out,
+                                      as_stream(stream));
+  pl->kernel_launches += 2;
+  if (e != cudaSuccess) return cuda_fail(pl, e);
+  return CLEAN_OK;
+}
+
+int clean_get(clean_plan_t pl, float* d_residual_out, float* d_model_out,
+              clean_component* d_comps_out, int64_t comps_cap, int64_t* n_comps,
+              void* stream) {
+  if (!pl) return CLEAN_ERR_INVALID_ARG;
+  if (pl->poisoned != CLEAN_OK) return pl->poisoned;
+  if (!pl->started) return CLEAN_ERR_INVALID_ARG;
+  if (d_comps_out && comps_cap < 0) return CLEAN_ERR_INVALID_ARG;
+  DeviceGuard g(pl->device);
+  cudaStream_t s = as_stream(stream);
+  const size_t img = sizeof(float) * (size_t)pl->d.ny * pl->d.nx;
+  cudaError_t e = cudaSuccess;
+  if (d_residual_out) e = cudaMemcpyAsync(d_residual_out, pl->d.R, img, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && d_model_out)
+    e = cudaMemcpyAsync(d_model_out, pl->d.model, img, cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(pl, e);
+  if (d_comps_out || n_comps) {
+    int rc = read_state(pl, s);
+    if (rc != CLEAN_OK) return rc;
+    const int64_t n = pl->h_st->total;
+    if (n_comps) *n_comps = n;
+    if (d_comps_out) {
+      const int64_t m = std::min(n, comps_cap);
+      if (m > 0) {
+        e = cudaMemcpyAsync(d_comps_out, pl->d.list, sizeof(clean_component) * (size_t)m,
+                            cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(pl, e);
+      }
+    }
+  }
+  return CLEAN_OK;
+}
+
+int clean_get_rounds(clean_plan_t pl, int64_t* h_offsets, int64_t cap, int64_t* n_rounds,
+                     void* stream) {
+  if (!pl) return CLEAN_ERR_INVALID_ARG;
+  if (pl->poisoned != CLEAN_OK) return pl->poisoned;
+  if (!pl->started || (h_offsets && cap < 0)) return CLEAN_ERR_INVALID_ARG;
+  DeviceGuard g(pl->device);
+  cudaStream_t s = as_stream(stream);
+  int rc = read_state(pl, s);
+  if (rc != CLEAN_OK) return rc;
+  const int64_t n = pl->h_st->n_rounds;
+  if (n_rounds) *n_rounds = n;
+  if (h_offsets && cap > 0 && n > 0) {
+    const int64_t m = std::min(n, cap);
+    cudaError_t e = cudaMemcpyAsync(h_offsets, pl->d.round_off, sizeof(int64_t) * (size_t)m,
+                                    cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(pl, e);
+  }
+  return CLEAN_OK;
+}
+
+int clean_deconvolve_host(clean_plan_t pl, const float* h_dirty, const float* h_psf,
+                          float* h_residual, float* h_model, clean_component* h_comps,
+                          int64_t comps_cap, int64_t* n_comps, void* stream) {
+  if (!pl || !h_dirty) return CLEAN_ERR_INVALID_ARG;
+  if (pl->poisoned != CLEAN_OK) return pl->poisoned;
+  DeviceGuard g(pl->device);
+  cudaStream_t s = as_stream(stream);
+  int rc;
+  if (h_psf) {
+    if ((rc = clean_set_psf(pl, h_psf, 1, stream)) != CLEAN_OK) return rc;
+  }
+  if ((rc = common_checks(pl)) != CLEAN_OK) return rc;
+  const size_t img = sizeof(float) * (size_t)pl->d.ny * pl->d.nx;
+  // the dirty image lands in the residual buffer; set-up copies it in place
+  cudaError_t e = cudaMemcpyAsync(pl->d.R, h_dirty, img, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(pl, e);
+  if ((rc = start_run(pl, pl->d.R, s)) != CLEAN_OK) return rc;
+  if ((rc = run_rounds(pl, -1, s)) != CLEAN_OK) return rc;
+  if (h_residual) e = cudaMemcpyAsync(h_residual, pl->d.R, img, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && h_model)
+    e = cudaMemcpyAsync(h_model, pl->d.model, img, cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_fail(pl, e);
+  const int64_t n = pl->h_st->total;  // read by run_rounds' last status read
+  if (n_comps) *n_comps = n;
+  if (h_comps && comps_cap > 0 && n > 0) {
+    e = cudaMemcpyAsync(h_comps, pl->d.list,
+                        sizeof(clean_component) * (size_t)std::min(n, comps_cap),
+                        cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(pl, e);
+  }
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(pl, e);
+  return CLEAN_OK;
+}
+
+int clean_stats(clean_plan_t pl, clean_stats_t* out, void* stream) {
+  if (!pl || !out) return CLEAN_ERR_INVALID_ARG;
+  std::memset(out, 0, sizeof(*out));
+  out->group_ctas = pl->mc.G;
+  out->group_sync = pl->mc.sync;
+  out->resident = pl->mc.resident;
+  out->feedback_mode = CLEAN_FB_GATHER;
+  out->sm_count = pl->sm_count;
+  out->rounds_launched = pl->rounds_launched;
+  out->kernel_launches = pl->kernel_launches;
+  if (pl->poisoned != CLEAN_OK) return pl->poisoned;
+  if (!pl->started) return CLEAN_OK;
+  DeviceGuard g(pl->device);
+  int rc = read_state(pl, as_stream(stream));
+  if (rc != CLEAN_OK) return rc;
+  out->n_components = pl->h_st->total;
+  out->rounds = pl->h_st->n_rounds;
+  out->minor_launches = pl->minor_launches;
+  out->feedback_launches = pl->feedback_launches;
+  out->minor_ms = pl->minor_ms;
+  out->feedback_ms = pl->feedback_ms;
+  return CLEAN_OK;
+}
+
+int clean_debug_set(clean_plan_t pl, int32_t what, int64_t value) {
+  if (!pl) return CLEAN_ERR_INVALID_ARG;
+  switch (what) {
+    case CLEAN_DEBUG_SPIN_LIMIT_NS:
+      if (value < 1) return CLEAN_ERR_INVALID_ARG;
+      pl->mc.spin_limit_ns = value;
+      return CLEAN_OK;
+    case CLEAN_DEBUG_FORCE_TIMEOUT:
+      pl->mc.force_timeout = value ? 1 : 0;
+      return CLEAN_OK;
+    case CLEAN_DEBUG_TIMING:
+      pl->timing = value != 0;
+      pl->ev_kind.clear();
+      pl->minor_launches = pl->feedback_launches = 0;
+      pl->minor_ms = pl->feedback_ms = 0.0;
+      return CLEAN_OK;
+    default:
+      return CLEAN_ERR_INVALID_ARG;
+  }
+}
+
+const char* clean_strerror(int status) {
+  switch (status) {
+    case CLEAN_OK: return "ok";
+    case CLEAN_ERR_INVALID_ARG: return "invalid argument";
+    case CLEAN_ERR_NONFINITE: return "non-finite value in the dirty image or PSF";
+    case CLEAN_ERR_OOM: return "out of device memory";
+    case CLEAN_ERR_CUDA: return "CUDA error";
+    case CLEAN_ERR_TIMEOUT: return "bounded device wait expired";
+    case CLEAN_ERR_UNSUPPORTED: return "unsupported by this build";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,128 @@
+// Internal declarations shared by the kernels and the C-ABI host code of
+// libcleangb.so.  Nothing here is part of the public ABI (include/cleangb.h).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "cleangb.h"
+
+namespace cleangb {
+
+// ---------------------------------------------------------------------------
+// Peak keys.  The peak search of Section 3 (first equation) picks the pixel
+// of largest |R|, ties to the lowest row-major index.  A pixel is encoded as
+// a 64-bit key whose unsigned order is exactly that order:
+//   bits 63..32  bit pattern of |R| (monotone in |R| for non-negative floats)
+//   bits 31..1   0x7fffffff - index (larger for lower indices)
+//   bit  0       sign bit of R, so the signed value is recovered exactly
+// Key 0 means "no pixel".  Requires index < 2^31 - 1.
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ uint64_t make_key(float v, int32_t idx) {
+  uint32_t bits;
+#ifdef __CUDA_ARCH__
+  bits = __float_as_uint(v);
+#else
+  __builtin_memcpy(&bits, &v, 4);
+#endif
+  uint32_t hi = bits & 0x7fffffffu;
+  uint32_t lo = ((0x7fffffffu - (uint32_t)idx) << 1) | (bits >> 31);
+  return ((uint64_t)hi << 32) | lo;
+}
+__host__ __device__ __forceinline__ int32_t key_index(uint64_t k) {
+  return (int32_t)(0x7fffffffu - ((uint32_t)k >> 1));
+}
+__device__ __forceinline__ float key_value(uint64_t k) {
+  uint32_t hi = (uint32_t)(k >> 32);
+  return __uint_as_float(hi | ((uint32_t)(k & 1u) << 31));
+}
+__device__ __forceinline__ float key_abs(uint64_t k) {
+  return __uint_as_float((uint32_t)(k >> 32));
+}
+
+// Tile bounds: tile (i, j) covers rows [floor(i ny / Ty), floor((i+1) ny / Ty))
+// and columns likewise (Section 2, Fig. 1; the split of a non-divisible size
+// is this library's reading).
+struct Rect {
+  int32_t y0, y1, x0, x1;
+};
+__host__ __device__ __forceinline__ Rect tile_rect(int32_t t, int32_t ny,
+                                                   int32_t nx, int32_t ty,
+                                                   int32_t tx) {
+  int32_t i = t / tx, j = t - (t / tx) * tx;
+  Rect r;
+  r.y0 = (int32_t)(((int64_t)i * ny) / ty);
+  r.y1 = (int32_t)(((int64_t)(i + 1) * ny) / ty);
+  r.x0 = (int32_t)(((int64_t)j * nx) / tx);
+  r.x1 = (int32_t)(((int64_t)(j + 1) * nx) / tx);
+  return r;
+}
+
+// Status bits (DevState::status).  Sticky for the run.
+enum : int32_t {
+  ST_NONFINITE_DIRTY = 1,
+  ST_NONFINITE_PSF = 2,
+  ST_PSF_OFFCENTRE = 4,
+  ST_TIMEOUT = 8,
+};
+
+// Device-resident control block of a plan.
+struct DevState {
+  int32_t status;        // ST_* bits
+  int32_t active;        // a tile can run in the next round
+  uint32_t fb_done;      // feedback blocks finished (last-block pattern)
+  int32_t pad0;
+  int64_t total;         // components in the list
+  int64_t n_rounds;      // rounds recorded (>= 1 component)
+  int64_t round_comps;   // components of the last closed round
+  int64_t max_budget;    // max over tiles of the remaining budget
+  int64_t timeout_where; // diagnostic: tile * 2^32 + barrier index of a timeout
+};
+
+// Pointers and sizes every kernel of a plan sees.
+struct PlanDev {
+  float* R;                 // residual, ny x nx
+  float* model;             // model image, ny x nx
+  const float* P;           // PSF, pny x pnx
+  int32_t ny, nx, pny, pnx, cy, cx;
+  int32_t ty, tx, T;        // tile grid and tile count
+  float gain, thr;
+  int32_t K;                // feedback interval (0 = none)
+  int32_t cap_round;        // per-tile capacity of the round buffer
+  int64_t* budget;          // [T] remaining iterations per tile
+  uint64_t* peak;           // [2][T] peak key per tile, indexed by round parity
+  int32_t* rcount;          // [T] components of the current round per tile
+  clean_component* rcomps;  // [T][cap_round] current round's components
+  clean_component* list;    // [niter] all components, list order
+  int64_t* round_off;       // [niter + 1] list offset of each recorded round
+  uint64_t* gkeys;          // [2][T * G] per-CTA partial keys (grid sync)
+  uint32_t* gbar;           // [T] grid-barrier arrival counters
+  DevState* st;
+};
+
+// Minor-loop launch configuration.
+struct MinorCfg {
+  int32_t G;          // CTAs per tile
+  int32_t sync;       // CLEAN_SYNC_CLUSTER or CLEAN_SYNC_GRID
+  int32_t resident;   // 1: residual rows live in shared memory for the round
+  int32_t threads;    // threads per CTA
+  int32_t smem;       // dynamic shared memory bytes
+  int64_t spin_limit_ns;
+  int32_t force_timeout;
+};
+
+// Launchers (return cudaError_t of the launch).
+cudaError_t launch_init(const PlanDev& d, const float* dirty, int64_t niter,
+                        cudaStream_t s);
+cudaError_t launch_validate_psf(const PlanDev& d, cudaStream_t s);
+cudaError_t launch_minor(const PlanDev& d, const MinorCfg& c, int parity,
+                         cudaStream_t s);
+cudaError_t minor_prepare(const MinorCfg& c);  // sets function attributes
+int minor_max_cluster_ctas(int G, int resident, int smem, int threads);
+cudaError_t launch_feedback(const PlanDev& d, int parity, int apply,
+                            cudaStream_t s);
+cudaError_t launch_restore_with(const PlanDev& d, float bmaj, float bmin, float bpa,
+                                float* beam_buf, int r, float* out, cudaStream_t s);
+int minor_threads();
+
+}  // namespace cleangb

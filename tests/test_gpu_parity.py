@@ -1,0 +1,194 @@
+"""Parity of the CUDA path with the CPU oracle (bit-exact in float32: the
+component list, the residual and the model image), element by element on
+seeded inputs.  Every call goes through the C ABI of libcleangb.so.
+
+Sizes span several tiles and CTA slabs and include ragged tiles (sizes not
+divisible by the grid), clipped PSFs, tie-heavy integer images, thresholds,
+every feedback interval kind (none, 1, small, larger than the budget), both
+group barriers (cluster, grid) and both residual placements (shared memory,
+global memory).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2501_01461_gb300 as cg
+import synth
+from gpu_helpers import assert_bit_exact, gpu_clean
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    cg.build()
+    cg.lib()
+
+
+SMALL = [
+    # (ny, nx, psf, tiles, K, niter, threshold, kind)
+    (16, 16, (32, 32), (1, 1), 0, 40, 0.0, "rand"),
+    (16, 16, (32, 32), (2, 2), 1, 60, 0.0, "tie"),
+    (16, 16, (32, 32), (4, 4), 3, 90, 0.05, "rand"),
+    (33, 47, (66, 94), (3, 2), 7, 200, 0.0, "rand"),
+    (64, 64, (128, 128), (2, 2), 50, 400, 0.0, "sky"),
+    (64, 64, (40, 50), (2, 3), 5, 300, 0.0, "rand"),     # clipped PSF
+    (250, 250, (500, 500), (4, 4), 10, 800, 0.0, "sky"),  # ragged 62/63-pixel tiles
+    (250, 250, (500, 500), (4, 4), 0, 800, 1e-3, "sky"),  # independent tiles
+    (128, 96, (256, 192), (1, 1), 20, 300, 0.0, "sky"),   # 1x1 grid with rounds
+    (96, 128, (192, 256), (3, 5), 1000, 900, 0.0, "tie"), # K larger than the budget
+]
+
+
+def _inputs(ny, nx, psf_shape, kind, seed):
+    rng = np.random.default_rng(seed)
+    if kind == "sky":
+        psf = synth.make_psf(*psf_shape)
+        ys, xs, fl = synth.make_sky(min(ny, nx), 8, 0.05, 2.1, rng)
+        d = synth.make_dirty(psf, min(ny, nx), ys, xs, fl, 1e-3, rng)
+        dirty = np.zeros((ny, nx), np.float32)
+        dirty[:d.shape[0], :d.shape[1]] = d
+        dirty += synth.random_image(ny, nx, rng, 1e-3)
+        return dirty, psf
+    psf = synth.random_psf(*psf_shape, rng)
+    img = synth.tie_image(ny, nx, rng) if kind == "tie" else synth.random_image(ny, nx, rng)
+    return img, psf
+
+
+@pytest.mark.parametrize("case", SMALL, ids=[f"{c[0]}x{c[1]}-t{c[3][0]}x{c[3][1]}-K{c[4]}-{c[7]}"
+                                             for c in SMALL])
+@pytest.mark.parametrize("sync", [cg.SYNC_CLUSTER, cg.SYNC_GRID])
+def test_small_bit_exact(case, sync):
+    ny, nx, ps, tiles, K, niter, thr, kind = case
+    dirty, psf = _inputs(ny, nx, ps, kind, seed=hash(case) % 2 ** 31)
+    o = oracle.clean_f32(dirty, psf, 0.2, niter, thr, tiles, K)
+    g = gpu_clean(dirty, psf, 0.2, niter, thr, tiles, K, group_sync=sync)
+    assert_bit_exact(g, o, str(case))
+
+
+@pytest.mark.parametrize("G", [1, 2, 3, 8, 16])
+def test_group_sizes_cluster(G):
+    """Every cluster size splits the tile rows differently; results agree."""
+    dirty, psf = _inputs(120, 100, (240, 200), "sky", 5)
+    o = oracle.clean_f32(dirty, psf, 0.1, 600, 0.0, (2, 2), 9)
+    g = gpu_clean(dirty, psf, 0.1, 600, 0.0, (2, 2), 9, group_ctas=G,
+                  group_sync=cg.SYNC_CLUSTER)
+    assert g["stats"]["group_ctas"] == G
+    assert_bit_exact(g, o, f"G={G}")
+
+
+@pytest.mark.parametrize("G", [1, 5, 37])
+def test_group_sizes_grid(G):
+    dirty, psf = _inputs(120, 100, (240, 200), "sky", 6)
+    o = oracle.clean_f32(dirty, psf, 0.1, 600, 0.0, (2, 2), 9)
+    g = gpu_clean(dirty, psf, 0.1, 600, 0.0, (2, 2), 9, group_ctas=G, group_sync=cg.SYNC_GRID)
+    assert g["stats"]["group_ctas"] == G and g["stats"]["group_sync"] == cg.SYNC_GRID
+    assert_bit_exact(g, o, f"G={G}")
+
+
+@pytest.mark.parametrize("sync", [cg.SYNC_CLUSTER, cg.SYNC_GRID])
+def test_streamed_residual(sync):
+    """Tiles whose CTA slabs exceed shared memory keep the residual in global
+    memory for the round."""
+    dirty, psf = _inputs(512, 512, (1024, 1024), "sky", 7)
+    o = oracle.clean_f32(dirty, psf, 0.1, 300, 0.0, (1, 2), 25)
+    g = gpu_clean(dirty, psf, 0.1, 300, 0.0, (1, 2), 25, group_ctas=1, group_sync=sync)
+    assert g["stats"]["resident"] == 0
+    assert_bit_exact(g, o, "streamed")
+
+
+def test_untiled_grid_256():
+    """Plain Hogbom CLEAN on the whole GPU: 256^2 image, 512^2 PSF, 20
+    sources, gain 0.1, 2000 iterations, threshold 5 mJy."""
+    w = synth.workload("untiled-256").build()
+    o = oracle.clean_f32(w["dirty"], w["psf"], 0.1, 2000, 5e-3)
+    g = gpu_clean(w["dirty"], w["psf"], 0.1, 2000, 5e-3, mode=cg.UNTILED_GRID)
+    assert g["stats"]["group_sync"] == cg.SYNC_GRID
+    assert_bit_exact(g, o, "untiled-256")
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("thr", [0.0, 5e-3])
+def test_tiled_1024(thr):
+    """1024^2 image, 2048^2 PSF, 2x2 tiles, K = 50, 10000 iterations: the
+    float32 lists and images are identical; the model is within 1e-4 Jy of
+    the float64 replay of the same list at every pixel."""
+    w = synth.workload("tiled-1024").build()
+    o = oracle.clean_f32(w["dirty"], w["psf"], 0.1, 10000, thr, (2, 2), 50)
+    g = gpu_clean(w["dirty"], w["psf"], 0.1, 10000, thr, (2, 2), 50)
+    assert_bit_exact(g, o, f"tiled-1024 thr={thr}")
+    rep = oracle.clean_f64(w["dirty"], w["psf"], 0.1, 10000, thr, (2, 2), 50, replay=g["comps"])
+    assert np.abs(g["model"].astype(np.float64) - rep.model).max() <= 1e-4
+
+
+def test_resume_and_step_equal_single_run():
+    """run(D, 3 rounds) + run(continue) == run(D); step/feedback == run."""
+    import torch
+    dirty, psf = _inputs(96, 96, (192, 192), "sky", 8)
+    full = gpu_clean(dirty, psf, 0.1, 400, 0.0, (2, 2), 10)
+    d_psf = torch.from_numpy(psf).cuda()
+    d_dirty = torch.from_numpy(dirty).cuda()
+    with cg.Plan(d_psf, 96, 96, gain=0.1, niter=400, tiles=(2, 2), feedback_interval=10) as p:
+        p.run(d_dirty, max_rounds=3)
+        assert p.n_components() == 3 * 4 * 10
+        p.run(None)
+        r, m, _ = p.get()
+        assert np.array_equal(r.cpu().numpy(), full["residual"])
+        assert np.array_equal(m.cpu().numpy(), full["model"])
+        # the same rounds driven one step at a time
+        p.run(d_dirty, max_rounds=0)
+        for _ in range(10):
+            p.step()
+            p.feedback()
+        p.feedback()  # nothing pending: no-op
+        r2, m2, _ = p.get()
+        assert np.array_equal(r2.cpu().numpy(), full["residual"])
+        assert p.n_components() == 400
+
+
+def test_truncated_rounds_match_oracle():
+    dirty, psf = _inputs(200, 200, (400, 400), "sky", 9)
+    for R in (1, 2, 5):
+        o = oracle.clean_f32(dirty, psf, 0.1, 2000, 0.0, (3, 3), 7, max_rounds=R)
+        g = gpu_clean(dirty, psf, 0.1, 2000, 0.0, (3, 3), 7, max_rounds=R)
+        assert_bit_exact(g, o, f"rounds={R}")
+
+
+def test_host_buffers_match_device_path():
+    dirty, psf = _inputs(128, 128, (256, 256), "sky", 10)
+    dev = gpu_clean(dirty, psf, 0.1, 500, 0.0, (2, 2), 20)
+    with cg.Plan(None, 128, 128, gain=0.1, niter=500, tiles=(2, 2), feedback_interval=20,
+                 psf_shape=psf.shape) as p:
+        res = np.empty_like(dirty)
+        mod = np.empty_like(dirty)
+        comps = np.empty(500, dtype=cg.COMPONENT_DTYPE)
+        for _ in range(2):
+            n = p.deconvolve_host(dirty, psf, res, mod, comps)
+            assert n == 500
+            assert np.array_equal(res, dev["residual"]) and np.array_equal(mod, dev["model"])
+            assert np.array_equal(comps["flux"], dev["comps"]["flux"])
+
+
+def test_empty_budget_and_zero_image():
+    dirty, psf = _inputs(32, 32, (64, 64), "rand", 11)
+    g = gpu_clean(dirty, psf, 0.1, 0, 0.0, (2, 2), 3)
+    assert g["n"] == 0 and np.array_equal(g["residual"], dirty)
+    z = np.zeros((32, 32), np.float32)
+    g = gpu_clean(z, psf, 0.1, 100, 0.0, (2, 2), 3)
+    assert g["n"] == 0 and not g["model"].any()
+
+
+def test_restore_matches_oracle():
+    import torch
+    w = synth.workload("untiled-256").build()
+    psf, dirty = w["psf"], w["dirty"]
+    bmaj, bmin, bpa = (float(np.float32(v)) for v in synth.fit_beam(psf))
+    bpa = float(np.float32(0.3))
+    d_psf, d_dirty = torch.from_numpy(psf).cuda(), torch.from_numpy(dirty).cuda()
+    with cg.Plan(d_psf, 256, 256, gain=0.1, niter=2000, threshold=5e-3, tiles=(2, 2),
+                 feedback_interval=30) as p:
+        p.run(d_dirty)
+        out = p.restore(bmaj, bmin * 0.8, bpa).cpu().numpy()
+        r, m, _ = p.get()
+        want = oracle.restore(m.cpu().numpy(), r.cpu().numpy(), bmaj, bmin * 0.8, bpa)
+        assert np.abs(out - want).max() <= 1e-5 * max(1.0, np.abs(want).max())
