@@ -118,6 +118,8 @@ typedef struct {
   int32_t resident;       /* 1 if each CTA keeps its residual rows in shared memory */
   int32_t feedback_mode;  /* the feedback path in use */
   int32_t sm_count;       /* SMs of the device */
+  int32_t feedback_tma;   /* 1 if feedback stages PSF windows with TMA */
+  int32_t minor_pipe;     /* 1 if the minor loop streams rows with bulk copies */
   int32_t reserved;
   int64_t kernel_launches;   /* kernels this plan has launched in total */
   int64_t minor_launches;    /* minor-loop launches timed (CLEAN_DEBUG_TIMING) */
@@ -228,13 +230,34 @@ CLEAN_API const char* clean_strerror(int status);
  *                              CLEAN_ERR_TIMEOUT and the kernel returns
  *   CLEAN_DEBUG_FORCE_TIMEOUT  1: the first grid-barrier wait waits for an
  *                              arrival that never comes (it must expire)
+ *   CLEAN_DEBUG_FEEDBACK_PATH  feedback kernel: 0 automatic (TMA when the
+ *                              PSF is 16-byte aligned with a row pitch that is
+ *                              a multiple of 4 floats), 1 plain loads, 2 TMA
+ *                              when possible (same results, bit for bit)
+ *   CLEAN_DEBUG_MINOR_PATH     minor-loop kernel: 0 automatic (bulk-copy
+ *                              pipeline when image and PSF rows are 16-byte
+ *                              aligned), 1 plain loads, 2 pipeline when
+ *                              possible (same results, bit for bit)
+ *   CLEAN_DEBUG_PIPE_CHUNK_PX  pipeline tuning: about this many pixels per
+ *                              staged chunk (0: 4096)
+ *   CLEAN_DEBUG_PIPE_STAGES    pipeline tuning: at most this many buffers in
+ *                              the ring (0: 8); both fail with
+ *                              CLEAN_ERR_INVALID_ARG if the ring no longer fits
  *   CLEAN_DEBUG_TIMING         1: bracket every minor-loop and feedback launch
  *                              with CUDA events on its stream and sum their
  *                              durations into clean_stats (0: off, resets)
  * clean_debug_alloc_limit(bytes): host-side cap on the bytes a plan may
  * allocate (-1 = none); a plan over it fails with CLEAN_ERR_OOM before
  * allocating. */
-enum { CLEAN_DEBUG_SPIN_LIMIT_NS = 1, CLEAN_DEBUG_FORCE_TIMEOUT = 2, CLEAN_DEBUG_TIMING = 3 };
+enum {
+  CLEAN_DEBUG_SPIN_LIMIT_NS = 1,
+  CLEAN_DEBUG_FORCE_TIMEOUT = 2,
+  CLEAN_DEBUG_TIMING = 3,
+  CLEAN_DEBUG_FEEDBACK_PATH = 4,
+  CLEAN_DEBUG_MINOR_PATH = 5,
+  CLEAN_DEBUG_PIPE_CHUNK_PX = 6,
+  CLEAN_DEBUG_PIPE_STAGES = 7
+};
 CLEAN_API int clean_debug_set(clean_plan_t plan, int32_t what, int64_t value);
 CLEAN_API void clean_debug_alloc_limit(int64_t bytes);
 

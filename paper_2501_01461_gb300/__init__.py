@@ -22,13 +22,16 @@ import numpy as np
 __all__ = ["CleanError", "Plan", "lib", "library_path", "build", "STATUS",
            "FB_GATHER", "FB_FFT", "FB_AUTO", "TILED", "UNTILED_GRID",
            "SYNC_AUTO", "SYNC_CLUSTER", "SYNC_GRID", "COMPONENT_DTYPE",
-           "DEBUG_SPIN_LIMIT_NS", "DEBUG_FORCE_TIMEOUT", "DEBUG_TIMING", "EXPORTED_SYMBOLS"]
+           "DEBUG_SPIN_LIMIT_NS", "DEBUG_FORCE_TIMEOUT", "DEBUG_TIMING", "DEBUG_FEEDBACK_PATH", "DEBUG_MINOR_PATH",
+           "DEBUG_PIPE_CHUNK_PX", "DEBUG_PIPE_STAGES",
+           "EXPORTED_SYMBOLS"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 FB_GATHER, FB_FFT, FB_AUTO = 0, 1, 2
 TILED, UNTILED_GRID = 0, 1
 SYNC_AUTO, SYNC_CLUSTER, SYNC_GRID = 0, 1, 2
 DEBUG_SPIN_LIMIT_NS, DEBUG_FORCE_TIMEOUT, DEBUG_TIMING = 1, 2, 3
+DEBUG_FEEDBACK_PATH, DEBUG_MINOR_PATH, DEBUG_PIPE_CHUNK_PX, DEBUG_PIPE_STAGES = 4, 5, 6, 7
 STATUS = {0: "CLEAN_OK", 1: "CLEAN_ERR_INVALID_ARG", 2: "CLEAN_ERR_NONFINITE",
           3: "CLEAN_ERR_OOM", 4: "CLEAN_ERR_CUDA", 5: "CLEAN_ERR_TIMEOUT",
           6: "CLEAN_ERR_UNSUPPORTED"}
@@ -58,6 +61,7 @@ class Stats(ctypes.Structure):
                 ("rounds_launched", ctypes.c_int64), ("group_ctas", ctypes.c_int32),
                 ("group_sync", ctypes.c_int32), ("resident", ctypes.c_int32),
                 ("feedback_mode", ctypes.c_int32), ("sm_count", ctypes.c_int32),
+                ("feedback_tma", ctypes.c_int32), ("minor_pipe", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("kernel_launches", ctypes.c_int64),
                 ("minor_launches", ctypes.c_int64), ("feedback_launches", ctypes.c_int64),
                 ("minor_ms", ctypes.c_double), ("feedback_ms", ctypes.c_double)]
@@ -279,7 +283,7 @@ class Plan:
     def stats(self, stream=None) -> dict:
         s = Stats()
         _check(lib().clean_stats(self._h, ctypes.byref(s), _stream_ptr(stream)), "clean_stats")
-        return {f: getattr(s, f) for f, _ in Stats._fields_ if f != "reserved"}
+        return {f: getattr(s, f) for f, _ in Stats._fields_}
 
     def deconvolve_host(self, dirty: np.ndarray, psf: np.ndarray | None = None,
                         residual: np.ndarray | None = None, model: np.ndarray | None = None,

@@ -27,7 +27,14 @@ struct clean_plan_s {
   int device = 0;
   int sm_count = 0;
   PlanDev d{};
-  MinorCfg mc{};
+  MinorCfg mc{};       // plain-load minor loop
+  MinorCfg mc_pipe{};  // bulk-copy pipeline minor loop (valid when pipe_ok)
+  bool pipe_ok = false;      // image rows 16-byte aligned and the pipeline fits
+  bool psf_aligned = false;  // PSF base and row pitch 16-byte aligned
+  int minor_path = 0;        // 0 auto, 1 plain loads, 2 pipeline
+  int pipe_chunk_px = 0;     // pipeline tuning (0: defaults)
+  int pipe_stages = 0;
+  int max_rows = 0, max_w = 0;  // largest CTA slab of the minor loop
   float* psf_own = nullptr;
   bool psf_set = false;
   int psf_status = CLEAN_OK;
@@ -46,6 +53,10 @@ struct clean_plan_s {
   std::vector<int> ev_kind;          // 0 minor, 1 feedback, per used pair
   int64_t minor_launches = 0, feedback_launches = 0;
   double minor_ms = 0.0, feedback_ms = 0.0;
+  // PSF tensor map for the TMA feedback kernel (valid when psf_map_ok)
+  CUtensorMap psf_map{};
+  bool psf_map_ok = false;
+  int feedback_path = 0;  // 0 auto, 1 plain loads, 2 TMA
 };
 
 namespace {
@@ -137,6 +148,8 @@ int read_state(clean_plan_s* pl, cudaStream_t s) {
 }
 
 int check_psf(clean_plan_s* pl, cudaStream_t s) {
+  pl->psf_map_ok = make_psf_tensor_map(&pl->psf_map, pl->d.P, pl->d.pny, pl->d.pnx);
+  pl->psf_aligned = (reinterpret_cast<uintptr_t>(pl->d.P) & 15u) == 0 && (pl->d.pnx % 4) == 0;
   cudaError_t e = cudaMemsetAsync(pl->d.st, 0, sizeof(DevState), s);
   if (e == cudaSuccess) e = launch_validate_psf(pl->d, s);
   ++pl->kernel_launches;
@@ -154,8 +167,10 @@ int check_psf(clean_plan_s* pl, cudaStream_t s) {
 
 int launch_round_feedback(clean_plan_s* pl, cudaStream_t s) {
   const int apply = (pl->d.K > 0 && pl->d.T > 1) ? 1 : 0;
+  const bool use_tma = pl->psf_map_ok && pl->feedback_path != 1;
   const int ev = timed_begin(pl, 1, s);
-  cudaError_t e = launch_feedback(pl->d, pl->parity, apply, s);
+  cudaError_t e = launch_feedback(pl->d, use_tma ? &pl->psf_map : nullptr, pl->parity, apply,
+                                  (uint64_t)pl->mc.spin_limit_ns, s);
   timed_end(pl, ev, s);
   ++pl->kernel_launches;
   if (e != cudaSuccess) return cuda_fail(pl, e);
@@ -165,9 +180,19 @@ int launch_round_feedback(clean_plan_s* pl, cudaStream_t s) {
   return CLEAN_OK;
 }
 
+// Minor-loop variant for this plan.  Automatic choice, from GB300
+// measurements: the bulk-copy pipeline for streamed (non-resident) slabs of
+// tiles at least 1024 columns wide, plain loads otherwise.
+bool use_pipe(const clean_plan_s* pl) {
+  if (!pl->pipe_ok || !pl->psf_aligned || pl->minor_path == 1) return false;
+  if (pl->minor_path == 2) return true;
+  return !pl->mc_pipe.resident && pl->max_w >= 1024;
+}
+
 int launch_round_minor(clean_plan_s* pl, cudaStream_t s) {
+  const bool pipe = use_pipe(pl);
   const int ev = timed_begin(pl, 0, s);
-  cudaError_t e = launch_minor(pl->d, pl->mc, pl->parity, s);
+  cudaError_t e = launch_minor(pl->d, pipe ? pl->mc_pipe : pl->mc, pl->parity, s);
   timed_end(pl, ev, s);
   ++pl->kernel_launches;
   if (e != cudaSuccess) return cuda_fail(pl, e);
@@ -186,6 +211,21 @@ int start_run(clean_plan_s* pl, const float* d_dirty, cudaStream_t s) {
   pl->parity = 0;
   pl->rounds_launched = 0;
   return CLEAN_OK;
+}
+
+// Pipeline geometry for the plan's group: resident slab when it fits beside
+// the ring, else streamed rows.
+bool configure_pipe(clean_plan_s* pl) {
+  MinorCfg q = pl->mc;
+  q.resident = 1;
+  bool ok = minor_pipe_geometry(q, pl->max_rows, pl->max_w, pl->pipe_chunk_px, pl->pipe_stages);
+  if (!ok) {
+    q = pl->mc;
+    q.resident = 0;
+    ok = minor_pipe_geometry(q, pl->max_rows, pl->max_w, pl->pipe_chunk_px, pl->pipe_stages);
+  }
+  if (ok) pl->mc_pipe = q;
+  return ok;
 }
 
 int common_checks(clean_plan_s* pl) {
@@ -324,7 +364,10 @@ int clean_plan(clean_plan_t* out, const clean_params* p, const float* d_psf, voi
     if (G == 0) G = sms;
   } else {
     const int per = std::max(1, sms / T);
-    if (sync == CLEAN_SYNC_AUTO) sync = (per > 16) ? CLEAN_SYNC_GRID : CLEAN_SYNC_CLUSTER;
+    // A grid-synchronised group needs all T * G CTAs resident (one per SM);
+    // measured on GB300 it beats clusters of up to 16 CTAs for every tile
+    // size tried, so clusters serve only grids with more tiles than SMs.
+    if (sync == CLEAN_SYNC_AUTO) sync = (T <= sms) ? CLEAN_SYNC_GRID : CLEAN_SYNC_CLUSTER;
     if (G == 0) {
       if (sync == CLEAN_SYNC_GRID) {
         G = per;
@@ -336,22 +379,35 @@ int clean_plan(clean_plan_t* out, const clean_params* p, const float* d_psf, voi
   }
   G = std::max(1, std::min(G, maxH));
   auto slab_bytes = [&](int g) { return (int64_t)((maxH + g - 1) / g) * maxW * 4; };
-  mc.sync = sync;
-  mc.G = G;
-  mc.resident = slab_bytes(G) <= kResidentMaxBytes ? 1 : 0;
-  mc.smem = mc.resident ? (int)slab_bytes(G) : 0;
+  // both minor-loop variants for group size g: plain loads, and the
+  // bulk-copy pipeline (resident slab if it fits beside the ring)
+  auto configure = [&](int g) {
+    mc.sync = sync;
+    mc.G = g;
+    mc.pipe = 0;
+    mc.resident = slab_bytes(g) <= kResidentMaxBytes ? 1 : 0;
+    mc.smem = mc.resident ? (int)slab_bytes(g) : 0;
+    pl->max_rows = (maxH + g - 1) / g;
+    pl->max_w = maxW;
+    pl->pipe_ok = configure_pipe(pl) && (p->nx % 4) == 0;
+  };
+  configure(G);
   if (sync == CLEAN_SYNC_CLUSTER) {
-    while (minor_max_cluster_ctas(mc.G, mc.resident, mc.smem, threads) < 1) {
+    for (;;) {
+      bool fits = minor_max_cluster_ctas(mc.G, mc.resident, mc.smem, threads) >= 1;
+      if (fits && pl->pipe_ok)
+        fits = minor_max_cluster_ctas(mc.G, pl->mc_pipe.resident, pl->mc_pipe.smem,
+                                      pl->mc_pipe.threads) >= 1;
+      if (fits) break;
       if (p->group_ctas != 0 || mc.G == 1) {
         delete pl;
         return mc.G == 1 ? CLEAN_ERR_CUDA : CLEAN_ERR_INVALID_ARG;
       }
-      mc.G /= 2;
-      mc.resident = slab_bytes(mc.G) <= kResidentMaxBytes ? 1 : 0;
-      mc.smem = mc.resident ? (int)slab_bytes(mc.G) : 0;
+      configure(mc.G / 2);
     }
   }
-  if (minor_prepare(mc) != cudaSuccess) {
+  if (minor_prepare(mc) != cudaSuccess || (pl->pipe_ok && minor_prepare(pl->mc_pipe) != cudaSuccess) ||
+      feedback_prepare(T) != cudaSuccess) {
     cudaGetLastError();
     delete pl;
     return CLEAN_ERR_CUDA;
@@ -612,10 +668,13 @@ int clean_deconvolve_host(clean_plan_t pl, const float* h_dirty, const float* h_
 int clean_stats(clean_plan_t pl, clean_stats_t* out, void* stream) {
   if (!pl || !out) return CLEAN_ERR_INVALID_ARG;
   std::memset(out, 0, sizeof(*out));
+  const bool pipe = use_pipe(pl);
   out->group_ctas = pl->mc.G;
   out->group_sync = pl->mc.sync;
-  out->resident = pl->mc.resident;
+  out->resident = pipe ? pl->mc_pipe.resident : pl->mc.resident;
+  out->minor_pipe = pipe ? 1 : 0;
   out->feedback_mode = CLEAN_FB_GATHER;
+  out->feedback_tma = (pl->psf_map_ok && pl->feedback_path != 1) ? 1 : 0;
   out->sm_count = pl->sm_count;
   out->rounds_launched = pl->rounds_launched;
   out->kernel_launches = pl->kernel_launches;
@@ -638,10 +697,42 @@ int clean_debug_set(clean_plan_t pl, int32_t what, int64_t value) {
   switch (what) {
     case CLEAN_DEBUG_SPIN_LIMIT_NS:
       if (value < 1) return CLEAN_ERR_INVALID_ARG;
-      pl->mc.spin_limit_ns = value;
+      pl->mc.spin_limit_ns = pl->mc_pipe.spin_limit_ns = value;
       return CLEAN_OK;
     case CLEAN_DEBUG_FORCE_TIMEOUT:
-      pl->mc.force_timeout = value ? 1 : 0;
+      pl->mc.force_timeout = pl->mc_pipe.force_timeout = value ? 1 : 0;
+      return CLEAN_OK;
+    case CLEAN_DEBUG_MINOR_PATH:
+      if (value < 0 || value > 2) return CLEAN_ERR_INVALID_ARG;
+      pl->minor_path = (int)value;
+      return CLEAN_OK;
+    case CLEAN_DEBUG_PIPE_CHUNK_PX:
+    case CLEAN_DEBUG_PIPE_STAGES: {
+      if (value < 0 || value > (1 << 20)) return CLEAN_ERR_INVALID_ARG;
+      const int old_chunk = pl->pipe_chunk_px, old_stages = pl->pipe_stages;
+      const MinorCfg old_cfg = pl->mc_pipe;
+      if (what == CLEAN_DEBUG_PIPE_CHUNK_PX)
+        pl->pipe_chunk_px = (int)value;
+      else
+        pl->pipe_stages = (int)value;
+      DeviceGuard g(pl->device);
+      bool ok = configure_pipe(pl);
+      if (ok && pl->mc.sync == CLEAN_SYNC_CLUSTER)
+        ok = minor_max_cluster_ctas(pl->mc_pipe.G, pl->mc_pipe.resident, pl->mc_pipe.smem,
+                                    pl->mc_pipe.threads) >= 1;
+      if (ok) ok = minor_prepare(pl->mc_pipe) == cudaSuccess;
+      if (!ok) {
+        cudaGetLastError();
+        pl->pipe_chunk_px = old_chunk;
+        pl->pipe_stages = old_stages;
+        pl->mc_pipe = old_cfg;
+        return CLEAN_ERR_INVALID_ARG;
+      }
+      return CLEAN_OK;
+    }
+    case CLEAN_DEBUG_FEEDBACK_PATH:
+      if (value < 0 || value > 2) return CLEAN_ERR_INVALID_ARG;
+      pl->feedback_path = (int)value;
       return CLEAN_OK;
     case CLEAN_DEBUG_TIMING:
       pl->timing = value != 0;

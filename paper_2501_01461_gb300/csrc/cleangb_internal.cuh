@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "cleangb.h"
@@ -109,7 +110,22 @@ struct MinorCfg {
   int32_t smem;       // dynamic shared memory bytes
   int64_t spin_limit_ns;
   int32_t force_timeout;
+  // bulk-copy pipeline (pipe = 1): rows stream through a ring of `stages`
+  // shared-memory buffers, `chunk_rows` rows per buffer
+  int32_t pipe;
+  int32_t tpr;        // consumer threads per row (power of two)
+  int32_t chunk_rows; // rows per chunk (a multiple of consumers / tpr)
+  int32_t wstride;    // floats per staged row (>= widest tile + 6, multiple of 4)
+  int32_t stages;
+  int32_t res_floats; // resident slab floats (0 when streamed)
 };
+
+// Pipeline geometry and shared-memory size for a minor-loop configuration
+// (fills the pipe fields of c; returns false if it does not fit).
+// chunk_px: target pixels per chunk (0: 4096); max_stages: ring depth cap
+// (0: 8).
+bool minor_pipe_geometry(MinorCfg& c, int max_rows, int max_w, int chunk_px = 0,
+                         int max_stages = 0);
 
 // Launchers (return cudaError_t of the launch).
 cudaError_t launch_init(const PlanDev& d, const float* dirty, int64_t niter,
@@ -119,8 +135,14 @@ cudaError_t launch_minor(const PlanDev& d, const MinorCfg& c, int parity,
                          cudaStream_t s);
 cudaError_t minor_prepare(const MinorCfg& c);  // sets function attributes
 int minor_max_cluster_ctas(int G, int resident, int smem, int threads);
-cudaError_t launch_feedback(const PlanDev& d, int parity, int apply,
-                            cudaStream_t s);
+// psf_map: a 2-D tensor map of the PSF (box 68 x 64 floats) selects the TMA
+// kernel; NULL selects the plain-load kernel.
+cudaError_t launch_feedback(const PlanDev& d, const CUtensorMap* psf_map, int parity,
+                            int apply, uint64_t limit_ns, cudaStream_t s);
+cudaError_t feedback_prepare(int T);
+// Encodes the PSF tensor map for the TMA feedback kernel; false if the PSF's
+// address or row pitch is not 16-byte aligned (or the driver lacks TMA).
+bool make_psf_tensor_map(CUtensorMap* map, const float* psf, int pny, int pnx);
 cudaError_t launch_restore_with(const PlanDev& d, float bmaj, float bmin, float bpa,
                                 float* beam_buf, int r, float* out, cudaStream_t s);
 int minor_threads();

@@ -19,7 +19,12 @@
 // components to the list (round-major, then tile, then iteration), records
 // the round's list offset, and decides whether any tile can still run
 // (budget left and |peak| > threshold).
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "cleangb_internal.cuh"
+#include "ptx.cuh"
 
 namespace cleangb {
 
@@ -84,6 +89,67 @@ __device__ __forceinline__ int find_tile(const int32_t* pre, int T, int g) {
   return lo;
 }
 
+
+// The last CTA of the feedback launch closes the round: appends the round's
+// components to the list (tile order, then iteration), records the round's
+// list offset, and decides whether any tile can run again.  Every thread of
+// every CTA calls this once, after its pixels are final.
+__device__ void close_round_if_last(const PlanDev& d, int parity, int total_blocks,
+                                    int32_t* s_cnt, int32_t* s_pre) {
+  __shared__ int s_last;
+  __shared__ int64_t s_mb[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nthr = blockDim.x, nwarps = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned done = atomicAdd(&d.st->fb_done, 1u);
+    s_last = (done == (unsigned)total_blocks - 1u);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+
+  for (int s = threadIdx.x; s < d.T; s += nthr) s_cnt[s] = ((volatile int32_t*)d.rcount)[s];
+  block_prefix(s_cnt, s_pre, d.T);
+  const int n_all = s_pre[d.T];
+  const int64_t total0 = d.st->total;
+  for (int g = threadIdx.x; g < n_all; g += nthr) {
+    const int s = find_tile(s_pre, d.T, g);
+    d.list[total0 + g] = d.rcomps[(int64_t)s * d.cap_round + (g - s_pre[s])];
+  }
+  // any tile that can run next round; largest remaining budget
+  int act = 0;
+  int64_t mb = 0;
+  for (int s = threadIdx.x; s < d.T; s += nthr) {
+    const int64_t b = ((volatile int64_t*)d.budget)[s];
+    const uint64_t pk = ((volatile unsigned long long*)d.peak)[(parity ^ 1) * d.T + s];
+    if (b > 0 && pk != 0ull && key_abs(pk) > d.thr) act = 1;
+    mb = b > mb ? b : mb;
+    d.gbar[s] = 0u;
+  }
+  act = __syncthreads_or(act);
+  for (int o = 16; o > 0; o >>= 1) {
+    const int64_t other = __shfl_xor_sync(0xffffffffu, mb, o);
+    mb = other > mb ? other : mb;
+  }
+  if (lane == 0) s_mb[warp] = mb;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t m = 0;
+    for (int w = 0; w < nwarps; ++w) m = s_mb[w] > m ? s_mb[w] : m;
+    if (n_all > 0) {
+      d.round_off[d.st->n_rounds] = total0;
+      d.st->n_rounds += 1;
+    }
+    d.st->total = total0 + n_all;
+    d.st->round_comps = n_all;
+    d.st->active = act;
+    d.st->max_budget = m;
+    d.st->fb_done = 0u;
+  }
+}
+
 __global__ void __launch_bounds__(kThreads)
     feedback_kernel(PlanDev d, int parity, int apply, int blocks_x, int blocks_y) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -91,7 +157,6 @@ __global__ void __launch_bounds__(kThreads)
   int32_t* s_cnt = reinterpret_cast<int32_t*>(s_comp + kChunk);
   int32_t* s_pre = s_cnt + d.T;  // [T + 1]
   __shared__ uint64_t s_warp[kWarps];
-  __shared__ int s_last;
 
   const int t = blockIdx.z;
   const Rect rc = tile_rect(t, d.ny, d.nx, d.ty, d.tx);
@@ -186,63 +251,228 @@ __global__ void __launch_bounds__(kThreads)
     }
   }
 
-  // ---- last CTA closes the round ----
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned total_blocks = (unsigned)(blocks_x * blocks_y * d.T);
-    const unsigned done = atomicAdd(&d.st->fb_done, 1u);
-    s_last = (done == total_blocks - 1);
-  }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
+  close_round_if_last(d, parity, blocks_x * blocks_y * d.T, s_cnt, s_pre);
+}
 
-  for (int s = threadIdx.x; s < d.T; s += kThreads) s_cnt[s] = ((volatile int32_t*)d.rcount)[s];
-  block_prefix(s_cnt, s_pre, d.T);
-  const int n_all = s_pre[d.T];
-  const int64_t total0 = d.st->total;
-  for (int g = threadIdx.x; g < n_all; g += kThreads) {
-    const int s = find_tile(s_pre, d.T, g);
-    d.list[total0 + g] = d.rcomps[(int64_t)s * d.cap_round + (g - s_pre[s])];
-  }
-  // any tile that can run next round; largest remaining budget
-  int act = 0;
-  int64_t mb = 0;
-  for (int s = threadIdx.x; s < d.T; s += kThreads) {
-    const int64_t b = ((volatile int64_t*)d.budget)[s];
-    const uint64_t pk = ((volatile unsigned long long*)d.peak)[(parity ^ 1) * d.T + s];
-    if (b > 0 && pk != 0ull && key_abs(pk) > d.thr) act = 1;
-    mb = b > mb ? b : mb;
-    d.gbar[s] = 0u;
-  }
-  act = __syncthreads_or(act);
-  // max of mb over the block
-  for (int o = 16; o > 0; o >>= 1) {
-    const int64_t other = __shfl_xor_sync(0xffffffffu, mb, o);
-    mb = other > mb ? other : mb;
-  }
-  __shared__ int64_t s_mb[kWarps];
-  if (lane == 0) s_mb[warp] = mb;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int64_t m = 0;
-    for (int w = 0; w < kWarps; ++w) m = s_mb[w] > m ? s_mb[w] : m;
-    if (n_all > 0) {
-      d.round_off[d.st->n_rounds] = total0;
-      d.st->n_rounds += 1;
+
+// ---------------------------------------------------------------------------
+// TMA variant.  The same arithmetic, with the PSF window of every component
+// staged into shared memory by one 2-D TMA box load (kBoxW x kRows floats at
+// an x rounded down to 4 floats) through a ring of kStages buffers.  A
+// producer warp issues the loads; eight consumer warps apply the updates
+// from shared memory and release each buffer through an mbarrier.  Every
+// mbarrier wait is bounded (status bit ST_TIMEOUT on expiry).
+// ---------------------------------------------------------------------------
+namespace tma {
+
+constexpr int kConsumerWarps = 8;
+constexpr int kThreads = (kConsumerWarps + 1) * 32;
+constexpr int kRowsPerWarp = 8;
+constexpr int kColsPerLane = 2;
+constexpr int kRows = kConsumerWarps * kRowsPerWarp;  // 64
+constexpr int kCols = 32 * kColsPerLane;              // 64
+constexpr int kBoxW = kCols + 4;                      // 68: covers any 4-float misalignment
+constexpr int kStages = 5;
+constexpr int kStageFloats = kBoxW * kRows;
+constexpr int kStageBytes = kStageFloats * 4;         // 17408 (multiple of 128)
+constexpr int kListCap = 1024;                        // components staged per chunk
+constexpr uint32_t kFull = 1u << 8;                   // window lies inside the PSF
+
+struct __align__(16) Win {
+  int32_t x;    // TMA x (PSF column of the window, rounded down to 4 floats)
+  int32_t y;    // PSF row of the block's first row
+  float f;      // component flux
+  uint32_t off; // bits 0-1: column offset within the box; kFull flag
+};
+
+size_t smem_bytes(int T) {
+  return 128 + (size_t)kStages * kStageBytes + (size_t)kListCap * sizeof(Win) +
+         sizeof(int32_t) * (2 * (size_t)T + 1);
+}
+
+__device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, uint64_t limit,
+                                              volatile int* abort, int32_t* status) {
+  if (ptx::mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = ptx::globaltimer_ns();
+  for (;;) {
+    if (ptx::mbar_try_wait(bar, parity)) return true;
+    if (*abort) return false;
+    if (ptx::globaltimer_ns() - t0 > limit) {
+      *abort = 1;
+      atomicOr(status, ST_TIMEOUT);
+      return false;
     }
-    d.st->total = total0 + n_all;
-    d.st->round_comps = n_all;
-    d.st->active = act;
-    d.st->max_budget = m;
-    d.st->fb_done = 0u;
   }
 }
 
+__global__ void __launch_bounds__(kThreads)
+    feedback_tma_kernel(PlanDev d, const __grid_constant__ CUtensorMap psf_map, int parity,
+                        int apply, int blocks_x, int blocks_y, uint64_t limit_ns) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  float* s_win = reinterpret_cast<float*>(base);
+  Win* s_list = reinterpret_cast<Win*>(base + (size_t)kStages * kStageBytes);
+  int32_t* s_cnt = reinterpret_cast<int32_t*>(s_list + kListCap);
+  int32_t* s_pre = s_cnt + d.T;
+  __shared__ __align__(8) uint64_t full_bar[kStages];
+  __shared__ __align__(8) uint64_t empty_bar[kStages];
+  __shared__ uint64_t s_warp[kConsumerWarps];
+  __shared__ int s_abort;
+
+  const int t = blockIdx.z;
+  const Rect rc = tile_rect(t, d.ny, d.nx, d.ty, d.tx);
+  const int by0 = rc.y0 + blockIdx.y * kRows;
+  const int bx0 = rc.x0 + blockIdx.x * kCols;
+  const bool live = by0 < rc.y1 && bx0 < rc.x1 && *(volatile int32_t*)&d.st->status == 0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool producer = warp == kConsumerWarps;
+
+  if (live) {
+    if (threadIdx.x == 0) {
+      s_abort = 0;
+      for (int i = 0; i < kStages; ++i) {
+        ptx::mbar_init(&full_bar[i], 1);
+        ptx::mbar_init(&empty_bar[i], kConsumerWarps);
+      }
+      ptx::fence_barrier_init();
+    }
+    if (producer && lane == 0) ptx::prefetch_tensormap(&psf_map);
+    for (int s = threadIdx.x; s < d.T; s += kThreads)
+      s_cnt[s] = (s == t || !apply) ? 0 : d.rcount[s];
+    block_prefix(s_cnt, s_pre, d.T);  // also orders the barrier set-up
+    const int n_other = s_pre[d.T];
+
+    float r[kRowsPerWarp][kColsPerLane];
+    const int y_first = by0 + warp * kRowsPerWarp;
+    if (!producer) {
+#pragma unroll
+      for (int i = 0; i < kRowsPerWarp; ++i)
+#pragma unroll
+        for (int j = 0; j < kColsPerLane; ++j) {
+          const int y = y_first + i, x = bx0 + lane + 32 * j;
+          r[i][j] = (y < rc.y1 && x < rc.x1) ? d.R[(int64_t)y * d.nx + x] : 0.f;
+        }
+    }
+
+    int issued = 0;  // producer: loads issued so far
+    for (int cbase = 0; cbase < n_other; cbase += kListCap) {
+      const int n = min(kListCap, n_other - cbase);
+      __syncthreads();
+      for (int jj = threadIdx.x; jj < n; jj += kThreads) {
+        const int g = cbase + jj;
+        const int s = find_tile(s_pre, d.T, g);
+        const clean_component cc = d.rcomps[(int64_t)s * d.cap_round + (g - s_pre[s])];
+        const int sy0 = by0 - cc.y + d.cy;
+        const int sx0 = bx0 - cc.x + d.cx;
+        Win w;
+        w.x = sx0 & ~3;
+        w.y = sy0;
+        w.f = cc.flux;
+        const bool inside = sy0 >= 0 && sy0 + kRows <= d.pny && sx0 >= 0 && sx0 + kCols <= d.pnx;
+        w.off = (uint32_t)(sx0 - w.x) | (inside ? kFull : 0u);
+        s_list[jj] = w;
+      }
+      __syncthreads();
+      if (producer) {
+        if (lane == 0) {
+          for (int jj = 0; jj < n; ++jj) {
+            const int j = cbase + jj;
+            const int st = j % kStages;
+            if (j >= kStages &&
+                !wait_or_abort(&empty_bar[st], (uint32_t)((j / kStages) - 1) & 1u, limit_ns,
+                               &s_abort, &d.st->status))
+              break;
+            ptx::mbar_arrive_expect_tx(&full_bar[st], kStageBytes);
+            ptx::tma_load_2d(s_win + (size_t)st * kStageFloats, &psf_map, s_list[jj].x,
+                             s_list[jj].y, &full_bar[st]);
+            ++issued;
+          }
+        }
+      } else {
+        for (int jj = 0; jj < n; ++jj) {
+          const int j = cbase + jj;
+          const int st = j % kStages;
+          if (!wait_or_abort(&full_bar[st], (uint32_t)(j / kStages) & 1u, limit_ns, &s_abort,
+                             &d.st->status))
+            break;
+          const Win w = s_list[jj];
+          const float* win = s_win + (size_t)st * kStageFloats +
+                             (warp * kRowsPerWarp) * kBoxW + (w.off & 3u) + lane;
+          if (w.off & kFull) {
+#pragma unroll
+            for (int i = 0; i < kRowsPerWarp; ++i)
+#pragma unroll
+              for (int c = 0; c < kColsPerLane; ++c)
+                r[i][c] = __fsub_rn(r[i][c], __fmul_rn(w.f, win[i * kBoxW + 32 * c]));
+          } else {
+            // window partly off the PSF array: those pixels stay unchanged
+            const int sxl = w.x + (int)(w.off & 3u) + lane;
+#pragma unroll
+            for (int i = 0; i < kRowsPerWarp; ++i) {
+              const bool yin = (unsigned)(w.y + warp * kRowsPerWarp + i) < (unsigned)d.pny;
+#pragma unroll
+              for (int c = 0; c < kColsPerLane; ++c)
+                if (yin && (unsigned)(sxl + 32 * c) < (unsigned)d.pnx)
+                  r[i][c] = __fsub_rn(r[i][c], __fmul_rn(w.f, win[i * kBoxW + 32 * c]));
+            }
+          }
+          __syncwarp();
+          if (lane == 0) ptx::mbar_arrive(&empty_bar[st]);
+        }
+      }
+    }
+    __syncthreads();
+    if (producer && lane == 0 && s_abort) {
+      // after an expired wait: let this CTA's own loads in flight land
+      for (int j = max(0, issued - kStages); j < issued; ++j) {
+        const uint64_t t0 = ptx::globaltimer_ns();
+        while (!ptx::mbar_try_wait(&full_bar[j % kStages], (uint32_t)(j / kStages) & 1u))
+          if (ptx::globaltimer_ns() - t0 > limit_ns) break;
+      }
+    }
+
+    // write back and reduce this block's peak key
+    uint64_t k = 0ull;
+    if (!producer) {
+      float best_a = -1.f, best_v = 0.f;
+      int best_i = 0x7fffffff;
+#pragma unroll
+      for (int i = 0; i < kRowsPerWarp; ++i)
+#pragma unroll
+        for (int c = 0; c < kColsPerLane; ++c) {
+          const int y = y_first + i, x = bx0 + lane + 32 * c;
+          if (y >= rc.y1 || x >= rc.x1) continue;
+          const int gi = y * d.nx + x;
+          if (n_other > 0) d.R[(int64_t)gi] = r[i][c];
+          const float a = fabsf(r[i][c]);
+          if (a > best_a || (a == best_a && gi < best_i)) {
+            best_a = a;
+            best_i = gi;
+            best_v = r[i][c];
+          }
+        }
+      k = best_a >= 0.f ? make_key(best_v, best_i) : 0ull;
+      k = warp_max_key(k);
+      if (lane == 0) s_warp[warp] = k;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint64_t m = 0;
+      for (int w = 0; w < kConsumerWarps; ++w) m = umax64(m, s_warp[w]);
+      if (m) atomicMax((unsigned long long*)&d.peak[(parity ^ 1) * d.T + t],
+                       (unsigned long long)m);
+    }
+  }
+  close_round_if_last(d, parity, blocks_x * blocks_y * d.T, s_cnt, s_pre);
+}
+
+}  // namespace tma
+
 }  // namespace
 
-cudaError_t launch_feedback(const PlanDev& d, int parity, int apply, cudaStream_t s) {
+cudaError_t launch_feedback(const PlanDev& d, const CUtensorMap* psf_map, int parity,
+                            int apply, uint64_t limit_ns, cudaStream_t s) {
   // blocks sized for the largest tile; blocks past a smaller tile's edge
   // only take part in the round close
   int maxH = 0, maxW = 0;
@@ -250,18 +480,55 @@ cudaError_t launch_feedback(const PlanDev& d, int parity, int apply, cudaStream_
     maxH = max(maxH, (int)(((int64_t)(i + 1) * d.ny) / d.ty - ((int64_t)i * d.ny) / d.ty));
   for (int j = 0; j < d.tx; ++j)
     maxW = max(maxW, (int)(((int64_t)(j + 1) * d.nx) / d.tx - ((int64_t)j * d.nx) / d.tx));
+  if (psf_map) {
+    const int bx = (maxW + tma::kCols - 1) / tma::kCols, by = (maxH + tma::kRows - 1) / tma::kRows;
+    const size_t smem = tma::smem_bytes(d.T);
+    tma::feedback_tma_kernel<<<dim3(bx, by, d.T), tma::kThreads, smem, s>>>(
+        d, *psf_map, parity, apply, bx, by, limit_ns);
+    return cudaGetLastError();
+  }
   const int bx = (maxW + kCols - 1) / kCols, by = (maxH + kRows - 1) / kRows;
   const size_t smem = sizeof(Comp4) * kChunk + sizeof(int32_t) * (2 * (size_t)d.T + 1);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(feedback_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         sizeof(Comp4) * kChunk + sizeof(int32_t) * (2 * 4096 + 1));
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
   feedback_kernel<<<dim3(bx, by, d.T), kThreads, smem, s>>>(d, parity, apply, bx, by);
   return cudaGetLastError();
+}
+
+cudaError_t feedback_prepare(int T) {
+  cudaError_t e = cudaFuncSetAttribute(feedback_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(sizeof(Comp4) * kChunk +
+                                             sizeof(int32_t) * (2 * (size_t)T + 1)));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(tma::feedback_tma_kernel,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)tma::smem_bytes(T));
+}
+
+
+bool make_psf_tensor_map(CUtensorMap* map, const float* psf, int pny, int pnx) {
+  if ((reinterpret_cast<uintptr_t>(psf) & 15u) != 0 || (pnx % 4) != 0) return false;
+  if (pnx < tma::kBoxW || pny < tma::kRows) return false;
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  std::call_once(once, [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                         cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    cudaGetLastError();
+  });
+  if (!encode) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)pnx, (cuuint64_t)pny};
+  const cuuint64_t strides[1] = {(cuuint64_t)pnx * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)tma::kBoxW, (cuuint32_t)tma::kRows};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(psf),
+                            dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
 }
 
 }  // namespace cleangb

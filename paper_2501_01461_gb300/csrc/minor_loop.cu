@@ -17,7 +17,10 @@
 // The loop stops when the tile's budget or K is reached or |v| <= threshold.
 // With `resident`, a CTA holds its rows in shared memory for the whole round
 // and only the PSF window streams in per iteration.
+#include <algorithm>
+
 #include "cleangb_internal.cuh"
+#include "ptx.cuh"
 
 namespace cleangb {
 
@@ -144,14 +147,68 @@ __device__ __forceinline__ void subtract_pass(const PlanDev& d, float* __restric
 // Block-wide max of keys; the result is valid in warp 0.
 __device__ __forceinline__ uint64_t block_max_key(uint64_t k, uint64_t* s_warp) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = (int)(blockDim.x >> 5);
   k = warp_max_key(k);
   if (lane == 0) s_warp[warp] = k;
   __syncthreads();
   if (warp == 0) {
-    k = lane < (kThreads / 32) ? s_warp[lane] : 0ull;
+    k = lane < nwarps ? s_warp[lane] : 0ull;
     k = warp_max_key(k);
   }
   return k;
+}
+
+// Step 4: every CTA of the tile group publishes its partial key `mine`
+// (valid in thread 0) and gets the group maximum back, identical in every
+// CTA.  Called by all threads; ends with a CTA barrier.  In grid mode an
+// expired barrier wait sets ST_TIMEOUT and *s_abort.
+template <int SYNC>
+__device__ __forceinline__ uint64_t exchange_keys(const PlanDev& d, const MinorCfg& c, int t,
+                                                  int rank, int64_t k, uint64_t mine,
+                                                  uint64_t* s_part, uint64_t* s_best,
+                                                  int* s_abort) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int G = c.G;
+  if (SYNC == CLEAN_SYNC_CLUSTER) {
+    if (threadIdx.x == 0) s_part[k & 1] = mine;
+    cluster_sync_all();
+    if (warp == 0) {
+      uint64_t kk = lane < G ? ld_cluster_u64(&s_part[k & 1], (uint32_t)lane) : 0ull;
+      kk = warp_max_key(kk);
+      if (lane == 0) *s_best = kk;
+    }
+  } else {
+    if (warp == 0) {
+      uint64_t* slot = d.gkeys + (int64_t)t * G + (k & 1) * ((int64_t)d.T * G);
+      int abort = 0;
+      if (lane == 0) {
+        st_relaxed_u64(slot + rank, mine);
+        red_release_add_u32(d.gbar + t, 1u);
+        const uint32_t target = (uint32_t)((k + 1) * G) + (uint32_t)(c.force_timeout ? 1 : 0);
+        const uint64_t t0 = globaltimer_ns();
+        while (ld_acquire_u32(d.gbar + t) < target) {
+          if (globaltimer_ns() - t0 > (uint64_t)c.spin_limit_ns) {
+            atomicOr(&d.st->status, ST_TIMEOUT);
+            d.st->timeout_where = ((int64_t)t << 32) | (int64_t)k;
+            abort = 1;
+            break;
+          }
+        }
+      }
+      abort = __shfl_sync(0xffffffffu, abort, 0);
+      __syncwarp();
+      uint64_t kk = 0ull;
+      if (!abort)
+        for (int j = lane; j < G; j += 32) kk = umax64(kk, ld_relaxed_u64(slot + j));
+      kk = warp_max_key(kk);
+      if (lane == 0) {
+        *s_best = kk;
+        if (abort) *s_abort = 1;
+      }
+    }
+  }
+  __syncthreads();
+  return *s_best;
 }
 
 template <int SYNC, bool RES>
@@ -171,7 +228,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int ya = rc.y0 + (int)(((int64_t)rank * H) / G);
   const int yb = rc.y0 + (int)(((int64_t)(rank + 1) * H) / G);
   const int W = rc.x1 - rc.x0;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
   // Status bits only change inside grid-synchronised launches (timeouts), so
   // every CTA of a cluster reads the same value here.
@@ -195,8 +251,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   __syncthreads();
 
-  uint64_t* gslot0 = d.gkeys + (int64_t)t * G;
-  const int64_t gstride = (int64_t)d.T * G;
   int64_t k = 0;
   while (k < kmax && key != 0ull) {
     const float v = key_value(key);
@@ -220,47 +274,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t mine = (best_a >= 0.f) ? make_key(best_v, best_i) : 0ull;
     mine = block_max_key(mine, s_warp);
 
-    if (SYNC == CLEAN_SYNC_CLUSTER) {
-      if (threadIdx.x == 0) s_part[k & 1] = mine;
-      cluster_sync_all();
-      if (warp == 0) {
-        uint64_t kk = lane < G ? ld_cluster_u64(&s_part[k & 1], (uint32_t)lane) : 0ull;
-        kk = warp_max_key(kk);
-        if (lane == 0) s_best = kk;
-      }
-    } else {
-      if (warp == 0) {
-        uint64_t* slot = gslot0 + (k & 1) * gstride;
-        int abort = 0;
-        if (lane == 0) {
-          st_relaxed_u64(slot + rank, mine);
-          red_release_add_u32(d.gbar + t, 1u);
-          const uint32_t target = (uint32_t)((k + 1) * G) + (uint32_t)(c.force_timeout ? 1 : 0);
-          const uint64_t t0 = globaltimer_ns();
-          while (ld_acquire_u32(d.gbar + t) < target) {
-            if (globaltimer_ns() - t0 > (uint64_t)c.spin_limit_ns) {
-              atomicOr(&d.st->status, ST_TIMEOUT);
-              d.st->timeout_where = ((int64_t)t << 32) | (int64_t)k;
-              abort = 1;
-              break;
-            }
-          }
-        }
-        abort = __shfl_sync(0xffffffffu, abort, 0);
-        __syncwarp();
-        uint64_t kk = 0ull;
-        if (!abort)
-          for (int j = lane; j < G; j += 32) kk = umax64(kk, ld_relaxed_u64(slot + j));
-        kk = warp_max_key(kk);
-        if (lane == 0) {
-          s_best = kk;
-          s_abort = abort;
-        }
-      }
-    }
-    __syncthreads();
+    key = exchange_keys<SYNC>(d, c, t, rank, k, mine, s_part, &s_best, &s_abort);
     if (s_abort) break;
-    key = s_best;
     ++k;
   }
 
@@ -281,17 +296,288 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Bulk-copy pipeline variant (same arithmetic, same results).  A producer
+// warp streams each iteration's rows chunk by chunk into a ring of
+// shared-memory buffers with cp.async.bulk (residual rows when they are not
+// resident, and the matching PSF row segments, rounded out to 16 bytes and
+// clipped to the PSF array); 16 consumer warps apply the subtraction from
+// shared memory, write the residual (to global memory, or to the resident
+// shared-memory slab) and track the peak.  Each mbarrier wait is bounded; a
+// CTA whose wait expires stops working but keeps joining the group exchange,
+// so every CTA of a cluster executes the same barriers.
+// ---------------------------------------------------------------------------
+constexpr int kPipeConsumers = 512;
+constexpr int kPipeThreads = kPipeConsumers + 32;
+constexpr int kPipeMaxStages = 8;
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(ptx::smem_u32(dst)), "l"(src), "r"(bytes), "r"(ptx::smem_u32(bar))
+      : "memory");
+}
+
+// (r0, r1) - f * (p0, p1), each lane a rounded multiply then a rounded
+// subtract.  Scalar on purpose: ptxas contracts a packed mul.rn.f32x2
+// followed by sub.rn.f32x2 into one fused multiply-add (a single rounding),
+// even with explicit .rn and --fmad=false, which would change the results;
+// the scalar __fmul_rn / __fsub_rn pair is never contracted.
+__device__ __forceinline__ void fms2(float& r0, float& r1, float p0, float p1, float f) {
+  r0 = __fsub_rn(r0, __fmul_rn(f, p0));
+  r1 = __fsub_rn(r1, __fmul_rn(f, p1));
+}
+
+__device__ __forceinline__ bool pipe_wait(uint64_t* bar, uint32_t parity, uint64_t limit,
+                                          volatile int* abort, int32_t* status) {
+  if (ptx::mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = ptx::globaltimer_ns();
+  for (;;) {
+    if (ptx::mbar_try_wait(bar, parity)) return true;
+    if (*abort) return false;
+    if (ptx::globaltimer_ns() - t0 > limit) {
+      *abort = 1;
+      atomicOr(status, ST_TIMEOUT);
+      return false;
+    }
+  }
+}
+
 template <int SYNC, bool RES>
-void* kernel_ptr() {
-  return (void*)minor_kernel<SYNC, RES>;
+__global__ void __launch_bounds__(kPipeThreads, 1)
+    minor_pipe_kernel(PlanDev d, MinorCfg c, int parity) {
+  extern __shared__ __align__(128) float smem[];
+  float* sRes = smem;                       // resident slab (RES), row stride WR
+  float* sStage = smem + c.res_floats;      // ring of stages
+  __shared__ __align__(8) uint64_t full_bar[kPipeMaxStages];
+  __shared__ __align__(8) uint64_t empty_bar[kPipeMaxStages];
+  __shared__ uint64_t s_warp[32];
+  __shared__ uint64_t s_part[2];
+  __shared__ uint64_t s_best;
+  __shared__ int s_abort;    // grid-barrier timeout: leave the loop
+  __shared__ int s_dead;     // mbarrier timeout: stop working, keep exchanging
+
+  const int G = c.G;
+  const int t = blockIdx.x / G;
+  const int rank = (SYNC == CLEAN_SYNC_CLUSTER) ? (int)cluster_rank() : (int)(blockIdx.x % G);
+  const Rect rc = tile_rect(t, d.ny, d.nx, d.ty, d.tx);
+  const int H = rc.y1 - rc.y0;
+  const int ya = rc.y0 + (int)(((int64_t)rank * H) / G);
+  const int yb = rc.y0 + (int)(((int64_t)(rank + 1) * H) / G);
+  const int x0 = rc.x0, x1 = rc.x1, W = x1 - x0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool producer = warp == kPipeConsumers / 32;
+  const int S = c.stages, CR = c.chunk_rows, WS = c.wstride;
+  const int stage_floats = (RES ? 1 : 2) * CR * WS;
+  const int nch = (yb - ya + CR - 1) / CR;  // chunks per iteration
+  const uint64_t limit = (uint64_t)c.spin_limit_ns;
+  const int WR = (W + 3) & ~3;              // resident slab row stride
+
+  if (*(volatile int32_t*)&d.st->status != 0) return;  // uniform, see minor_kernel
+
+  uint64_t key = d.peak[parity * d.T + t];
+  const int64_t budget = d.budget[t];
+  const int64_t kmax = (d.K > 0 && (int64_t)d.K < budget) ? (int64_t)d.K : budget;
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    s_dead = 0;
+    if (rank == 0) d.peak[(parity ^ 1) * d.T + t] = 0ull;
+    for (int i = 0; i < S; ++i) {
+      ptx::mbar_init(&full_bar[i], 1);
+      ptx::mbar_init(&empty_bar[i], kPipeConsumers / 32);
+    }
+    ptx::fence_barrier_init();
+  }
+  if (RES) {
+    const int n = (yb - ya) * W;
+    for (int i = threadIdx.x; i < n; i += kPipeThreads) {
+      const int r = i / W, cc = i - r * W;
+      sRes[r * WR + cc] = d.R[(int64_t)(ya + r) * d.nx + x0 + cc];
+    }
+  }
+  __syncthreads();
+
+  // vector geometry: 4-pixel groups (tiles whose columns start and end on a
+  // 16-byte boundary), tpr4 threads per row, rpp4 rows per pass
+  const bool vec_cols = (x0 % 4) == 0 && (W % 4) == 0;
+  const int G4 = W / 4;
+  int tpr4 = 32;
+  while (tpr4 < G4 && tpr4 < kPipeConsumers) tpr4 <<= 1;
+  const int rpp4 = kPipeConsumers / tpr4;
+  const int vrow = threadIdx.x / tpr4, vcol = threadIdx.x % tpr4;
+
+  // scalar geometry: tpr threads per row, rpp rows per pass
+  const int tpr = c.tpr, rpp = kPipeConsumers / tpr;
+  const int crow = threadIdx.x / tpr, ccol = threadIdx.x % tpr;
+  const int x0a = x0 & ~3;                             // staged residual row start
+  const int64_t row_bytes_r = (int64_t)(((x1 + 3) & ~3) - x0a) * 4;
+
+  int64_t gchunk = 0;  // ring position: chunks of all earlier iterations
+  int64_t jnext = 0;   // producer: next chunk to issue
+  int64_t k = 0;
+  while (k < kmax && key != 0ull) {
+    const float v = key_value(key);
+    if (!(fabsf(v) > d.thr)) break;
+    const int idx = key_index(key);
+    const float f = __fmul_rn(d.gain, v);  // first equation
+    const int py = idx / d.nx, px = idx - py * d.nx;
+    const int dy = d.cy - py, dx = d.cx - px;  // PSF index = pixel + (dy, dx)
+    const int pxa = (x0 + dx) & ~3;             // staged PSF row start (may be < 0)
+    // whole window inside the PSF array and 16-byte-aligned columns: the
+    // vector path with no per-pixel range checks
+    const bool fast = vec_cols && ya + dy >= 0 && yb - 1 + dy < d.pny && x0 + dx >= 0 &&
+                      x1 - 1 + dx < d.pnx;
+    if (rank == 0 && threadIdx.x == 0) {
+      clean_component cc;
+      cc.y = py;
+      cc.x = px;
+      cc.flux = f;
+      cc.tile = t;
+      d.rcomps[(int64_t)t * d.cap_round + k] = cc;
+      d.model[idx] = __fadd_rn(d.model[idx], f);
+    }
+
+    float best_a = -1.f, best_v = 0.f;
+    int best_i = 0x7fffffff;
+    if (producer) {
+      if (lane == 0) {
+        const int cs = max(0, pxa), ce = min(d.pnx, (x1 + dx + 3) & ~3);
+        for (int ch = 0; ch < nch && !*(volatile int*)&s_dead; ++ch) {
+          const int64_t j = gchunk + ch;
+          const int st = (int)(j % S);
+          if (j >= S && !pipe_wait(&empty_bar[st], (uint32_t)((j / S) - 1) & 1u, limit, &s_dead,
+                                   &d.st->status))
+            break;
+          const int r0 = ya + ch * CR, r1 = min(yb, r0 + CR);
+          uint32_t bytes = 0;
+          for (int y = r0; y < r1; ++y) {
+            if (!RES) bytes += (uint32_t)row_bytes_r;
+            const int sy = y + dy;
+            if ((unsigned)sy < (unsigned)d.pny && cs < ce) bytes += (uint32_t)(ce - cs) * 4u;
+          }
+          float* stg = sStage + (size_t)st * stage_floats;
+          ptx::mbar_arrive_expect_tx(&full_bar[st], bytes);
+          for (int y = r0; y < r1; ++y) {
+            if (!RES)
+              bulk_g2s(stg + (y - r0) * WS, d.R + (int64_t)y * d.nx + x0a, (uint32_t)row_bytes_r,
+                       &full_bar[st]);
+            const int sy = y + dy;
+            if ((unsigned)sy < (unsigned)d.pny && cs < ce)
+              bulk_g2s(stg + (RES ? 0 : CR * WS) + (y - r0) * WS + (cs - pxa),
+                       d.P + (int64_t)sy * d.pnx + cs, (uint32_t)(ce - cs) * 4u, &full_bar[st]);
+          }
+          jnext = j + 1;
+        }
+      }
+    } else {
+      for (int ch = 0; ch < nch; ++ch) {
+        const int64_t j = gchunk + ch;
+        const int st = (int)(j % S);
+        if (*(volatile int*)&s_dead ||
+            !pipe_wait(&full_bar[st], (uint32_t)(j / S) & 1u, limit, &s_dead,
+                                 &d.st->status))
+          break;
+        const int r0 = ya + ch * CR, r1 = min(yb, r0 + CR);
+        const float* stg = sStage + (size_t)st * stage_floats;
+        const float* stgP = stg + (RES ? 0 : CR * WS);
+        if (fast) {
+          for (int y = r0 + vrow; y < r1; y += rpp4) {
+            const float* rowP = stgP + (y - r0) * WS + (x0 + dx - pxa);  // pixel x0 first
+            float4* rowR4 = RES ? reinterpret_cast<float4*>(sRes + (y - ya) * WR)
+                                : reinterpret_cast<float4*>(const_cast<float*>(stg) + (y - r0) * WS);
+            float4* gR4 = reinterpret_cast<float4*>(d.R + (int64_t)y * d.nx + x0);
+            for (int g = vcol; g < G4; g += tpr4) {
+              float4 r = rowR4[g];
+              const float* pp = rowP + 4 * g;
+              fms2(r.x, r.y, pp[0], pp[1], f);
+              fms2(r.z, r.w, pp[2], pp[3], f);
+              if (RES)
+                rowR4[g] = r;
+              else
+                gR4[g] = r;
+              const float m = fmaxf(fmaxf(fabsf(r.x), fabsf(r.y)), fmaxf(fabsf(r.z), fabsf(r.w)));
+              if (m > best_a) {  // groups are visited in increasing index order
+                const int k4 = fabsf(r.x) == m ? 0 : fabsf(r.y) == m ? 1 : fabsf(r.z) == m ? 2 : 3;
+                best_a = m;
+                best_i = y * d.nx + x0 + 4 * g + k4;
+                best_v = k4 == 0 ? r.x : k4 == 1 ? r.y : k4 == 2 ? r.z : r.w;
+              }
+            }
+          }
+        } else
+        for (int y = r0 + crow; y < r1; y += rpp) {
+          const int sy = y + dy;
+          const bool yin = (unsigned)sy < (unsigned)d.pny;
+          const float* rowP = stgP + (y - r0) * WS - pxa + dx;   // index by x
+          const float* rowR = stg + (y - r0) * WS - x0a;         // index by x (streamed)
+          float* rowRes = sRes + (y - ya) * WR - x0;             // index by x (resident)
+          for (int x = x0 + ccol; x < x1; x += tpr) {
+            float r = RES ? rowRes[x] : rowR[x];
+            if (yin && (unsigned)(x + dx) < (unsigned)d.pnx) r = __fsub_rn(r, __fmul_rn(f, rowP[x]));
+            if (RES)
+              rowRes[x] = r;
+            else
+              d.R[(int64_t)y * d.nx + x] = r;
+            const float a = fabsf(r);
+            if (a > best_a) {  // pixels are visited in increasing index order
+              best_a = a;
+              best_i = y * d.nx + x;
+              best_v = r;
+            }
+          }
+        }
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(&empty_bar[st]);
+      }
+      // residual rows written through the generic proxy are read back by
+      // bulk copies (async proxy) in the next iteration
+      if (!RES) asm volatile("fence.proxy.async.global;" ::: "memory");
+    }
+    gchunk += nch;
+    uint64_t mine = (best_a >= 0.f) ? make_key(best_v, best_i) : 0ull;
+    mine = block_max_key(mine, s_warp);
+    key = exchange_keys<SYNC>(d, c, t, rank, k, mine, s_part, &s_best, &s_abort);
+    if (s_abort) break;
+    ++k;
+  }
+
+  if (SYNC == CLEAN_SYNC_CLUSTER) cluster_sync_all();
+  if (producer && lane == 0 && s_dead) {
+    // after an expired wait: let this CTA's own copies in flight land
+    for (int64_t j = max((int64_t)0, jnext - S); j < jnext; ++j) {
+      const uint64_t t0 = ptx::globaltimer_ns();
+      while (!ptx::mbar_try_wait(&full_bar[j % S], (uint32_t)(j / S) & 1u))
+        if (ptx::globaltimer_ns() - t0 > limit) break;
+    }
+  }
+  if (RES) {
+    __syncthreads();
+    const int n = (yb - ya) * W;
+    for (int i = threadIdx.x; i < n; i += kPipeThreads) {
+      const int r = i / W, cc = i - r * W;
+      d.R[(int64_t)(ya + r) * d.nx + x0 + cc] = sRes[r * WR + cc];
+    }
+  }
+  if (rank == 0 && threadIdx.x == 0) {
+    d.rcount[t] = (int32_t)k;
+    d.budget[t] = budget - k;
+  }
+}
+
+template <int SYNC, bool RES>
+void* kernel_ptr(bool pipe) {
+  return pipe ? (void*)minor_pipe_kernel<SYNC, RES> : (void*)minor_kernel<SYNC, RES>;
 }
 
 void* pick(const MinorCfg& c) {
+  const bool p = c.pipe != 0;
   if (c.sync == CLEAN_SYNC_CLUSTER)
-    return c.resident ? kernel_ptr<CLEAN_SYNC_CLUSTER, true>()
-                      : kernel_ptr<CLEAN_SYNC_CLUSTER, false>();
-  return c.resident ? kernel_ptr<CLEAN_SYNC_GRID, true>()
-                    : kernel_ptr<CLEAN_SYNC_GRID, false>();
+    return c.resident ? kernel_ptr<CLEAN_SYNC_CLUSTER, true>(p)
+                      : kernel_ptr<CLEAN_SYNC_CLUSTER, false>(p);
+  return c.resident ? kernel_ptr<CLEAN_SYNC_GRID, true>(p)
+                    : kernel_ptr<CLEAN_SYNC_GRID, false>(p);
 }
 
 }  // namespace
@@ -310,6 +596,32 @@ cudaError_t minor_prepare(const MinorCfg& c) {
 
 int minor_threads() { return kThreads; }
 
+bool minor_pipe_geometry(MinorCfg& c, int max_rows, int max_w, int chunk_px, int max_stages) {
+  // measured on GB300: streamed slabs want large chunks (few bulk copies in
+  // flight per byte); resident slabs only stage PSF rows
+  if (chunk_px <= 0) chunk_px = c.resident ? 4096 : 8192;
+  if (max_stages <= 0 || max_stages > kPipeMaxStages) max_stages = kPipeMaxStages;
+  int tpr = 32;
+  while (tpr < max_w && tpr < kPipeConsumers) tpr <<= 1;
+  const int rpp = kPipeConsumers / tpr;
+  int m = 1;
+  while ((m + 1) * rpp * max_w <= chunk_px) ++m;  // about chunk_px pixels per chunk
+  c.tpr = tpr;
+  c.chunk_rows = rpp * m;
+  c.wstride = ((max_w + 6) + 3) & ~3;
+  const int64_t stage = (int64_t)(c.resident ? 1 : 2) * c.chunk_rows * c.wstride * 4;
+  c.res_floats = c.resident ? max_rows * ((max_w + 3) & ~3) : 0;
+  c.res_floats = (c.res_floats + 31) & ~31;  // keep the stages 128-byte aligned
+  const int64_t budget = 200 * 1024 - (int64_t)c.res_floats * 4;
+  c.stages = (int)std::min<int64_t>(max_stages, budget / stage);
+  if (c.stages < 2) return false;
+  const int64_t total = (int64_t)c.res_floats * 4 + c.stages * stage;
+  c.smem = (int)total;
+  c.threads = kPipeThreads;
+  c.pipe = 1;
+  return true;
+}
+
 // Number of G-CTA clusters that can be co-resident (0 if none).
 int minor_max_cluster_ctas(int G, int resident, int smem, int threads) {
   MinorCfg c{};
@@ -317,6 +629,7 @@ int minor_max_cluster_ctas(int G, int resident, int smem, int threads) {
   c.sync = CLEAN_SYNC_CLUSTER;
   c.resident = resident;
   c.smem = smem;
+  c.pipe = threads == kPipeThreads ? 1 : 0;
   if (minor_prepare(c) != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -344,7 +657,7 @@ cudaError_t launch_minor(const PlanDev& d, const MinorCfg& c, int parity,
                          cudaStream_t s) {
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3((unsigned)(d.T * c.G), 1, 1);
-  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.blockDim = dim3(c.pipe ? kPipeThreads : kThreads, 1, 1);
   cfg.dynamicSmemBytes = c.smem;
   cfg.stream = s;
   cudaLaunchAttribute at[1];

@@ -169,9 +169,11 @@ def make_dirty(psf: np.ndarray, n: int, ys: np.ndarray, xs: np.ndarray,
 def fit_beam(psf: np.ndarray, level: float = 0.5) -> tuple[float, float, float]:
     """Gaussian clean beam (FWHM major px, FWHM minor px, position angle rad).
 
-    Second moments of the PSF main lobe: the 4-connected pixels >= ``level``
-    around the centre, weighted by their value.  The angle is measured from
-    the +x (column) axis toward +y (row).
+    Fits log P over the PSF main lobe (the 4-connected pixels >= ``level``
+    around the centre) by least squares with the quadratic form
+    -(a dx^2 + 2 b dx dy + c dy^2) / 2 (peak fixed at 1), which is exact for
+    a sampled Gaussian.  The angle of the major axis is measured from +x
+    (columns) toward +y (rows).
     """
     py, px = psf.shape
     cy, cx = py // 2, px // 2
@@ -185,20 +187,21 @@ def fit_beam(psf: np.ndarray, level: float = 0.5) -> tuple[float, float, float]:
                     and psf[yy, xx] >= level:
                 seen.add((yy, xx))
                 stack.append((yy, xx))
-    pts = np.array(sorted(seen), dtype=np.float64)
-    w = psf[pts[:, 0].astype(int), pts[:, 1].astype(int)].astype(np.float64)
-    dy, dx = pts[:, 0] - cy, pts[:, 1] - cx
-    W = w.sum()
-    syy, sxx, sxy = (w * dy * dy).sum() / W, (w * dx * dx).sum() / W, (w * dx * dy).sum() / W
-    # a truncated Gaussian's weighted second moment underestimates sigma^2;
-    # for a lobe cut at level L the moment is sigma^2 * m(L), with
-    # m(L) = 1 + L ln L / (1 - L) for the 2-D Gaussian cut at radius r_L.
-    m = 1.0 + level * math.log(level) / (1.0 - level)
-    cov = np.array([[sxx, sxy], [sxy, syy]]) / m
-    evals, evecs = np.linalg.eigh(cov)
-    smin, smaj = math.sqrt(max(evals[0], 1e-12)), math.sqrt(max(evals[1], 1e-12))
-    vx, vy = evecs[0, 1], evecs[1, 1]
+    pts = np.array(sorted(seen), dtype=np.int64)
+    v = psf[pts[:, 0], pts[:, 1]].astype(np.float64) / float(psf[cy, cx])
+    dy = (pts[:, 0] - cy).astype(np.float64)
+    dx = (pts[:, 1] - cx).astype(np.float64)
+    keep = (dy != 0) | (dx != 0)
+    A = np.stack([dx * dx, 2 * dx * dy, dy * dy], axis=1)[keep]
+    rhs = -2.0 * np.log(v[keep])
+    (a, b, c), *_ = np.linalg.lstsq(A, rhs, rcond=None)
+    inv = np.array([[a, b], [b, c]])              # inverse covariance (x, y)
+    evals, evecs = np.linalg.eigh(inv)            # ascending: major axis first
+    evals = np.maximum(evals, 1e-12)
+    smaj, smin = 1.0 / math.sqrt(evals[0]), 1.0 / math.sqrt(evals[1])
+    vx, vy = evecs[0, 0], evecs[1, 0]
     pa = math.atan2(vy, vx)
+    pa = (pa + math.pi / 2) % math.pi - math.pi / 2
     k = 2.0 * math.sqrt(2.0 * math.log(2.0))
     return k * smaj, k * smin, pa
 

@@ -7,7 +7,7 @@ import paper_2501_01461_gb300 as cg
 
 
 def gpu_clean(dirty, psf, gain, niter, threshold=0.0, tiles=(1, 1), K=0, max_rounds=-1,
-              mode=cg.TILED, group_ctas=0, group_sync=cg.SYNC_AUTO):
+              mode=cg.TILED, group_ctas=0, group_sync=cg.SYNC_AUTO, feedback_path=0, minor_path=0):
     import torch
     d_psf = torch.from_numpy(np.ascontiguousarray(psf, np.float32)).cuda()
     d_dirty = torch.from_numpy(np.ascontiguousarray(dirty, np.float32)).cuda()
@@ -15,6 +15,10 @@ def gpu_clean(dirty, psf, gain, niter, threshold=0.0, tiles=(1, 1), K=0, max_rou
     with cg.Plan(d_psf, ny, nx, gain=gain, niter=niter, threshold=threshold, tiles=tiles,
                  feedback_interval=K, mode=mode, group_ctas=group_ctas,
                  group_sync=group_sync) as plan:
+        if feedback_path:
+            plan.debug_set(cg.DEBUG_FEEDBACK_PATH, feedback_path)
+        if minor_path:
+            plan.debug_set(cg.DEBUG_MINOR_PATH, minor_path)
         plan.run(d_dirty, max_rounds=max_rounds)
         res, mod, _ = plan.get()
         comps = plan.components_with_rounds()

@@ -87,14 +87,50 @@ def test_group_sizes_grid(G):
 
 
 @pytest.mark.parametrize("sync", [cg.SYNC_CLUSTER, cg.SYNC_GRID])
-def test_streamed_residual(sync):
+@pytest.mark.parametrize("minor_path", [1, 2])
+def test_streamed_residual(sync, minor_path):
     """Tiles whose CTA slabs exceed shared memory keep the residual in global
-    memory for the round."""
+    memory for the round (plain loads, and the bulk-copy pipeline)."""
     dirty, psf = _inputs(512, 512, (1024, 1024), "sky", 7)
     o = oracle.clean_f32(dirty, psf, 0.1, 300, 0.0, (1, 2), 25)
-    g = gpu_clean(dirty, psf, 0.1, 300, 0.0, (1, 2), 25, group_ctas=1, group_sync=sync)
+    g = gpu_clean(dirty, psf, 0.1, 300, 0.0, (1, 2), 25, group_ctas=1, group_sync=sync,
+                  minor_path=minor_path)
     assert g["stats"]["resident"] == 0
+    assert g["stats"]["minor_pipe"] == (1 if minor_path == 2 else 0)
     assert_bit_exact(g, o, "streamed")
+
+
+MINOR_CASES = [
+    # (ny, nx, psf, tiles, K, niter, G, sync): resident and streamed slabs,
+    # ragged tiles, clipped PSFs, every group barrier
+    (128, 128, (256, 256), (2, 2), 7, 500, 4, cg.SYNC_CLUSTER),
+    (200, 240, (400, 480), (3, 4), 11, 900, 3, cg.SYNC_GRID),
+    (96, 160, (64, 80), (2, 2), 5, 400, 2, cg.SYNC_CLUSTER),     # clipped PSF rows/columns
+    (1024, 1024, (2048, 2048), (2, 2), 20, 600, 1, cg.SYNC_CLUSTER),  # streamed slabs
+    (300, 600, (600, 1200), (1, 1), 0, 500, 16, cg.SYNC_GRID),   # untiled-style group
+]
+
+
+@pytest.mark.parametrize("case", MINOR_CASES, ids=[f"{c[0]}x{c[1]}-t{c[3][0]}x{c[3][1]}-G{c[6]}-s{c[7]}"
+                                                   for c in MINOR_CASES])
+def test_minor_paths_bit_exact(case):
+    """Plain-load and bulk-copy-pipeline minor loops give the oracle's bits."""
+    ny, nx, ps, tiles, K, niter, G, sync = case
+    rng = np.random.default_rng(ny + nx)
+    psf = synth.make_psf(*ps) if ps[0] >= 2 * ny else synth.random_psf(*ps, rng)
+    if ps[0] >= 2 * ny:
+        ys, xs, fl = synth.make_sky(min(ny, nx), 10, 0.05, 2.1, rng)
+        d = synth.make_dirty(psf, min(ny, nx), ys, xs, fl, 1e-3, rng)
+        dirty = synth.random_image(ny, nx, rng, 1e-3)
+        dirty[:d.shape[0], :d.shape[1]] += d
+    else:
+        dirty = synth.random_image(ny, nx, rng)
+    o = oracle.clean_f32(dirty, psf, 0.1, niter, 0.0, tiles, K)
+    for path in (1, 2):
+        g = gpu_clean(dirty, psf, 0.1, niter, 0.0, tiles, K, group_ctas=G, group_sync=sync,
+                      minor_path=path)
+        assert g["stats"]["minor_pipe"] == (1 if path == 2 else 0)
+        assert_bit_exact(g, o, f"{case} path={path}")
 
 
 def test_untiled_grid_256():
@@ -192,3 +228,27 @@ def test_restore_matches_oracle():
         r, m, _ = p.get()
         want = oracle.restore(m.cpu().numpy(), r.cpu().numpy(), bmaj, bmin * 0.8, bpa)
         assert np.abs(out - want).max() <= 1e-5 * max(1.0, np.abs(want).max())
+
+
+FB_CASES = [
+    # (ny, nx, psf, tiles, K, niter)
+    (250, 250, (500, 500), (4, 4), 10, 800),    # ragged tiles, full PSF
+    (130, 200, (100, 120), (3, 2), 6, 400),     # PSF smaller than the image: clipped windows
+    (256, 256, (512, 512), (2, 2), 300, 1200),  # more components than one staged chunk
+    (300, 260, (600, 520), (5, 3), 40, 3000),
+]
+
+
+@pytest.mark.parametrize("case", FB_CASES, ids=[f"{c[0]}x{c[1]}-psf{c[2][0]}x{c[2][1]}-t{c[3][0]}x{c[3][1]}-K{c[4]}"
+                                                for c in FB_CASES])
+def test_feedback_paths_bit_exact(case):
+    """Plain-load and TMA feedback kernels give the oracle's bits."""
+    ny, nx, ps, tiles, K, niter = case
+    rng = np.random.default_rng(sum(case[:2]))
+    psf = synth.make_psf(*ps) if ps[0] >= 2 * ny else synth.random_psf(*ps, rng)
+    dirty = synth.random_image(ny, nx, rng)
+    o = oracle.clean_f32(dirty, psf, 0.1, niter, 0.0, tiles, K)
+    for path in (1, 2):
+        g = gpu_clean(dirty, psf, 0.1, niter, 0.0, tiles, K, feedback_path=path)
+        assert g["stats"]["feedback_tma"] == (1 if path == 2 else 0)
+        assert_bit_exact(g, o, f"{case} path={path}")
