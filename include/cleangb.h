@@ -214,6 +214,36 @@ CLEAN_API int clean_deconvolve_host(clean_plan_t plan, const float* h_dirty,
                           float* h_model, clean_component* h_comps,
                           int64_t comps_cap, int64_t* n_comps, void* stream);
 
+/* Plain (untiled) Hogbom CLEAN on the whole GPU without allocating any
+ * memory.  The paper has no counterpart; this entry point exists for callers
+ * that cannot allocate device memory while they run -- for example an
+ * imaging pipeline that reserves all of its device memory in one pool at
+ * start-up, because cudaMalloc can block, synchronise the device or fail on a
+ * fragmented heap, or code inside a framework that owns every allocation.
+ * The caller passes the inputs (d_dirty ny x nx, d_psf psf_ny x psf_nx,
+ * device, read only) and the outputs (d_residual and d_model ny x nx, device;
+ * d_comps room for niter components, device; *n_comps, host, receives the
+ * count); gain, niter and threshold as in clean_params; d_residual may equal
+ * d_dirty.  Results are identical to clean_plan + clean_run with
+ * CLEAN_UNTILED_GRID.  The kernels' other memory (grid-barrier counters,
+ * per-CTA partial peak keys, control words: 16.5 KiB) is a fixed array
+ * compiled into the library, which every GPU that loads the library holds
+ * until the process exits.  The first call on a device looks up that
+ * array's device address, so make the first call on each device before any
+ * stream capture.  All calls share the array and it keeps the last call's
+ * contents (the parts that must start at zero are cleared by each call):
+ * calls that overlap on the GPU -- on two streams, or from two threads --
+ * race and must be serialised by the caller.  Uses one CTA per SM, at most
+ * 1024 (CLEAN_ERR_UNSUPPORTED beyond).  Synchronises `stream`.
+ * Returns CLEAN_OK, CLEAN_ERR_INVALID_ARG (bad size or pointer, PSF peak not
+ * at the centre), CLEAN_ERR_NONFINITE, CLEAN_ERR_UNSUPPORTED, CLEAN_ERR_CUDA
+ * or CLEAN_ERR_TIMEOUT; it calls no cudaMalloc or cudaFree. */
+CLEAN_API int clean_hogbom_noalloc(const float* d_dirty, const float* d_psf, int32_t ny,
+                                   int32_t nx, int32_t psf_ny, int32_t psf_nx, float gain,
+                                   int64_t niter, float threshold, float* d_residual,
+                                   float* d_model, clean_component* d_comps,
+                                   int64_t* n_comps, void* stream);
+
 /* Fills *out (host) with the plan's counters.  Synchronises. */
 CLEAN_API int clean_stats(clean_plan_t plan, clean_stats_t* out, void* stream);
 

@@ -86,6 +86,8 @@ _SIGS = {
     "clean_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "clean_debug_set": (ctypes.c_int, [_vp, _i32, _i64]),
     "clean_debug_alloc_limit": (None, [_i64]),
+    "clean_hogbom_noalloc": (ctypes.c_int, [_vp, _vp, _i32, _i32, _i32, _i32, _f32, _i64, _f32,
+                                            _vp, _vp, _vp, _vp, _vp]),
 }
 EXPORTED_SYMBOLS = tuple(_SIGS)
 
