@@ -56,6 +56,9 @@ struct clean_plan_s {
   // PSF tensor map for the TMA feedback kernel (valid when psf_map_ok)
   CUtensorMap psf_map{};
   bool psf_map_ok = false;
+  // residual and PSF tensor maps with the pipelined minor loop's box
+  CUtensorMap r_map{}, p_map_minor{};
+  bool pipe_maps_ok = false;
   int feedback_path = 0;  // 0 auto, 1 plain loads, 2 TMA
 };
 
@@ -147,9 +150,20 @@ int read_state(clean_plan_s* pl, cudaStream_t s) {
   return CLEAN_OK;
 }
 
+// Tensor maps for the pipelined minor loop (box = its chunk geometry).
+void refresh_pipe_maps(clean_plan_s* pl) {
+  const MinorCfg& q = pl->mc_pipe;
+  pl->pipe_maps_ok =
+      pl->pipe_ok && pl->d.R && pl->d.P &&
+      make_box_tensor_map(&pl->p_map_minor, pl->d.P, pl->d.pny, pl->d.pnx, q.box_w, q.chunk_h) &&
+      (q.resident || make_box_tensor_map(&pl->r_map, pl->d.R, pl->d.ny, pl->d.nx, q.box_w,
+                                         q.chunk_h));
+}
+
 int check_psf(clean_plan_s* pl, cudaStream_t s) {
   pl->psf_map_ok = make_psf_tensor_map(&pl->psf_map, pl->d.P, pl->d.pny, pl->d.pnx);
   pl->psf_aligned = (reinterpret_cast<uintptr_t>(pl->d.P) & 15u) == 0 && (pl->d.pnx % 4) == 0;
+  refresh_pipe_maps(pl);
   cudaError_t e = cudaMemsetAsync(pl->d.st, 0, sizeof(DevState), s);
   if (e == cudaSuccess) e = launch_validate_psf(pl->d, s);
   ++pl->kernel_launches;
@@ -181,18 +195,19 @@ int launch_round_feedback(clean_plan_s* pl, cudaStream_t s) {
 }
 
 // Minor-loop variant for this plan.  Automatic choice, from GB300
-// measurements: the bulk-copy pipeline for streamed (non-resident) slabs of
-// tiles at least 1024 columns wide, plain loads otherwise.
+// measurements: the TMA pipeline whenever the slab is streamed (it wins for
+// every streamed tile shape measured), plain loads for resident slabs.
 bool use_pipe(const clean_plan_s* pl) {
-  if (!pl->pipe_ok || !pl->psf_aligned || pl->minor_path == 1) return false;
+  if (!pl->pipe_ok || !pl->pipe_maps_ok || !pl->psf_aligned || pl->minor_path == 1) return false;
   if (pl->minor_path == 2) return true;
-  return !pl->mc_pipe.resident && pl->max_w >= 1024;
+  return !pl->mc_pipe.resident;
 }
 
 int launch_round_minor(clean_plan_s* pl, cudaStream_t s) {
   const bool pipe = use_pipe(pl);
   const int ev = timed_begin(pl, 0, s);
-  cudaError_t e = launch_minor(pl->d, pipe ? pl->mc_pipe : pl->mc, pl->parity, s);
+  cudaError_t e = launch_minor(pl->d, pipe ? pl->mc_pipe : pl->mc, pl->parity, &pl->r_map,
+                               &pl->p_map_minor, s);
   timed_end(pl, ev, s);
   ++pl->kernel_launches;
   if (e != cudaSuccess) return cuda_fail(pl, e);
@@ -496,6 +511,7 @@ int clean_plan(clean_plan_t* out, const clean_params* p, const float* d_psf, voi
     clean_destroy(pl);
     return CLEAN_ERR_CUDA;
   }
+  refresh_pipe_maps(pl);
   if (d_psf) {
     rc = check_psf(pl, s);
     if (rc != CLEAN_OK) {
@@ -721,6 +737,7 @@ int clean_debug_set(clean_plan_t pl, int32_t what, int64_t value) {
         ok = minor_max_cluster_ctas(pl->mc_pipe.G, pl->mc_pipe.resident, pl->mc_pipe.smem,
                                     pl->mc_pipe.threads) >= 1;
       if (ok) ok = minor_prepare(pl->mc_pipe) == cudaSuccess;
+      if (ok) refresh_pipe_maps(pl);
       if (!ok) {
         cudaGetLastError();
         pl->pipe_chunk_px = old_chunk;

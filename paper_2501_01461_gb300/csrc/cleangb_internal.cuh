@@ -113,9 +113,9 @@ struct MinorCfg {
   // bulk-copy pipeline (pipe = 1): rows stream through a ring of `stages`
   // shared-memory buffers, `chunk_rows` rows per buffer
   int32_t pipe;
-  int32_t tpr;        // consumer threads per row (power of two)
-  int32_t chunk_rows; // rows per chunk (a multiple of consumers / tpr)
-  int32_t wstride;    // floats per staged row (>= widest tile + 6, multiple of 4)
+  int32_t chunk_w;    // columns per chunk (multiple of 4, <= 128)
+  int32_t chunk_h;    // rows per chunk
+  int32_t box_w;      // TMA box width in floats (chunk_w + 4)
   int32_t stages;
   int32_t res_floats; // resident slab floats (0 when streamed)
 };
@@ -131,8 +131,16 @@ bool minor_pipe_geometry(MinorCfg& c, int max_rows, int max_w, int chunk_px = 0,
 cudaError_t launch_init(const PlanDev& d, const float* dirty, int64_t niter,
                         cudaStream_t s);
 cudaError_t launch_validate_psf(const PlanDev& d, cudaStream_t s);
+// r_map / p_map: 2-D tensor maps of the residual and the PSF with the box
+// (c.box_w x c.chunk_h) of a pipelined configuration (ignored otherwise).
 cudaError_t launch_minor(const PlanDev& d, const MinorCfg& c, int parity,
-                         cudaStream_t s);
+                         const CUtensorMap* r_map, const CUtensorMap* p_map, cudaStream_t s);
+// Encodes a 2-D float32 tensor map (rows x cols, row pitch cols floats) with
+// the given box; false if the base or pitch is not 16-byte aligned.
+bool make_box_tensor_map(CUtensorMap* map, const float* base, int rows, int cols, int box_w,
+                         int box_h);
+bool encode_tensor_map_2d(CUtensorMap* map, const float* base, int rows, int cols, int box_w,
+                          int box_h);
 cudaError_t minor_prepare(const MinorCfg& c);  // sets function attributes
 int minor_max_cluster_ctas(int G, int resident, int smem, int threads);
 // psf_map: a 2-D tensor map of the PSF (box 68 x 64 floats) selects the TMA

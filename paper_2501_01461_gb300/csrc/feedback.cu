@@ -505,9 +505,8 @@ cudaError_t feedback_prepare(int T) {
 }
 
 
-bool make_psf_tensor_map(CUtensorMap* map, const float* psf, int pny, int pnx) {
-  if ((reinterpret_cast<uintptr_t>(psf) & 15u) != 0 || (pnx % 4) != 0) return false;
-  if (pnx < tma::kBoxW || pny < tma::kRows) return false;
+bool encode_tensor_map_2d(CUtensorMap* map, const float* base, int rows, int cols, int box_w,
+                          int box_h) {
   static std::once_flag once;
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   std::call_once(once, [] {
@@ -520,15 +519,21 @@ bool make_psf_tensor_map(CUtensorMap* map, const float* psf, int pny, int pnx) {
     cudaGetLastError();
   });
   if (!encode) return false;
-  const cuuint64_t dims[2] = {(cuuint64_t)pnx, (cuuint64_t)pny};
-  const cuuint64_t strides[1] = {(cuuint64_t)pnx * sizeof(float)};
-  const cuuint32_t box[2] = {(cuuint32_t)tma::kBoxW, (cuuint32_t)tma::kRows};
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)cols * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)box_h};
   const cuuint32_t estr[2] = {1, 1};
-  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(psf),
+  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base),
                             dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
+}
+
+bool make_psf_tensor_map(CUtensorMap* map, const float* psf, int pny, int pnx) {
+  if ((reinterpret_cast<uintptr_t>(psf) & 15u) != 0 || (pnx % 4) != 0) return false;
+  if (pnx < tma::kBoxW || pny < tma::kRows) return false;
+  return encode_tensor_map_2d(map, psf, pny, pnx, tma::kBoxW, tma::kRows);
 }
 
 }  // namespace cleangb

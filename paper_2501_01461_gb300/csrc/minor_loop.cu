@@ -298,27 +298,20 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 
 // ---------------------------------------------------------------------------
-// Bulk-copy pipeline variant (same arithmetic, same results).  A producer
-// warp streams each iteration's rows chunk by chunk into a ring of
-// shared-memory buffers with cp.async.bulk (residual rows when they are not
-// resident, and the matching PSF row segments, rounded out to 16 bytes and
-// clipped to the PSF array); 16 consumer warps apply the subtraction from
-// shared memory, write the residual (to global memory, or to the resident
-// shared-memory slab) and track the peak.  Each mbarrier wait is bounded; a
-// CTA whose wait expires stops working but keeps joining the group exchange,
-// so every CTA of a cluster executes the same barriers.
+// TMA pipeline variant (same arithmetic, same results).  The CTA's rows are
+// cut into chunks of chunk_h rows x chunk_w columns.  A producer warp loads,
+// per chunk, one 2-D TMA box of the residual (unless the rows are resident in
+// shared memory) and one box of the PSF window, each box_w x chunk_h floats
+// at an x rounded down to 4 floats, into a ring of mbarrier-guarded stages;
+// 16 consumer warps apply the subtraction from shared memory, write the
+// residual (to global memory with 16-byte stores, or to the resident slab)
+// and track the peak.  Each mbarrier wait is bounded; a CTA whose wait
+// expires stops working but keeps joining the group exchange, so every CTA
+// of a cluster executes the same barriers.
 // ---------------------------------------------------------------------------
 constexpr int kPipeConsumers = 512;
 constexpr int kPipeThreads = kPipeConsumers + 32;
 constexpr int kPipeMaxStages = 8;
-
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
-                                         uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-      ::"r"(ptx::smem_u32(dst)), "l"(src), "r"(bytes), "r"(ptx::smem_u32(bar))
-      : "memory");
-}
 
 // (r0, r1) - f * (p0, p1), each lane a rounded multiply then a rounded
 // subtract.  Scalar on purpose: ptxas contracts a packed mul.rn.f32x2
@@ -345,9 +338,73 @@ __device__ __forceinline__ bool pipe_wait(uint64_t* bar, uint32_t parity, uint64
   }
 }
 
+// Keeps the larger |r| (ties: the lower index).
+__device__ __forceinline__ void take_peak(float r, int idx, float& best_a, int& best_i,
+                                          float& best_v) {
+  const float a = fabsf(r);
+  if (a > best_a || (a == best_a && idx < best_i)) {
+    best_a = a;
+    best_i = idx;
+    best_v = r;
+  }
+}
+
+// PSF values for pixels 4g .. 4g+3 of a staged row whose first pixel sits
+// OFF floats into the 16-byte-aligned row: two aligned 16-byte loads and a
+// fixed shift (consecutive lanes read consecutive 16 bytes: no bank
+// conflicts).
+template <int OFF>
+__device__ __forceinline__ float4 psf4(const float4* rowP4, int g) {
+  const float4 a = rowP4[g];
+  if (OFF == 0) return a;
+  const float4 b = rowP4[g + 1];
+  if (OFF == 1) return make_float4(a.y, a.z, a.w, b.x);
+  if (OFF == 2) return make_float4(a.z, a.w, b.x, b.y);
+  return make_float4(a.w, b.x, b.y, b.z);
+}
+
+// Vector path over one chunk for this thread: rows r0 + vrow, + rpp4, ...;
+// 4-pixel groups vcol, + tpr4, ...  Subtracts, stores (global or resident
+// slab) and keeps the peak.
+template <bool RES, int OFF>
+__device__ __forceinline__ void chunk_vec(const PlanDev& d, float* sRes, int WR, int ya,
+                                          const float* stgR, const float* stgP, int BW,
+                                          int r0, int r1, int c0, int c1, int x0, float f,
+                                          int vrow, int rpp4, int vcol, int tpr4,
+                                          float& best_a, int& best_i, float& best_v) {
+  for (int y = r0 + vrow; y < r1; y += rpp4) {
+    const float4* rowP4 = reinterpret_cast<const float4*>(stgP + (y - r0) * BW);
+    float4* rowR4 = RES ? reinterpret_cast<float4*>(sRes + (y - ya) * WR + (c0 - x0))
+                        : reinterpret_cast<float4*>(const_cast<float*>(stgR) + (y - r0) * BW);
+    float4* gR4 = reinterpret_cast<float4*>(d.R + (int64_t)y * d.nx + c0);
+    for (int g = vcol; 4 * g < c1 - c0; g += tpr4) {
+      float4 r = rowR4[g];
+      const float4 p = psf4<OFF>(rowP4, g);
+      fms2(r.x, r.y, p.x, p.y, f);
+      fms2(r.z, r.w, p.z, p.w, f);
+      if (RES)
+        rowR4[g] = r;
+      else
+        gR4[g] = r;
+      const float m = fmaxf(fmaxf(fabsf(r.x), fabsf(r.y)), fmaxf(fabsf(r.z), fabsf(r.w)));
+      const int base = y * d.nx + c0 + 4 * g;
+      if (m > best_a || (m == best_a && base < best_i)) {
+        const int k4 = fabsf(r.x) == m ? 0 : fabsf(r.y) == m ? 1 : fabsf(r.z) == m ? 2 : 3;
+        if (m > best_a || base + k4 < best_i) {
+          best_a = m;
+          best_i = base + k4;
+          best_v = k4 == 0 ? r.x : k4 == 1 ? r.y : k4 == 2 ? r.z : r.w;
+        }
+      }
+    }
+  }
+}
+
 template <int SYNC, bool RES>
 __global__ void __launch_bounds__(kPipeThreads, 1)
-    minor_pipe_kernel(PlanDev d, MinorCfg c, int parity) {
+    minor_pipe_kernel(PlanDev d, MinorCfg c, int parity,
+                      const __grid_constant__ CUtensorMap r_map,
+                      const __grid_constant__ CUtensorMap p_map) {
   extern __shared__ __align__(128) float smem[];
   float* sRes = smem;                       // resident slab (RES), row stride WR
   float* sStage = smem + c.res_floats;      // ring of stages
@@ -369,9 +426,12 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
   const int x0 = rc.x0, x1 = rc.x1, W = x1 - x0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const bool producer = warp == kPipeConsumers / 32;
-  const int S = c.stages, CR = c.chunk_rows, WS = c.wstride;
-  const int stage_floats = (RES ? 1 : 2) * CR * WS;
-  const int nch = (yb - ya + CR - 1) / CR;  // chunks per iteration
+  const int S = c.stages, BH = c.chunk_h, CW = c.chunk_w, BW = c.box_w;
+  const int box_floats = (BW * BH + 31) & ~31;  // each box starts 128-byte aligned
+  const int stage_floats = (RES ? 1 : 2) * box_floats;
+  const uint32_t stage_bytes = (uint32_t)((RES ? 1 : 2) * BW * BH) * 4u;  // bytes the boxes land
+  const int nrb = (yb - ya + BH - 1) / BH, ncb = (W + CW - 1) / CW;
+  const int nch = nrb * ncb;                // chunks per iteration
   const uint64_t limit = (uint64_t)c.spin_limit_ns;
   const int WR = (W + 3) & ~3;              // resident slab row stride
 
@@ -390,6 +450,10 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
     }
     ptx::fence_barrier_init();
   }
+  if (producer && lane == 0) {
+    if (!RES) ptx::prefetch_tensormap(&r_map);
+    ptx::prefetch_tensormap(&p_map);
+  }
   if (RES) {
     const int n = (yb - ya) * W;
     for (int i = threadIdx.x; i < n; i += kPipeThreads) {
@@ -399,20 +463,17 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
   }
   __syncthreads();
 
-  // vector geometry: 4-pixel groups (tiles whose columns start and end on a
-  // 16-byte boundary), tpr4 threads per row, rpp4 rows per pass
-  const bool vec_cols = (x0 % 4) == 0 && (W % 4) == 0;
-  const int G4 = W / 4;
-  int tpr4 = 32;
-  while (tpr4 < G4 && tpr4 < kPipeConsumers) tpr4 <<= 1;
+  // consumer geometry within a chunk: 4-pixel groups (vector path) or single
+  // pixels, threads per row a power of two
+  const bool vec_cols = (x0 % 4) == 0 && (W % 4) == 0 && (CW % 4) == 0;
+  int tpr4 = 1;
+  while (tpr4 < CW / 4 && tpr4 < kPipeConsumers) tpr4 <<= 1;
   const int rpp4 = kPipeConsumers / tpr4;
   const int vrow = threadIdx.x / tpr4, vcol = threadIdx.x % tpr4;
-
-  // scalar geometry: tpr threads per row, rpp rows per pass
-  const int tpr = c.tpr, rpp = kPipeConsumers / tpr;
+  int tpr = 1;
+  while (tpr < CW && tpr < kPipeConsumers) tpr <<= 1;
+  const int rpp = kPipeConsumers / tpr;
   const int crow = threadIdx.x / tpr, ccol = threadIdx.x % tpr;
-  const int x0a = x0 & ~3;                             // staged residual row start
-  const int64_t row_bytes_r = (int64_t)(((x1 + 3) & ~3) - x0a) * 4;
 
   int64_t gchunk = 0;  // ring position: chunks of all earlier iterations
   int64_t jnext = 0;   // producer: next chunk to issue
@@ -424,7 +485,6 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
     const float f = __fmul_rn(d.gain, v);  // first equation
     const int py = idx / d.nx, px = idx - py * d.nx;
     const int dy = d.cy - py, dx = d.cx - px;  // PSF index = pixel + (dy, dx)
-    const int pxa = (x0 + dx) & ~3;             // staged PSF row start (may be < 0)
     // whole window inside the PSF array and 16-byte-aligned columns: the
     // vector path with no per-pixel range checks
     const bool fast = vec_cols && ya + dy >= 0 && yb - 1 + dy < d.pny && x0 + dx >= 0 &&
@@ -443,31 +503,18 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
     int best_i = 0x7fffffff;
     if (producer) {
       if (lane == 0) {
-        const int cs = max(0, pxa), ce = min(d.pnx, (x1 + dx + 3) & ~3);
         for (int ch = 0; ch < nch && !*(volatile int*)&s_dead; ++ch) {
           const int64_t j = gchunk + ch;
           const int st = (int)(j % S);
           if (j >= S && !pipe_wait(&empty_bar[st], (uint32_t)((j / S) - 1) & 1u, limit, &s_dead,
                                    &d.st->status))
             break;
-          const int r0 = ya + ch * CR, r1 = min(yb, r0 + CR);
-          uint32_t bytes = 0;
-          for (int y = r0; y < r1; ++y) {
-            if (!RES) bytes += (uint32_t)row_bytes_r;
-            const int sy = y + dy;
-            if ((unsigned)sy < (unsigned)d.pny && cs < ce) bytes += (uint32_t)(ce - cs) * 4u;
-          }
+          const int r0 = ya + (ch / ncb) * BH, c0 = x0 + (ch % ncb) * CW;
           float* stg = sStage + (size_t)st * stage_floats;
-          ptx::mbar_arrive_expect_tx(&full_bar[st], bytes);
-          for (int y = r0; y < r1; ++y) {
-            if (!RES)
-              bulk_g2s(stg + (y - r0) * WS, d.R + (int64_t)y * d.nx + x0a, (uint32_t)row_bytes_r,
-                       &full_bar[st]);
-            const int sy = y + dy;
-            if ((unsigned)sy < (unsigned)d.pny && cs < ce)
-              bulk_g2s(stg + (RES ? 0 : CR * WS) + (y - r0) * WS + (cs - pxa),
-                       d.P + (int64_t)sy * d.pnx + cs, (uint32_t)(ce - cs) * 4u, &full_bar[st]);
-          }
+          ptx::mbar_arrive_expect_tx(&full_bar[st], stage_bytes);
+          if (!RES) ptx::tma_load_2d(stg, &r_map, c0 & ~3, r0, &full_bar[st]);
+          ptx::tma_load_2d(stg + (RES ? 0 : box_floats), &p_map, (c0 + dx) & ~3, r0 + dy,
+                           &full_bar[st]);
           jnext = j + 1;
         }
       }
@@ -476,63 +523,56 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
         const int64_t j = gchunk + ch;
         const int st = (int)(j % S);
         if (*(volatile int*)&s_dead ||
-            !pipe_wait(&full_bar[st], (uint32_t)(j / S) & 1u, limit, &s_dead,
-                                 &d.st->status))
+            !pipe_wait(&full_bar[st], (uint32_t)(j / S) & 1u, limit, &s_dead, &d.st->status))
           break;
-        const int r0 = ya + ch * CR, r1 = min(yb, r0 + CR);
+        const int r0 = ya + (ch / ncb) * BH, r1 = min(yb, r0 + BH);
+        const int c0 = x0 + (ch % ncb) * CW, c1 = min(x1, c0 + CW);
         const float* stg = sStage + (size_t)st * stage_floats;
-        const float* stgP = stg + (RES ? 0 : CR * WS);
+        const float* stgR = stg;                            // streamed residual box
+        const float* stgP = stg + (RES ? 0 : box_floats);   // PSF box
+        const int offR = c0 - (c0 & ~3), offP = (c0 + dx) - ((c0 + dx) & ~3);
         if (fast) {
-          for (int y = r0 + vrow; y < r1; y += rpp4) {
-            const float* rowP = stgP + (y - r0) * WS + (x0 + dx - pxa);  // pixel x0 first
-            float4* rowR4 = RES ? reinterpret_cast<float4*>(sRes + (y - ya) * WR)
-                                : reinterpret_cast<float4*>(const_cast<float*>(stg) + (y - r0) * WS);
-            float4* gR4 = reinterpret_cast<float4*>(d.R + (int64_t)y * d.nx + x0);
-            for (int g = vcol; g < G4; g += tpr4) {
-              float4 r = rowR4[g];
-              const float* pp = rowP + 4 * g;
-              fms2(r.x, r.y, pp[0], pp[1], f);
-              fms2(r.z, r.w, pp[2], pp[3], f);
-              if (RES)
-                rowR4[g] = r;
-              else
-                gR4[g] = r;
-              const float m = fmaxf(fmaxf(fabsf(r.x), fabsf(r.y)), fmaxf(fabsf(r.z), fabsf(r.w)));
-              if (m > best_a) {  // groups are visited in increasing index order
-                const int k4 = fabsf(r.x) == m ? 0 : fabsf(r.y) == m ? 1 : fabsf(r.z) == m ? 2 : 3;
-                best_a = m;
-                best_i = y * d.nx + x0 + 4 * g + k4;
-                best_v = k4 == 0 ? r.x : k4 == 1 ? r.y : k4 == 2 ? r.z : r.w;
-              }
-            }
+          switch (offP) {
+            case 0:
+              chunk_vec<RES, 0>(d, sRes, WR, ya, stgR, stgP, BW, r0, r1, c0, c1, x0, f, vrow,
+                                rpp4, vcol, tpr4, best_a, best_i, best_v);
+              break;
+            case 1:
+              chunk_vec<RES, 1>(d, sRes, WR, ya, stgR, stgP, BW, r0, r1, c0, c1, x0, f, vrow,
+                                rpp4, vcol, tpr4, best_a, best_i, best_v);
+              break;
+            case 2:
+              chunk_vec<RES, 2>(d, sRes, WR, ya, stgR, stgP, BW, r0, r1, c0, c1, x0, f, vrow,
+                                rpp4, vcol, tpr4, best_a, best_i, best_v);
+              break;
+            default:
+              chunk_vec<RES, 3>(d, sRes, WR, ya, stgR, stgP, BW, r0, r1, c0, c1, x0, f, vrow,
+                                rpp4, vcol, tpr4, best_a, best_i, best_v);
+              break;
           }
-        } else
-        for (int y = r0 + crow; y < r1; y += rpp) {
-          const int sy = y + dy;
-          const bool yin = (unsigned)sy < (unsigned)d.pny;
-          const float* rowP = stgP + (y - r0) * WS - pxa + dx;   // index by x
-          const float* rowR = stg + (y - r0) * WS - x0a;         // index by x (streamed)
-          float* rowRes = sRes + (y - ya) * WR - x0;             // index by x (resident)
-          for (int x = x0 + ccol; x < x1; x += tpr) {
-            float r = RES ? rowRes[x] : rowR[x];
-            if (yin && (unsigned)(x + dx) < (unsigned)d.pnx) r = __fsub_rn(r, __fmul_rn(f, rowP[x]));
-            if (RES)
-              rowRes[x] = r;
-            else
-              d.R[(int64_t)y * d.nx + x] = r;
-            const float a = fabsf(r);
-            if (a > best_a) {  // pixels are visited in increasing index order
-              best_a = a;
-              best_i = y * d.nx + x;
-              best_v = r;
+        } else {
+          for (int y = r0 + crow; y < r1; y += rpp) {
+            const bool yin = (unsigned)(y + dy) < (unsigned)d.pny;
+            const float* rowP = stgP + (y - r0) * BW + offP - c0;  // index by x
+            const float* rowR = stgR + (y - r0) * BW + offR - c0;  // index by x (streamed)
+            float* rowRes = sRes + (y - ya) * WR - x0;             // index by x (resident)
+            for (int x = c0 + ccol; x < c1; x += tpr) {
+              float r = RES ? rowRes[x] : rowR[x];
+              if (yin && (unsigned)(x + dx) < (unsigned)d.pnx)
+                r = __fsub_rn(r, __fmul_rn(f, rowP[x]));
+              if (RES)
+                rowRes[x] = r;
+              else
+                d.R[(int64_t)y * d.nx + x] = r;
+              take_peak(r, y * d.nx + x, best_a, best_i, best_v);
             }
           }
         }
         __syncwarp();
         if (lane == 0) ptx::mbar_arrive(&empty_bar[st]);
       }
-      // residual rows written through the generic proxy are read back by
-      // bulk copies (async proxy) in the next iteration
+      // residual rows written through the generic proxy are read back by TMA
+      // (async proxy) in the next iteration
       if (!RES) asm volatile("fence.proxy.async.global;" ::: "memory");
     }
     gchunk += nch;
@@ -596,20 +636,25 @@ cudaError_t minor_prepare(const MinorCfg& c) {
 
 int minor_threads() { return kThreads; }
 
+bool make_box_tensor_map(CUtensorMap* map, const float* base, int rows, int cols, int box_w,
+                         int box_h) {
+  if ((reinterpret_cast<uintptr_t>(base) & 15u) != 0 || (cols % 4) != 0) return false;
+  if (box_w > 256 || box_h > 256 || box_w < 4 || (box_w % 4) != 0 || box_h < 1) return false;
+  return encode_tensor_map_2d(map, base, rows, cols, box_w, box_h);
+}
+
 bool minor_pipe_geometry(MinorCfg& c, int max_rows, int max_w, int chunk_px, int max_stages) {
-  // measured on GB300: streamed slabs want large chunks (few bulk copies in
-  // flight per byte); resident slabs only stage PSF rows
+  // measured on GB300: few large TMA boxes per byte keep the copy engine
+  // busy; streamed slabs take 8192-pixel chunks, resident ones 4096
   if (chunk_px <= 0) chunk_px = c.resident ? 4096 : 8192;
   if (max_stages <= 0 || max_stages > kPipeMaxStages) max_stages = kPipeMaxStages;
-  int tpr = 32;
-  while (tpr < max_w && tpr < kPipeConsumers) tpr <<= 1;
-  const int rpp = kPipeConsumers / tpr;
-  int m = 1;
-  while ((m + 1) * rpp * max_w <= chunk_px) ++m;  // about chunk_px pixels per chunk
-  c.tpr = tpr;
-  c.chunk_rows = rpp * m;
-  c.wstride = ((max_w + 6) + 3) & ~3;
-  const int64_t stage = (int64_t)(c.resident ? 1 : 2) * c.chunk_rows * c.wstride * 4;
+  // columns: the tile width split into equal blocks of at most 252 (the box,
+  // 4 floats wider, stays within TMA's 256); rows: up to the CTA's row count
+  const int nblk = (max_w + 251) / 252;
+  c.chunk_w = ((max_w + nblk - 1) / nblk + 3) & ~3;
+  c.box_w = c.chunk_w + 4;                       // covers any 4-float misalignment
+  c.chunk_h = std::max(1, std::min(std::min(256, max_rows), chunk_px / c.chunk_w));
+  const int64_t stage = (int64_t)(c.resident ? 1 : 2) * ((c.box_w * c.chunk_h + 31) & ~31) * 4;
   c.res_floats = c.resident ? max_rows * ((max_w + 3) & ~3) : 0;
   c.res_floats = (c.res_floats + 31) & ~31;  // keep the stages 128-byte aligned
   const int64_t budget = 200 * 1024 - (int64_t)c.res_floats * 4;
@@ -654,7 +699,7 @@ int minor_max_cluster_ctas(int G, int resident, int smem, int threads) {
 }
 
 cudaError_t launch_minor(const PlanDev& d, const MinorCfg& c, int parity,
-                         cudaStream_t s) {
+                         const CUtensorMap* r_map, const CUtensorMap* p_map, cudaStream_t s) {
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3((unsigned)(d.T * c.G), 1, 1);
   cfg.blockDim = dim3(c.pipe ? kPipeThreads : kThreads, 1, 1);
@@ -674,6 +719,12 @@ cudaError_t launch_minor(const PlanDev& d, const MinorCfg& c, int parity,
   cfg.numAttrs = 1;
   PlanDev dd = d;
   MinorCfg cc = c;
+  if (c.pipe) {
+    if (!p_map || (!c.resident && !r_map)) return cudaErrorInvalidValue;
+    CUtensorMap rm = c.resident ? *p_map : *r_map, pm = *p_map;
+    void* args[] = {&dd, &cc, &parity, &rm, &pm};
+    return cudaLaunchKernelExC(&cfg, pick(c), args);
+  }
   void* args[] = {&dd, &cc, &parity};
   return cudaLaunchKernelExC(&cfg, pick(c), args);
 }

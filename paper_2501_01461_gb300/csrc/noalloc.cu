@@ -157,7 +157,7 @@ extern "C" CLEAN_API int clean_hogbom_noalloc(const float* d_dirty, const float*
   }
   if (hs.status & (ST_NONFINITE_DIRTY | ST_NONFINITE_PSF)) return CLEAN_ERR_NONFINITE;
   if (hs.status & ST_PSF_OFFCENTRE) return CLEAN_ERR_INVALID_ARG;
-  e = launch_minor(d, mc, 0, s);
+  e = launch_minor(d, mc, 0, nullptr, nullptr, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(&hs, d.st, sizeof(DevState), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess)
