@@ -8,6 +8,8 @@
 #include <new>
 #include <vector>
 
+#include <cufft.h>
+
 #include "cleangb_internal.cuh"
 
 using namespace cleangb;
@@ -59,6 +61,16 @@ struct clean_plan_s {
   // residual and PSF tensor maps with the pipelined minor loop's box
   CUtensorMap r_map{}, p_map_minor{};
   bool pipe_maps_ok = false;
+  // FFT feedback (feedback_mode FFT, or AUTO when it is estimated faster)
+  bool fft = false;
+  int Ly = 0, Lx = 0;
+  cufftHandle fft_r2c = 0, fft_c2r = 0;
+  bool fft_plans = false;
+  float* fft_A = nullptr;    // component grid, Ly x Lx, kept zero between rounds
+  float* fft_S = nullptr;    // convolution result, Ly x Lx
+  void* fft_X = nullptr;     // spectrum work, Ly x (Lx/2+1) complex
+  void* fft_Kh = nullptr;    // PSF kernel spectrum, Ly x (Lx/2+1) complex
+  float* R0 = nullptr;       // residual at the start of the current round
   int feedback_path = 0;  // 0 auto, 1 plain loads, 2 TMA
 };
 
@@ -150,6 +162,29 @@ int read_state(clean_plan_s* pl, cudaStream_t s) {
   return CLEAN_OK;
 }
 
+// Smallest n >= m whose only prime factors are 2, 3, 5 and 7.
+int fft_size(int m) {
+  for (int n = std::max(m, 1);; ++n) {
+    int r = n;
+    for (int f : {2, 3, 5, 7})
+      while (r % f == 0) r /= f;
+    if (r == 1) return n;
+  }
+}
+
+// PSF kernel spectrum for the FFT feedback (after every PSF change).
+int fft_prepare_psf(clean_plan_s* pl, cudaStream_t s) {
+  if (!pl->fft) return CLEAN_OK;
+  cudaError_t e = fft_build_kernel_image(pl->d, pl->Ly, pl->Lx, pl->fft_S, s);
+  if (e != cudaSuccess) return cuda_fail(pl, e);
+  if (cufftSetStream(pl->fft_r2c, s) != CUFFT_SUCCESS ||
+      cufftExecR2C(pl->fft_r2c, pl->fft_S, reinterpret_cast<cufftComplex*>(pl->fft_Kh)) !=
+          CUFFT_SUCCESS)
+    return poison(pl, CLEAN_ERR_CUDA);
+  pl->kernel_launches += 1;
+  return CLEAN_OK;
+}
+
 // Tensor maps for the pipelined minor loop (box = its chunk geometry).
 void refresh_pipe_maps(clean_plan_s* pl) {
   const MinorCfg& q = pl->mc_pipe;
@@ -176,11 +211,44 @@ int check_psf(clean_plan_s* pl, cudaStream_t s) {
                    : (bits & ST_PSF_OFFCENTRE) ? CLEAN_ERR_INVALID_ARG
                                                : CLEAN_OK;
   pl->started = false;  // a run's state refers to the old PSF
+  if (pl->psf_status == CLEAN_OK && (rc = fft_prepare_psf(pl, s)) != CLEAN_OK) return rc;
   return pl->psf_status;
+}
+
+// One FFT feedback: scatter the round's components, convolve with the PSF
+// through the cached spectrum, R <- R0 - S everywhere, next peaks, close.
+cudaError_t launch_fft_feedback(clean_plan_s* pl, cudaStream_t s) {
+  const int64_t pitch = pl->Lx;
+  const int64_t nspec = (int64_t)pl->Ly * (pl->Lx / 2 + 1);
+  cudaError_t e = fft_launch_scatter(pl->d, pl->fft_A, pitch, s);
+  if (e != cudaSuccess) return e;
+  if (cufftSetStream(pl->fft_r2c, s) != CUFFT_SUCCESS ||
+      cufftSetStream(pl->fft_c2r, s) != CUFFT_SUCCESS ||
+      cufftExecR2C(pl->fft_r2c, pl->fft_A, reinterpret_cast<cufftComplex*>(pl->fft_X)) !=
+          CUFFT_SUCCESS)
+    return cudaErrorUnknown;
+  e = fft_launch_multiply(pl->fft_X, pl->fft_Kh, nspec, 1.0f / ((float)pl->Ly * (float)pl->Lx), s);
+  if (e != cudaSuccess) return e;
+  if (cufftExecC2R(pl->fft_c2r, reinterpret_cast<cufftComplex*>(pl->fft_X), pl->fft_S) !=
+      CUFFT_SUCCESS)
+    return cudaErrorUnknown;
+  pl->kernel_launches += 2;
+  return fft_launch_subtract(pl->d, pl->R0, pl->fft_S, pitch, pl->fft_A, pl->parity, s);
 }
 
 int launch_round_feedback(clean_plan_s* pl, cudaStream_t s) {
   const int apply = (pl->d.K > 0 && pl->d.T > 1) ? 1 : 0;
+  if (apply && pl->fft) {
+    const int ev = timed_begin(pl, 1, s);
+    cudaError_t e = launch_fft_feedback(pl, s);
+    timed_end(pl, ev, s);
+    ++pl->kernel_launches;
+    if (e != cudaSuccess) return cuda_fail(pl, e);
+    pl->parity ^= 1;
+    pl->pending = false;
+    ++pl->rounds_launched;
+    return CLEAN_OK;
+  }
   const bool use_tma = pl->psf_map_ok && pl->feedback_path != 1;
   const int ev = timed_begin(pl, 1, s);
   cudaError_t e = launch_feedback(pl->d, use_tma ? &pl->psf_map : nullptr, pl->parity, apply,
@@ -220,6 +288,9 @@ int start_run(clean_plan_s* pl, const float* d_dirty, cudaStream_t s) {
   if (e == cudaSuccess) e = cudaMemsetAsync(pl->d.st, 0, sizeof(DevState), s);
   if (e == cudaSuccess) e = launch_init(pl->d, d_dirty, pl->p.niter, s);
   ++pl->kernel_launches;
+  if (e == cudaSuccess && pl->fft)
+    e = cudaMemcpyAsync(pl->R0, pl->d.R, sizeof(float) * (size_t)pl->d.ny * pl->d.nx,
+                        cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return cuda_fail(pl, e);
   pl->started = true;
   pl->pending = false;
@@ -329,6 +400,10 @@ void clean_destroy(clean_plan_t pl) {
   {
     DeviceGuard g(pl->device);
     cudaDeviceSynchronize();
+    if (pl->fft_plans) {
+      cufftDestroy(pl->fft_r2c);
+      cufftDestroy(pl->fft_c2r);
+    }
     for (void* a : pl->allocs) cudaFree(a);
     for (cudaEvent_t e : pl->ev_pool) cudaEventDestroy(e);
     if (pl->h_st) cudaFreeHost(pl->h_st);
@@ -342,7 +417,7 @@ int clean_plan(clean_plan_t* out, const clean_params* p, const float* d_psf, voi
   *out = nullptr;
   int rc = clean_params_check(p);
   if (rc != CLEAN_OK) return rc;
-  if (p->feedback_mode == CLEAN_FB_FFT) return CLEAN_ERR_UNSUPPORTED;
+
 
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -449,6 +524,22 @@ int clean_plan(clean_plan_t* out, const clean_params* p, const float* d_psf, voi
     void** dst;
     size_t bytes;
   };
+  // FFT feedback: a grid of at least (2 ny - 1) x (2 nx - 1) so the circular
+  // convolution never wraps onto an image pixel.  AUTO takes it when a round's
+  // gather (about 0.26 ns per pixel-component update on GB300) would cost more
+  // than the transforms (estimated 16 ps per grid cell plus 60 us of launches).
+  const bool feedback_on = p->feedback_interval > 0 && T > 1;
+  pl->Ly = fft_size(2 * p->ny - 1);
+  pl->Lx = fft_size(2 * p->nx - 1);
+  if (feedback_on && p->feedback_mode == CLEAN_FB_FFT) pl->fft = true;
+  if (feedback_on && p->feedback_mode == CLEAN_FB_AUTO) {
+    const double comps = (double)std::min<int64_t>(p->feedback_interval, per_tile_max) * T;
+    const double gather_s = comps * ((double)npix - (double)npix / T) * 0.26e-9;
+    const double fft_s = (double)pl->Ly * pl->Lx * 16e-12 + 60e-6;
+    pl->fft = fft_s < gather_s;
+  }
+  const size_t grid_bytes = sizeof(float) * (size_t)pl->Ly * pl->Lx;
+  const size_t spec_bytes = sizeof(cufftComplex) * (size_t)pl->Ly * (pl->Lx / 2 + 1);
   const int beam_n = (2 * kMaxBeamRadius + 1) * (2 * kMaxBeamRadius + 1);
   std::vector<Req> req = {
       {(void**)&pl->d.R, sizeof(float) * (size_t)npix},
@@ -465,6 +556,13 @@ int clean_plan(clean_plan_t* out, const clean_params* p, const float* d_psf, voi
       {(void**)&pl->beam_buf, sizeof(float) * (size_t)beam_n},
   };
   if (!d_psf) req.push_back({(void**)&pl->psf_own, sizeof(float) * (size_t)p->psf_ny * p->psf_nx});
+  if (pl->fft) {
+    req.push_back({(void**)&pl->fft_A, grid_bytes});
+    req.push_back({(void**)&pl->fft_S, grid_bytes});
+    req.push_back({(void**)&pl->fft_X, spec_bytes});
+    req.push_back({(void**)&pl->fft_Kh, spec_bytes});
+    req.push_back({(void**)&pl->R0, sizeof(float) * (size_t)npix});
+  }
   size_t total = 0;
   for (auto& r : req) total += r.bytes;
   const int64_t lim = g_alloc_limit.load();
@@ -505,6 +603,23 @@ int clean_plan(clean_plan_t* out, const clean_params* p, const float* d_psf, voi
   d.K = p->feedback_interval;
   d.cap_round = (int32_t)cap_round;
 
+  if (pl->fft) {
+    if (cufftPlan2d(&pl->fft_r2c, pl->Ly, pl->Lx, CUFFT_R2C) != CUFFT_SUCCESS) {
+      clean_destroy(pl);
+      return CLEAN_ERR_OOM;
+    }
+    if (cufftPlan2d(&pl->fft_c2r, pl->Ly, pl->Lx, CUFFT_C2R) != CUFFT_SUCCESS) {
+      cufftDestroy(pl->fft_r2c);
+      clean_destroy(pl);
+      return CLEAN_ERR_OOM;
+    }
+    pl->fft_plans = true;
+    if (cudaMemsetAsync(pl->fft_A, 0, grid_bytes, s) != cudaSuccess) {
+      cudaGetLastError();
+      clean_destroy(pl);
+      return CLEAN_ERR_CUDA;
+    }
+  }
   if (cudaMemsetAsync(d.gbar, 0, sizeof(uint32_t) * T, s) != cudaSuccess ||
       cudaMemsetAsync(d.st, 0, sizeof(DevState), s) != cudaSuccess) {
     cudaGetLastError();
@@ -689,7 +804,7 @@ int clean_stats(clean_plan_t pl, clean_stats_t* out, void* stream) {
   out->group_sync = pl->mc.sync;
   out->resident = pipe ? pl->mc_pipe.resident : pl->mc.resident;
   out->minor_pipe = pipe ? 1 : 0;
-  out->feedback_mode = CLEAN_FB_GATHER;
+  out->feedback_mode = pl->fft ? CLEAN_FB_FFT : CLEAN_FB_GATHER;
   out->feedback_tma = (pl->psf_map_ok && pl->feedback_path != 1) ? 1 : 0;
   out->sm_count = pl->sm_count;
   out->rounds_launched = pl->rounds_launched;

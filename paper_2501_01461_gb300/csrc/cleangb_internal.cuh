@@ -148,6 +148,14 @@ int minor_max_cluster_ctas(int G, int resident, int smem, int threads);
 cudaError_t launch_feedback(const PlanDev& d, const CUtensorMap* psf_map, int parity,
                             int apply, uint64_t limit_ns, cudaStream_t s);
 cudaError_t feedback_prepare(int T);
+// FFT feedback pieces (see feedback.cu).  Grids are Ly x Lx floats (pitch Lx).
+cudaError_t fft_build_kernel_image(const PlanDev& d, int Ly, int Lx, float* Kimg,
+                                   cudaStream_t s);
+cudaError_t fft_launch_scatter(const PlanDev& d, float* A, int64_t pitch, cudaStream_t s);
+cudaError_t fft_launch_multiply(void* X, const void* Kh, int64_t n, float scale,
+                                cudaStream_t s);
+cudaError_t fft_launch_subtract(const PlanDev& d, float* R0, const float* S, int64_t pitch,
+                                float* A, int parity, cudaStream_t s);
 // Encodes the PSF tensor map for the TMA feedback kernel; false if the PSF's
 // address or row pitch is not 16-byte aligned (or the driver lacks TMA).
 bool make_psf_tensor_map(CUtensorMap* map, const float* psf, int pny, int pnx);

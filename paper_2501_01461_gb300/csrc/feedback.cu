@@ -95,7 +95,8 @@ __device__ __forceinline__ int find_tile(const int32_t* pre, int T, int g) {
 // list offset, and decides whether any tile can run again.  Every thread of
 // every CTA calls this once, after its pixels are final.
 __device__ void close_round_if_last(const PlanDev& d, int parity, int total_blocks,
-                                    int32_t* s_cnt, int32_t* s_pre) {
+                                    int32_t* s_cnt, int32_t* s_pre, float* clear_grid = nullptr,
+                                    int64_t clear_pitch = 0) {
   __shared__ int s_last;
   __shared__ int64_t s_mb[32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -116,7 +117,9 @@ __device__ void close_round_if_last(const PlanDev& d, int parity, int total_bloc
   const int64_t total0 = d.st->total;
   for (int g = threadIdx.x; g < n_all; g += nthr) {
     const int s = find_tile(s_pre, d.T, g);
-    d.list[total0 + g] = d.rcomps[(int64_t)s * d.cap_round + (g - s_pre[s])];
+    const clean_component cc = d.rcomps[(int64_t)s * d.cap_round + (g - s_pre[s])];
+    d.list[total0 + g] = cc;
+    if (clear_grid) clear_grid[(int64_t)cc.y * clear_pitch + cc.x] = 0.f;
   }
   // any tile that can run next round; largest remaining budget
   int act = 0;
@@ -469,6 +472,105 @@ __global__ void __launch_bounds__(kThreads)
 
 }  // namespace tma
 
+
+// ---------------------------------------------------------------------------
+// FFT feedback (tolerance-exact alternative to the gather).  The round's
+// components, scattered onto an L x L grid (L >= 2N - 1 in each axis),
+// convolved circularly with the PSF kernel K[d mod L] = P[d + c] give, at
+// every image pixel q, S[q] = sum_c f_c P[q - p_c + c] with no wrap-around.
+// The residual after the round is then the residual at the round's start
+// minus S on every pixel of every tile (the minor loops' own-tile
+// subtractions included), so no per-tile correction is needed.
+// ---------------------------------------------------------------------------
+constexpr int kFftThreads = 256;
+constexpr int kFftRows = 16;
+
+// K[(dy mod Ly), (dx mod Lx)] = P[dy + cy, dx + cx] for |dy| < ny, |dx| < nx
+// inside the PSF; zero elsewhere.  One thread per grid element.
+__global__ void fft_kernel_image(const float* __restrict__ P, int pny, int pnx, int cy, int cx,
+                                 int ny, int nx, int Ly, int Lx, float* __restrict__ Kimg) {
+  const int64_t n = (int64_t)Ly * Lx;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int my = (int)(i / Lx), mx = (int)(i - (int64_t)my * Lx);
+    const int dy = my < ny ? my : my - Ly;   // represent m as d in (-(L - ny), ny)
+    const int dx = mx < nx ? mx : mx - Lx;
+    float v = 0.f;
+    if (dy > -ny && dx > -nx) {
+      const int sy = dy + cy, sx = dx + cx;
+      if ((unsigned)sy < (unsigned)pny && (unsigned)sx < (unsigned)pnx)
+        v = P[(int64_t)sy * pnx + sx];
+    }
+    Kimg[i] = v;
+  }
+}
+
+// The round's components onto the (zeroed) grid: one thread per tile, its
+// components in iteration order, so the sums are deterministic.
+__global__ void fft_scatter(PlanDev d, float* __restrict__ A, int64_t pitch) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= d.T) return;
+  const int n = d.rcount[t];
+  for (int k = 0; k < n; ++k) {
+    const clean_component cc = d.rcomps[(int64_t)t * d.cap_round + k];
+    float* a = &A[(int64_t)cc.y * pitch + cc.x];
+    *a = *a + cc.flux;
+  }
+}
+
+// X <- X * K / (Ly Lx), complex, element by element.
+__global__ void fft_multiply(float2* __restrict__ X, const float2* __restrict__ Kh, int64_t n,
+                             float scale) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float2 a = X[i], b = Kh[i];
+    X[i] = make_float2((a.x * b.x - a.y * b.y) * scale, (a.x * b.y + a.y * b.x) * scale);
+  }
+}
+
+// R <- R0 - S on tile t's rows [ya, ya + kFftRows); R0 <- R; the block's
+// peak into the tile's next-round key; the last block closes the round and
+// clears the scattered grid cells.
+__global__ void __launch_bounds__(kFftThreads)
+    fft_subtract(PlanDev d, float* __restrict__ R0, const float* __restrict__ S, int64_t pitch,
+                 float* __restrict__ A, int parity, int blocks_x) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  int32_t* s_cnt = reinterpret_cast<int32_t*>(smem_raw);
+  int32_t* s_pre = s_cnt + d.T;
+  __shared__ uint64_t s_warp[kFftThreads / 32];
+  const int t = blockIdx.y;
+  const Rect rc = tile_rect(t, d.ny, d.nx, d.ty, d.tx);
+  const int ya = rc.y0 + blockIdx.x * kFftRows, yb = min(rc.y1, ya + kFftRows);
+  const bool live = *(volatile int32_t*)&d.st->status == 0;
+  float best_a = -1.f, best_v = 0.f;
+  int best_i = 0x7fffffff;
+  if (live) {
+    for (int y = ya; y < yb; ++y)
+      for (int x = rc.x0 + threadIdx.x; x < rc.x1; x += kFftThreads) {
+        const int64_t gi = (int64_t)y * d.nx + x;
+        const float r = R0[gi] - S[(int64_t)y * pitch + x];
+        d.R[gi] = r;
+        R0[gi] = r;
+        const float a = fabsf(r);
+        if (a > best_a || (a == best_a && (int)gi < best_i)) {
+          best_a = a;
+          best_i = (int)gi;
+          best_v = r;
+        }
+      }
+  }
+  uint64_t k = best_a >= 0.f ? make_key(best_v, best_i) : 0ull;
+  k = warp_max_key(k);
+  if ((threadIdx.x & 31) == 0) s_warp[threadIdx.x >> 5] = k;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint64_t m = 0;
+    for (int w = 0; w < kFftThreads / 32; ++w) m = umax64(m, s_warp[w]);
+    if (m) atomicMax((unsigned long long*)&d.peak[(parity ^ 1) * d.T + t], (unsigned long long)m);
+  }
+  close_round_if_last(d, parity, blocks_x * d.T, s_cnt, s_pre, A, pitch);
+}
+
 }  // namespace
 
 cudaError_t launch_feedback(const PlanDev& d, const CUtensorMap* psf_map, int parity,
@@ -490,6 +592,36 @@ cudaError_t launch_feedback(const PlanDev& d, const CUtensorMap* psf_map, int pa
   const int bx = (maxW + kCols - 1) / kCols, by = (maxH + kRows - 1) / kRows;
   const size_t smem = sizeof(Comp4) * kChunk + sizeof(int32_t) * (2 * (size_t)d.T + 1);
   feedback_kernel<<<dim3(bx, by, d.T), kThreads, smem, s>>>(d, parity, apply, bx, by);
+  return cudaGetLastError();
+}
+
+
+cudaError_t fft_build_kernel_image(const PlanDev& d, int Ly, int Lx, float* Kimg,
+                                   cudaStream_t s) {
+  fft_kernel_image<<<4096, 256, 0, s>>>(d.P, d.pny, d.pnx, d.cy, d.cx, d.ny, d.nx, Ly, Lx, Kimg);
+  return cudaGetLastError();
+}
+
+cudaError_t fft_launch_scatter(const PlanDev& d, float* A, int64_t pitch, cudaStream_t s) {
+  fft_scatter<<<(d.T + 127) / 128, 128, 0, s>>>(d, A, pitch);
+  return cudaGetLastError();
+}
+
+cudaError_t fft_launch_multiply(void* X, const void* Kh, int64_t n, float scale,
+                                cudaStream_t s) {
+  fft_multiply<<<4096, 256, 0, s>>>(reinterpret_cast<float2*>(X),
+                                    reinterpret_cast<const float2*>(Kh), n, scale);
+  return cudaGetLastError();
+}
+
+cudaError_t fft_launch_subtract(const PlanDev& d, float* R0, const float* S, int64_t pitch,
+                                float* A, int parity, cudaStream_t s) {
+  int maxH = 0;
+  for (int i = 0; i < d.ty; ++i)
+    maxH = max(maxH, (int)(((int64_t)(i + 1) * d.ny) / d.ty - ((int64_t)i * d.ny) / d.ty));
+  const int bx = (maxH + kFftRows - 1) / kFftRows;
+  const size_t smem = sizeof(int32_t) * (2 * (size_t)d.T + 1);
+  fft_subtract<<<dim3(bx, d.T), kFftThreads, smem, s>>>(d, R0, S, pitch, A, parity, bx);
   return cudaGetLastError();
 }
 
