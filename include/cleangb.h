@@ -244,6 +244,44 @@ CLEAN_API int clean_hogbom_noalloc(const float* d_dirty, const float* d_psf, int
                                    float* d_model, clean_component* d_comps,
                                    int64_t* n_comps, void* stream);
 
+/* ---- Batches: many images deconvolved together ----------------------
+ * A batch holds n independent deconvolutions (each its own dirty image, PSF
+ * and clean_params, sizes and tile grids free) and runs all of them round by
+ * round in shared launches: one minor-loop launch per residual placement with
+ * one CTA per (image, tile), largest tiles first, and one feedback launch over
+ * every image's blocks.  The paper treats one image; batching changes only
+ * which CTA serves which tile, so each image's results are bit for bit those
+ * of its own clean_plan + clean_run (exact gather feedback; FFT feedback and
+ * the untiled mode are not accepted). */
+typedef struct clean_batch_s* clean_batch_t;
+
+/* Creates a batch of n images: params[i] as for clean_plan (checked before
+ * any CUDA call), d_psfs[i] device PSFs, BORROWED as in clean_plan.
+ * Allocates each image's state.  Synchronises.  CLEAN_OK,
+ * CLEAN_ERR_INVALID_ARG, CLEAN_ERR_NONFINITE, CLEAN_ERR_OOM, CLEAN_ERR_CUDA. */
+CLEAN_API int clean_batch_create(clean_batch_t* out, int32_t n, const clean_params* params,
+                                 const float* const* d_psfs, void* stream);
+
+/* Runs every image: d_dirties != NULL (host array of n device pointers)
+ * starts new runs from those dirty images; NULL continues.  At most
+ * max_rounds rounds (-1: until no tile of any image is active).  Images that
+ * finish early stop costing work.  Synchronises between batches of rounds. */
+CLEAN_API int clean_batch_run(clean_batch_t b, const float* const* d_dirties,
+                              int32_t max_rounds, void* stream);
+
+/* Image i's residual, model and component list, as clean_get. */
+CLEAN_API int clean_batch_get(clean_batch_t b, int32_t i, float* d_residual, float* d_model,
+                              clean_component* d_comps, int64_t comps_cap, int64_t* n_comps,
+                              void* stream);
+
+/* Rounds and kernels launched by the last runs, components over all images
+ * (as of the last status read).  Any output may be NULL. */
+CLEAN_API int clean_batch_stats(clean_batch_t b, int64_t* rounds_launched,
+                                int64_t* kernel_launches, int64_t* n_components);
+
+/* Frees the batch and its images' state (not the borrowed PSFs). */
+CLEAN_API void clean_batch_destroy(clean_batch_t b);
+
 /* Fills *out (host) with the plan's counters.  Synchronises. */
 CLEAN_API int clean_stats(clean_plan_t plan, clean_stats_t* out, void* stream);
 

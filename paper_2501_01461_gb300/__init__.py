@@ -19,7 +19,7 @@ import threading
 
 import numpy as np
 
-__all__ = ["CleanError", "Plan", "lib", "library_path", "build", "STATUS",
+__all__ = ["CleanError", "Plan", "Batch", "lib", "library_path", "build", "STATUS",
            "FB_GATHER", "FB_FFT", "FB_AUTO", "TILED", "UNTILED_GRID",
            "SYNC_AUTO", "SYNC_CLUSTER", "SYNC_GRID", "COMPONENT_DTYPE",
            "DEBUG_SPIN_LIMIT_NS", "DEBUG_FORCE_TIMEOUT", "DEBUG_TIMING", "DEBUG_FEEDBACK_PATH", "DEBUG_MINOR_PATH",
@@ -88,6 +88,11 @@ _SIGS = {
     "clean_debug_alloc_limit": (None, [_i64]),
     "clean_hogbom_noalloc": (ctypes.c_int, [_vp, _vp, _i32, _i32, _i32, _i32, _f32, _i64, _f32,
                                             _vp, _vp, _vp, _vp, _vp]),
+    "clean_batch_create": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp]),
+    "clean_batch_run": (ctypes.c_int, [_vp, _vp, _i32, _vp]),
+    "clean_batch_get": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp, _i64, _vp, _vp]),
+    "clean_batch_stats": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "clean_batch_destroy": (None, [_vp]),
 }
 EXPORTED_SYMBOLS = tuple(_SIGS)
 
@@ -303,3 +308,83 @@ class Plan:
 
     def debug_set(self, what: int, value: int):
         _check(lib().clean_debug_set(self._h, int(what), int(value)), "clean_debug_set")
+
+
+class Batch:
+    """Many images deconvolved together (clean_batch_*).
+
+    ``jobs`` is a list of dicts with keys psf (CUDA float32 tensor, borrowed),
+    ny, nx and any Plan keyword (gain, niter, threshold, tiles,
+    feedback_interval).
+    """
+
+    def __init__(self, jobs, stream=None):
+        self.n = len(jobs)
+        arr = (Params * self.n)()
+        self._psfs = []
+        ptrs = (ctypes.c_void_p * self.n)()
+        self.shapes = []
+        for i, j in enumerate(jobs):
+            j = dict(j)
+            psf = j.pop("psf")
+            ny, nx = j.pop("ny"), j.pop("nx")
+            arr[i] = make_params(ny, nx, tuple(psf.shape), **j)
+            ptrs[i] = _dptr(psf, what="psf").value
+            self._psfs.append(psf)
+            self.shapes.append((ny, nx))
+        self._params = arr
+        self._h = ctypes.c_void_p()
+        _check(lib().clean_batch_create(ctypes.byref(self._h), self.n, arr, ptrs,
+                                        _stream_ptr(stream)), "clean_batch_create")
+
+    def close(self):
+        if self._h:
+            lib().clean_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def run(self, dirties=None, max_rounds=-1, stream=None):
+        if dirties is None:
+            p = None
+        else:
+            ptrs = (ctypes.c_void_p * self.n)()
+            for i, d in enumerate(dirties):
+                ptrs[i] = _dptr(d, self.shapes[i], "dirty").value
+            p = ptrs
+        _check(lib().clean_batch_run(self._h, p, int(max_rounds), _stream_ptr(stream)),
+               "clean_batch_run")
+
+    def get(self, i, stream=None):
+        import torch
+        ny, nx = self.shapes[i]
+        n = ctypes.c_int64(0)
+        _check(lib().clean_batch_get(self._h, int(i), None, None, None, 0, ctypes.byref(n),
+                                     _stream_ptr(stream)), "clean_batch_get")
+        res = torch.empty((ny, nx), dtype=torch.float32, device="cuda")
+        mod = torch.empty_like(res)
+        comps = torch.empty((max(n.value, 1), 4), dtype=torch.int32, device="cuda")
+        _check(lib().clean_batch_get(self._h, int(i), _dptr(res), _dptr(mod),
+                                     ctypes.c_void_p(comps.data_ptr()), n.value, ctypes.byref(n),
+                                     _stream_ptr(stream)), "clean_batch_get")
+        host = comps[:n.value].cpu().numpy()
+        arr = np.empty(n.value, dtype=COMPONENT_DTYPE)
+        arr["y"], arr["x"], arr["tile"] = host[:, 0], host[:, 1], host[:, 3]
+        arr["flux"] = host[:, 2].view(np.float32)
+        return res, mod, arr
+
+    def stats(self):
+        r, k, c = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
+        _check(lib().clean_batch_stats(self._h, ctypes.byref(r), ctypes.byref(k), ctypes.byref(c)),
+               "clean_batch_stats")
+        return {"rounds_launched": r.value, "kernel_launches": k.value, "n_components": c.value}

@@ -349,6 +349,20 @@ int run_rounds(clean_plan_s* pl, int32_t max_rounds, cudaStream_t s) {
 
 }  // namespace
 
+namespace cleangb {
+
+PlanDev plan_device_state(const clean_plan_s* pl) { return pl->d; }
+
+bool plan_psf_tensor_map(const clean_plan_s* pl, CUtensorMap* out) {
+  if (!pl->psf_map_ok) return false;
+  *out = pl->psf_map;
+  return true;
+}
+
+int64_t plan_niter(const clean_plan_s* pl) { return pl->p.niter; }
+
+}  // namespace cleangb
+
 extern "C" {
 
 int clean_params_default(clean_params* p) {

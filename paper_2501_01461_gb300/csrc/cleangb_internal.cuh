@@ -101,6 +101,19 @@ struct PlanDev {
   DevState* st;
 };
 
+// A batched work item: tile `tile` of image `image`.
+struct BatchItem {
+  int32_t image;
+  int32_t tile;
+};
+
+// Per-image geometry of a batched feedback launch.
+struct BatchImage {
+  int32_t block0;    // first flattened block of this image
+  int32_t bx, by;    // blocks per tile in x and y
+  int32_t nblocks;   // bx * by * T
+};
+
 // Minor-loop launch configuration.
 struct MinorCfg {
   int32_t G;          // CTAs per tile
@@ -142,6 +155,17 @@ bool make_box_tensor_map(CUtensorMap* map, const float* base, int rows, int cols
 bool encode_tensor_map_2d(CUtensorMap* map, const float* base, int rows, int cols, int box_w,
                           int box_h);
 cudaError_t minor_prepare(const MinorCfg& c);  // sets function attributes
+// One CTA per item, each reading its image's plan state from `plans` (device
+// arrays); resident: the tile fits `smem` bytes of shared memory.
+cudaError_t launch_minor_batch(const PlanDev* plans, const BatchItem* items, int n_items,
+                               int resident, int smem, int parity, cudaStream_t s);
+// Feedback for many images in one launch (plain loads, or TMA when maps is
+// non-NULL: one PSF tensor map per image in device memory, 64-byte aligned).
+cudaError_t launch_feedback_batch(const PlanDev* plans, const BatchImage* imgs, int n_images,
+                                  int total_blocks, int max_T, const CUtensorMap* maps,
+                                  int parity, int apply, uint64_t limit_ns, cudaStream_t s);
+// Feedback block grid of one image (blocks per tile in x and y).
+void feedback_blocks(const PlanDev& d, bool tma, int* bx, int* by);
 int minor_max_cluster_ctas(int G, int resident, int smem, int threads);
 // psf_map: a 2-D tensor map of the PSF (box 68 x 64 floats) selects the TMA
 // kernel; NULL selects the plain-load kernel.
@@ -162,5 +186,10 @@ bool make_psf_tensor_map(CUtensorMap* map, const float* psf, int pny, int pnx);
 cudaError_t launch_restore_with(const PlanDev& d, float bmaj, float bmin, float bpa,
                                 float* beam_buf, int r, float* out, cudaStream_t s);
 int minor_threads();
+
+// Accessors the batch code uses on single-image plans (defined with the C ABI).
+PlanDev plan_device_state(const clean_plan_s* pl);
+bool plan_psf_tensor_map(const clean_plan_s* pl, CUtensorMap* out);
+int64_t plan_niter(const clean_plan_s* pl);
 
 }  // namespace cleangb

@@ -153,24 +153,34 @@ __device__ void close_round_if_last(const PlanDev& d, int parity, int total_bloc
   }
 }
 
-__global__ void __launch_bounds__(kThreads)
-    feedback_kernel(PlanDev d, int parity, int apply, int blocks_x, int blocks_y) {
+// Sum of the round's component counts over all tiles (0: the round changed
+// nothing, so the image's residual and peaks need no new pass).
+__device__ __forceinline__ int round_total(const PlanDev& d) {
+  int n = 0;
+  for (int s = 0; s < d.T; ++s) n += d.rcount[s];
+  return n;
+}
+
+// Block (bxi, byi) of tile t; blocks_x * blocks_y blocks per tile.
+__device__ __forceinline__ void feedback_body(const PlanDev& d, int parity, int apply, int t,
+                                              int bxi, int byi, int blocks_x, int blocks_y) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Comp4* s_comp = reinterpret_cast<Comp4*>(smem_raw);
   int32_t* s_cnt = reinterpret_cast<int32_t*>(s_comp + kChunk);
   int32_t* s_pre = s_cnt + d.T;  // [T + 1]
   __shared__ uint64_t s_warp[kWarps];
 
-  const int t = blockIdx.z;
   const Rect rc = tile_rect(t, d.ny, d.nx, d.ty, d.tx);
-  const int by0 = rc.y0 + blockIdx.y * kRows;
-  const int bx0 = rc.x0 + blockIdx.x * kCols;
-  const bool live = by0 < rc.y1 && bx0 < rc.x1 && *(volatile int32_t*)&d.st->status == 0;
+  const int by0 = rc.y0 + byi * kRows;
+  const int bx0 = rc.x0 + bxi * kCols;
+  const bool live = by0 < rc.y1 && bx0 < rc.x1 && *(volatile int32_t*)&d.st->status == 0 &&
+                    round_total(d) > 0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
   if (live) {
     // the other tiles' components of this round, in list order
-    for (int s = threadIdx.x; s < d.T; s += kThreads) s_cnt[s] = (s == t || !apply) ? 0 : d.rcount[s];
+    const bool fb = apply && d.K > 0 && d.T > 1;  // this image feeds back at all
+    for (int s = threadIdx.x; s < d.T; s += kThreads) s_cnt[s] = (s == t || !fb) ? 0 : d.rcount[s];
     block_prefix(s_cnt, s_pre, d.T);
     const int n_other = s_pre[d.T];
 
@@ -257,6 +267,11 @@ __global__ void __launch_bounds__(kThreads)
   close_round_if_last(d, parity, blocks_x * blocks_y * d.T, s_cnt, s_pre);
 }
 
+__global__ void __launch_bounds__(kThreads)
+    feedback_kernel(PlanDev d, int parity, int apply, int blocks_x, int blocks_y) {
+  feedback_body(d, parity, apply, blockIdx.z, blockIdx.x, blockIdx.y, blocks_x, blocks_y);
+}
+
 
 // ---------------------------------------------------------------------------
 // TMA variant.  The same arithmetic, with the PSF window of every component
@@ -308,9 +323,9 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, ui
   }
 }
 
-__global__ void __launch_bounds__(kThreads)
-    feedback_tma_kernel(PlanDev d, const __grid_constant__ CUtensorMap psf_map, int parity,
-                        int apply, int blocks_x, int blocks_y, uint64_t limit_ns) {
+__device__ __forceinline__ void feedback_tma_body(const PlanDev& d, const CUtensorMap* psf_map,
+                                                  int parity, int apply, int t, int bxi, int byi,
+                                                  int blocks_x, int blocks_y, uint64_t limit_ns) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
@@ -323,11 +338,11 @@ __global__ void __launch_bounds__(kThreads)
   __shared__ uint64_t s_warp[kConsumerWarps];
   __shared__ int s_abort;
 
-  const int t = blockIdx.z;
   const Rect rc = tile_rect(t, d.ny, d.nx, d.ty, d.tx);
-  const int by0 = rc.y0 + blockIdx.y * kRows;
-  const int bx0 = rc.x0 + blockIdx.x * kCols;
-  const bool live = by0 < rc.y1 && bx0 < rc.x1 && *(volatile int32_t*)&d.st->status == 0;
+  const int by0 = rc.y0 + byi * kRows;
+  const int bx0 = rc.x0 + bxi * kCols;
+  const bool live = by0 < rc.y1 && bx0 < rc.x1 && *(volatile int32_t*)&d.st->status == 0 &&
+                    round_total(d) > 0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const bool producer = warp == kConsumerWarps;
 
@@ -340,9 +355,9 @@ __global__ void __launch_bounds__(kThreads)
       }
       ptx::fence_barrier_init();
     }
-    if (producer && lane == 0) ptx::prefetch_tensormap(&psf_map);
+    if (producer && lane == 0) ptx::prefetch_tensormap(psf_map);
     for (int s = threadIdx.x; s < d.T; s += kThreads)
-      s_cnt[s] = (s == t || !apply) ? 0 : d.rcount[s];
+      s_cnt[s] = (s == t || !(apply && d.K > 0 && d.T > 1)) ? 0 : d.rcount[s];
     block_prefix(s_cnt, s_pre, d.T);  // also orders the barrier set-up
     const int n_other = s_pre[d.T];
 
@@ -387,7 +402,7 @@ __global__ void __launch_bounds__(kThreads)
                                &s_abort, &d.st->status))
               break;
             ptx::mbar_arrive_expect_tx(&full_bar[st], kStageBytes);
-            ptx::tma_load_2d(s_win + (size_t)st * kStageFloats, &psf_map, s_list[jj].x,
+            ptx::tma_load_2d(s_win + (size_t)st * kStageFloats, psf_map, s_list[jj].x,
                              s_list[jj].y, &full_bar[st]);
             ++issued;
           }
@@ -470,7 +485,57 @@ __global__ void __launch_bounds__(kThreads)
   close_round_if_last(d, parity, blocks_x * blocks_y * d.T, s_cnt, s_pre);
 }
 
+__global__ void __launch_bounds__(kThreads)
+    feedback_tma_kernel(PlanDev d, const __grid_constant__ CUtensorMap psf_map, int parity,
+                        int apply, int blocks_x, int blocks_y, uint64_t limit_ns) {
+  feedback_tma_body(d, &psf_map, parity, apply, blockIdx.z, blockIdx.x, blockIdx.y, blocks_x,
+                    blocks_y, limit_ns);
+}
+
 }  // namespace tma
+
+// ---------------------------------------------------------------------------
+// Batched feedback: the blocks of many images in one flattened grid; block
+// b belongs to the image whose [block0, block0 + nblocks) range holds it.
+// Each image closes its own round (its own last block).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int batch_image(const BatchImage* imgs, int n, int b) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (imgs[mid].block0 <= b)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(kThreads)
+    feedback_batch_kernel(const PlanDev* __restrict__ plans, const BatchImage* __restrict__ imgs,
+                          int n_images, int parity, int apply) {
+  const int i = batch_image(imgs, n_images, blockIdx.x);
+  const BatchImage im = imgs[i];
+  const PlanDev d = plans[i];
+  const int local = blockIdx.x - im.block0;
+  const int per_tile = im.bx * im.by;
+  const int t = local / per_tile, rem = local - t * per_tile;
+  feedback_body(d, parity, apply, t, rem % im.bx, rem / im.bx, im.bx, im.by);
+}
+
+__global__ void __launch_bounds__(tma::kThreads)
+    feedback_tma_batch_kernel(const PlanDev* __restrict__ plans,
+                              const BatchImage* __restrict__ imgs, const CUtensorMap* maps,
+                              int n_images, int parity, int apply, uint64_t limit_ns) {
+  const int i = batch_image(imgs, n_images, blockIdx.x);
+  const BatchImage im = imgs[i];
+  const PlanDev d = plans[i];
+  const int local = blockIdx.x - im.block0;
+  const int per_tile = im.bx * im.by;
+  const int t = local / per_tile, rem = local - t * per_tile;
+  tma::feedback_tma_body(d, maps + i, parity, apply, t, rem % im.bx, rem / im.bx, im.bx, im.by,
+                         limit_ns);
+}
 
 
 // ---------------------------------------------------------------------------
@@ -622,6 +687,40 @@ cudaError_t fft_launch_subtract(const PlanDev& d, float* R0, const float* S, int
   const int bx = (maxH + kFftRows - 1) / kFftRows;
   const size_t smem = sizeof(int32_t) * (2 * (size_t)d.T + 1);
   fft_subtract<<<dim3(bx, d.T), kFftThreads, smem, s>>>(d, R0, S, pitch, A, parity, bx);
+  return cudaGetLastError();
+}
+
+void feedback_blocks(const PlanDev& d, bool use_tma, int* bx, int* by) {
+  int maxH = 0, maxW = 0;
+  for (int i = 0; i < d.ty; ++i)
+    maxH = max(maxH, (int)(((int64_t)(i + 1) * d.ny) / d.ty - ((int64_t)i * d.ny) / d.ty));
+  for (int j = 0; j < d.tx; ++j)
+    maxW = max(maxW, (int)(((int64_t)(j + 1) * d.nx) / d.tx - ((int64_t)j * d.nx) / d.tx));
+  const int kc = use_tma ? tma::kCols : kCols, kr = use_tma ? tma::kRows : kRows;
+  *bx = (maxW + kc - 1) / kc;
+  *by = (maxH + kr - 1) / kr;
+}
+
+cudaError_t launch_feedback_batch(const PlanDev* plans, const BatchImage* imgs, int n_images,
+                                  int total_blocks, int max_T, const CUtensorMap* maps,
+                                  int parity, int apply, uint64_t limit_ns, cudaStream_t s) {
+  if (n_images <= 0 || total_blocks <= 0) return cudaSuccess;
+  if (maps) {
+    const size_t smem = tma::smem_bytes(max_T);
+    cudaError_t e = cudaFuncSetAttribute(feedback_tma_batch_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    feedback_tma_batch_kernel<<<total_blocks, tma::kThreads, smem, s>>>(plans, imgs, maps,
+                                                                         n_images, parity, apply,
+                                                                         limit_ns);
+  } else {
+    const size_t smem = sizeof(Comp4) * kChunk + sizeof(int32_t) * (2 * (size_t)max_T + 1);
+    cudaError_t e = cudaFuncSetAttribute(feedback_batch_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    feedback_batch_kernel<<<total_blocks, kThreads, smem, s>>>(plans, imgs, n_images, parity,
+                                                               apply);
+  }
   return cudaGetLastError();
 }
 

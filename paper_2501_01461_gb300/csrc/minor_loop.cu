@@ -28,6 +28,7 @@ namespace {
 
 constexpr int kThreads = 1024;
 constexpr int kUnroll = 8;
+constexpr int kSyncNone = 3;  // one CTA per tile (batched launches)
 
 __device__ __forceinline__ uint64_t umax64(uint64_t a, uint64_t b) {
   return a > b ? a : b;
@@ -169,7 +170,9 @@ __device__ __forceinline__ uint64_t exchange_keys(const PlanDev& d, const MinorC
                                                   int* s_abort) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int G = c.G;
-  if (SYNC == CLEAN_SYNC_CLUSTER) {
+  if (SYNC == kSyncNone) {
+    if (threadIdx.x == 0) *s_best = mine;  // one CTA per tile: nothing to exchange
+  } else if (SYNC == CLEAN_SYNC_CLUSTER) {
     if (threadIdx.x == 0) s_part[k & 1] = mine;
     cluster_sync_all();
     if (warp == 0) {
@@ -211,9 +214,10 @@ __device__ __forceinline__ uint64_t exchange_keys(const PlanDev& d, const MinorC
   return *s_best;
 }
 
+// One tile group member: CTA `rank` of the G serving tile t.
 template <int SYNC, bool RES>
-__global__ void __launch_bounds__(kThreads, 1)
-    minor_kernel(PlanDev d, MinorCfg c, int parity) {
+__device__ __forceinline__ void minor_body(const PlanDev& d, const MinorCfg& c, int parity,
+                                           int t, int rank) {
   extern __shared__ __align__(16) float sR[];
   __shared__ uint64_t s_warp[32];
   __shared__ uint64_t s_part[2];
@@ -221,8 +225,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ int s_abort;
 
   const int G = c.G;
-  const int t = blockIdx.x / G;
-  const int rank = (SYNC == CLEAN_SYNC_CLUSTER) ? (int)cluster_rank() : (int)(blockIdx.x % G);
   const Rect rc = tile_rect(t, d.ny, d.nx, d.ty, d.tx);
   const int H = rc.y1 - rc.y0;
   const int ya = rc.y0 + (int)(((int64_t)rank * H) / G);
@@ -294,6 +296,25 @@ __global__ void __launch_bounds__(kThreads, 1)
     d.rcount[t] = (int32_t)k;
     d.budget[t] = budget - k;
   }
+}
+
+template <int SYNC, bool RES>
+__global__ void __launch_bounds__(kThreads, 1)
+    minor_kernel(PlanDev d, MinorCfg c, int parity) {
+  const int t = blockIdx.x / c.G;
+  const int rank = (SYNC == CLEAN_SYNC_CLUSTER) ? (int)cluster_rank() : (int)(blockIdx.x % c.G);
+  minor_body<SYNC, RES>(d, c, parity, t, rank);
+}
+
+// Batched launch: one CTA per (image, tile) item, each image's plan state in
+// `plans`.  Tiles are independent within a round, so no CTA waits on another.
+template <bool RES>
+__global__ void __launch_bounds__(kThreads, 1)
+    minor_batch_kernel(const PlanDev* __restrict__ plans, const BatchItem* __restrict__ items,
+                       MinorCfg c, int parity) {
+  const BatchItem it = items[blockIdx.x];
+  const PlanDev d = plans[it.image];
+  minor_body<kSyncNone, RES>(d, c, parity, it.tile, 0);
 }
 
 
@@ -621,6 +642,26 @@ void* pick(const MinorCfg& c) {
 }
 
 }  // namespace
+
+cudaError_t launch_minor_batch(const PlanDev* plans, const BatchItem* items, int n_items,
+                               int resident, int smem, int parity, cudaStream_t s) {
+  if (n_items <= 0) return cudaSuccess;
+  MinorCfg c{};
+  c.G = 1;
+  c.sync = kSyncNone;
+  c.resident = resident;
+  c.smem = smem;
+  c.threads = kThreads;
+  c.spin_limit_ns = 2000000000ll;
+  const void* fn = resident ? (const void*)minor_batch_kernel<true> : (const void*)minor_batch_kernel<false>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  if (resident)
+    minor_batch_kernel<true><<<n_items, kThreads, smem, s>>>(plans, items, c, parity);
+  else
+    minor_batch_kernel<false><<<n_items, kThreads, 0, s>>>(plans, items, c, parity);
+  return cudaGetLastError();
+}
 
 cudaError_t minor_prepare(const MinorCfg& c) {
   const void* fn = pick(c);

@@ -1,0 +1,91 @@
+"""Batched deconvolution: many images of uneven sizes in shared launches.
+
+Each image's component list, residual and model must equal its own solo run
+(clean_plan + clean_run) bit for bit -- batching only changes which CTA
+serves which tile -- and the small ones must equal the CPU oracle.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2501_01461_gb300 as cg
+import synth
+from gpu_helpers import assert_bit_exact, gpu_clean
+
+pytestmark = pytest.mark.gpu
+
+JOBS = [
+    # (n, tiles, K, niter, threshold, freq_scale)
+    (128, (2, 2), 10, 400, 0.0, 1.0),      # tiles resident in shared memory
+    (250, (4, 4), 7, 900, 1e-3, 1.3),      # ragged tiles
+    (512, (2, 2), 20, 600, 0.0, 1.6),      # streamed tiles
+    (96, (3, 2), 0, 300, 0.0, 1.1),        # no feedback (independent tiles)
+    (1024, (4, 4), 50, 1600, 5e-3, 2.0),   # larger, with a threshold
+    (200, (1, 1), 25, 500, 0.0, 1.8),      # a single tile
+]
+
+
+def _job(n, fs, seed):
+    rng = np.random.default_rng(seed)
+    psf = synth.make_psf(2 * n, 2 * n, freq_scale=fs)
+    ys, xs, fl = synth.make_sky(n, 10, 0.05, 2.1, rng)
+    dirty = synth.make_dirty(psf, n, ys, xs, fl, 1e-3, rng)
+    return psf, dirty
+
+
+def test_batch_equals_solo_runs():
+    import torch
+    data = [_job(n, fs, 100 + i) for i, (n, tiles, K, niter, thr, fs) in enumerate(JOBS)]
+    d_psfs = [torch.from_numpy(p).cuda() for p, _ in data]
+    d_dirties = [torch.from_numpy(d).cuda() for _, d in data]
+    jobs = [dict(psf=d_psfs[i], ny=n, nx=n, gain=0.1, niter=niter, threshold=thr, tiles=tiles,
+                 feedback_interval=K) for i, (n, tiles, K, niter, thr, fs) in enumerate(JOBS)]
+    with cg.Batch(jobs) as b:
+        for rep in range(2):          # a second run must start clean
+            b.run(d_dirties)
+            for i, (n, tiles, K, niter, thr, fs) in enumerate(JOBS):
+                res, mod, comps = b.get(i)
+                solo = gpu_clean(data[i][1], data[i][0], 0.1, niter, thr, tiles, K)
+                assert len(comps) == solo["n"], (i, rep)
+                assert np.array_equal(comps["y"], solo["comps"]["y"])
+                assert np.array_equal(comps["x"], solo["comps"]["x"])
+                assert np.array_equal(comps["flux"].view(np.uint32),
+                                      solo["comps"]["flux"].view(np.uint32))
+                assert np.array_equal(res.cpu().numpy().view(np.uint32),
+                                      solo["residual"].view(np.uint32)), (i, rep)
+                assert np.array_equal(mod.cpu().numpy().view(np.uint32),
+                                      solo["model"].view(np.uint32)), (i, rep)
+        st = b.stats()
+        assert st["n_components"] == sum(len(b.get(i)[2]) for i in range(len(JOBS)))
+
+
+def test_batch_small_images_equal_oracle_and_resume():
+    import torch
+    picks = [0, 1, 3]
+    data = [_job(JOBS[i][0], JOBS[i][5], 200 + i) for i in picks]
+    jobs = []
+    for (psf, dirty), i in zip(data, picks):
+        n, tiles, K, niter, thr, fs = JOBS[i]
+        jobs.append(dict(psf=torch.from_numpy(psf).cuda(), ny=n, nx=n, gain=0.1, niter=niter,
+                         threshold=thr, tiles=tiles, feedback_interval=K))
+    dirties = [torch.from_numpy(d).cuda() for _, d in data]
+    with cg.Batch(jobs) as b:
+        b.run(dirties, max_rounds=2)   # stop early, then continue
+        b.run(None)
+        for k, ((psf, dirty), i) in enumerate(zip(data, picks)):
+            n, tiles, K, niter, thr, fs = JOBS[i]
+            o = oracle.clean_f32(dirty, psf, 0.1, niter, thr, tiles, K)
+            res, mod, comps = b.get(k)
+            assert len(comps) == o.n
+            assert np.array_equal(comps["flux"].view(np.uint32), o.comps["flux"].view(np.uint32))
+            assert np.array_equal(res.cpu().numpy().view(np.uint32), o.residual.view(np.uint32))
+            assert np.array_equal(mod.cpu().numpy().view(np.uint32), o.model.view(np.uint32))
+
+
+def test_batch_rejects_fft_and_untiled():
+    import torch
+    psf = torch.from_numpy(synth.make_psf(128, 128)).cuda()
+    with pytest.raises(cg.CleanError):
+        cg.Batch([dict(psf=psf, ny=64, nx=64, niter=10, feedback_mode=cg.FB_FFT)])
+    with pytest.raises(cg.CleanError):
+        cg.Batch([dict(psf=psf, ny=64, nx=64, niter=10, mode=cg.UNTILED_GRID)])
