@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fft", action="store_true", help="skip the FFT-feedback comparison run")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched 64-image leg")
     ap.add_argument("--untiled-iters", type=int, default=2000,
                     help="iterations of the untiled whole-GPU comparison run (0: skip)")
     ap.add_argument("--profile", type=int, default=0, metavar="R",
@@ -196,6 +197,56 @@ def ncu_traffic() -> dict:
             if h == r.get("sha256_16"):
                 out[name] = r["bytes_per_launch"]
     return out
+
+
+def batch_leg(cg, torch, stream, n_images=64):
+    """64 images of uneven sizes (512..2048, per-channel PSFs): one batch vs
+    the same images one at a time, tiled (same results, bit for bit) and
+    plain untiled CLEAN on the whole GPU."""
+    jobs = synth.batch_jobs(n_images)
+    psfs = [torch.from_numpy(j["psf"]).cuda() for j in jobs]
+    dirties = [torch.from_numpy(j["dirty"]).cuda() for j in jobs]
+    total_iters = sum(j["niter"] for j in jobs)
+    spec = [dict(psf=psfs[i], ny=j["n"], nx=j["n"], gain=j["gain"], niter=j["niter"],
+                 threshold=0.0, tiles=j["tiles"], feedback_interval=j["K"])
+            for i, j in enumerate(jobs)]
+
+    def timed(fn, reps=2):
+        fn()
+        torch.cuda.synchronize()
+        best = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            best.append(a.elapsed_time(b))
+        return sum(best) / len(best)
+
+    with cg.Batch(spec) as bt:
+        ms_batch = timed(lambda: bt.run(dirties))
+        st = bt.stats()
+    solo = [cg.Plan(psfs[i], j["n"], j["n"], gain=j["gain"], niter=j["niter"], threshold=0.0,
+                    tiles=j["tiles"], feedback_interval=j["K"]) for i, j in enumerate(jobs)]
+    ms_solo = timed(lambda: [p.run(dirties[i]) for i, p in enumerate(solo)])
+    for p in solo:
+        p.close()
+    plain = [cg.Plan(psfs[i], j["n"], j["n"], gain=j["gain"], niter=j["niter"], threshold=0.0,
+                     mode=cg.UNTILED_GRID) for i, j in enumerate(jobs)]
+    ms_plain = timed(lambda: [p.run(dirties[i]) for i, p in enumerate(plain)], reps=1)
+    for p in plain:
+        p.close()
+    sides = [j["n"] for j in jobs]
+    return {"workload": f"{n_images} images, sides {sorted(set(sides))} (counts "
+                        f"{[sides.count(v) for v in sorted(set(sides))]}), PSF 2N, freq scale 1-2, "
+                        "2x2 tiles up to 1024 else 4x4, K 50, 2000 iterations each",
+            "iters_per_s": total_iters / (ms_batch / 1e3), "ms_per_step": ms_batch,
+            "one_at_a_time_tiled_iters_per_s": total_iters / (ms_solo / 1e3),
+            "one_at_a_time_plain_iters_per_s": total_iters / (ms_plain / 1e3),
+            "vs_one_at_a_time_tiled": ms_solo / ms_batch,
+            "vs_one_at_a_time_plain": ms_plain / ms_batch,
+            "rounds": st["rounds_launched"], "kernel_launches": st["kernel_launches"]}
 
 
 def cpu_baseline(w, data):
@@ -434,6 +485,11 @@ def main():
                        "residual within 1e-4 Jy of the float64 replay, not bit-exact"}
         fp.close()
 
+    # ---- batched: many uneven images together vs one at a time ----
+    batched = None
+    if not args.no_batch:
+        batched = batch_leg(cg, torch, stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(w, data)
@@ -456,6 +512,7 @@ def main():
             "cpu_baseline": cpu, "e2e": e2e, "untiled_gpu": untiled,
             "vs_untiled_gpu": (value / untiled["iters_per_s"]) if untiled else None,
             "fft_feedback": fft,
+            "batched": batched,
             "gpu_launches": int(gpu_launches),
             "clocks": clocks, "wall_s_timed": wall,
             "plan": {k: st[k] for k in ("group_ctas", "group_sync", "resident", "sm_count")},

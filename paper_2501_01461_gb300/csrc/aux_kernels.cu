@@ -171,8 +171,7 @@ cudaError_t launch_restore_with(const PlanDev& d, float bmaj, float bmin, float 
   if (e != cudaSuccess) return e;
   const int side = kRB + 2 * r;
   const size_t smem = sizeof(float) * ((size_t)side * side + (size_t)(2 * r + 1) * (2 * r + 1));
-  e = cudaFuncSetAttribute(restore_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem);
+  e = allow_max_smem((const void*)restore_kernel);
   if (e != cudaSuccess) return e;
   dim3 grid((d.nx + kRB - 1) / kRB, (d.ny + kRB - 1) / kRB, 1);
   restore_kernel<<<grid, kRB * 8, smem, s>>>(d, beam_buf, r, out);

@@ -140,6 +140,23 @@ struct MinorCfg {
 bool minor_pipe_geometry(MinorCfg& c, int max_rows, int max_w, int chunk_px = 0,
                          int max_stages = 0);
 
+// Raises a kernel's dynamic shared-memory cap to the device's opt-in maximum.
+// The cap is process-wide state of the kernel, so every plan sets the same
+// value (setting a plan's own size would break launches of plans that need
+// more); each launch still requests only its own size.
+inline cudaError_t allow_max_smem(const void* fn) {
+  int dev = 0, optin = 0;
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, fn);  // static shared memory counts too
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - (int)fa.sharedSizeBytes);
+  return e;
+}
+
 // Launchers (return cudaError_t of the launch).
 cudaError_t launch_init(const PlanDev& d, const float* dirty, int64_t niter,
                         cudaStream_t s);

@@ -707,16 +707,14 @@ cudaError_t launch_feedback_batch(const PlanDev* plans, const BatchImage* imgs, 
   if (n_images <= 0 || total_blocks <= 0) return cudaSuccess;
   if (maps) {
     const size_t smem = tma::smem_bytes(max_T);
-    cudaError_t e = cudaFuncSetAttribute(feedback_tma_batch_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_max_smem((const void*)feedback_tma_batch_kernel);
     if (e != cudaSuccess) return e;
     feedback_tma_batch_kernel<<<total_blocks, tma::kThreads, smem, s>>>(plans, imgs, maps,
                                                                          n_images, parity, apply,
                                                                          limit_ns);
   } else {
     const size_t smem = sizeof(Comp4) * kChunk + sizeof(int32_t) * (2 * (size_t)max_T + 1);
-    cudaError_t e = cudaFuncSetAttribute(feedback_batch_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_max_smem((const void*)feedback_batch_kernel);
     if (e != cudaSuccess) return e;
     feedback_batch_kernel<<<total_blocks, kThreads, smem, s>>>(plans, imgs, n_images, parity,
                                                                apply);
@@ -725,14 +723,12 @@ cudaError_t launch_feedback_batch(const PlanDev* plans, const BatchImage* imgs, 
 }
 
 cudaError_t feedback_prepare(int T) {
-  cudaError_t e = cudaFuncSetAttribute(feedback_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)(sizeof(Comp4) * kChunk +
-                                             sizeof(int32_t) * (2 * (size_t)T + 1)));
+  (void)T;
+  cudaError_t e = allow_max_smem((const void*)feedback_kernel);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(tma::feedback_tma_kernel,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)tma::smem_bytes(T));
+  e = allow_max_smem((const void*)tma::feedback_tma_kernel);
+  if (e != cudaSuccess) return e;
+  return allow_max_smem((const void*)fft_subtract);
 }
 
 

@@ -654,7 +654,7 @@ cudaError_t launch_minor_batch(const PlanDev* plans, const BatchItem* items, int
   c.threads = kThreads;
   c.spin_limit_ns = 2000000000ll;
   const void* fn = resident ? (const void*)minor_batch_kernel<true> : (const void*)minor_batch_kernel<false>;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = allow_max_smem(fn);
   if (e != cudaSuccess) return e;
   if (resident)
     minor_batch_kernel<true><<<n_items, kThreads, smem, s>>>(plans, items, c, parity);
@@ -665,8 +665,7 @@ cudaError_t launch_minor_batch(const PlanDev* plans, const BatchItem* items, int
 
 cudaError_t minor_prepare(const MinorCfg& c) {
   const void* fn = pick(c);
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       c.smem);
+  cudaError_t e = allow_max_smem(fn);
   if (e != cudaSuccess) return e;
   if (c.sync == CLEAN_SYNC_CLUSTER && c.G > 8) {
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);

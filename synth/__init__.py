@@ -95,7 +95,8 @@ def make_psf(py: int, px: int, freq_scale: float = 1.0,
     ok = (iu >= 0) & (iu < px) & (iv >= 0) & (iv < py)
     grid = np.zeros((py, px), dtype=np.float64)
     np.add.at(grid, (iv[ok], iu[ok]), 1.0)
-    img = np.fft.fftshift(np.fft.ifft2(np.fft.ifftshift(grid)).real)
+    import scipy.fft as sfft
+    img = np.fft.fftshift(sfft.ifft2(np.fft.ifftshift(grid), workers=-1).real)
     cy, cx = py // 2, px // 2
     img /= img[cy, cx]
     psf = img.astype(np.float32)
@@ -279,3 +280,23 @@ def tie_image(ny: int, nx: int, rng, levels: int = 3) -> np.ndarray:
     """Integer-valued signed image with many equal |values| (tie-heavy)."""
     rng = np.random.default_rng(rng) if not isinstance(rng, np.random.Generator) else rng
     return rng.integers(-levels, levels + 1, size=(ny, nx)).astype(np.float32)
+
+
+def batch_jobs(n_images: int = 64, seed: int = 1003, niter: int = 2000, n_sources: int = 40):
+    """Uneven multi-channel batch: sides drawn uniformly from {512, 1024, 1536,
+    2048}, per-channel PSFs from the same array with frequency scaling
+    linspace(1, 2, n_images), 2 x 2 tiles up to 1024 and 4 x 4 above, K = 50,
+    gain 0.1, threshold 0.  Returns a list of dicts (n, psf, dirty, tiles, K,
+    niter, gain)."""
+    rng = np.random.default_rng(seed)
+    sides = rng.choice([512, 1024, 1536, 2048], size=n_images)
+    freqs = np.linspace(1.0, 2.0, n_images)
+    jobs = []
+    for i in range(n_images):
+        n = int(sides[i])
+        psf = make_psf(2 * n, 2 * n, freq_scale=float(freqs[i]))
+        ys, xs, fl = make_sky(n, n_sources, 0.01, 2.1, rng)
+        dirty = make_dirty(psf, n, ys, xs, fl, 1e-3, rng)
+        jobs.append(dict(n=n, psf=psf, dirty=dirty, tiles=(2, 2) if n <= 1024 else (4, 4),
+                         K=50, niter=niter, gain=0.1))
+    return jobs

@@ -252,3 +252,26 @@ def test_feedback_paths_bit_exact(case):
         g = gpu_clean(dirty, psf, 0.1, niter, 0.0, tiles, K, feedback_path=path)
         assert g["stats"]["feedback_tma"] == (1 if path == 2 else 0)
         assert_bit_exact(g, o, f"{case} path={path}")
+
+
+def test_plans_with_different_shared_memory_coexist():
+    """A plan created later with a smaller shared-memory need must not break
+    launches of an earlier plan that needs more (kernel attributes are
+    process-wide)."""
+    import torch
+    dirty, psf = _inputs(200, 256, (400, 512), "sky", 12)
+    big_ref = oracle.clean_f32(dirty, psf, 0.1, 300, 0.0, (1, 1), 10)
+    d_psf, d_dirty = torch.from_numpy(psf).cuda(), torch.from_numpy(dirty).cuda()
+    big = cg.Plan(d_psf, 200, 256, gain=0.1, niter=300, tiles=(1, 1), feedback_interval=10,
+                  group_ctas=1, group_sync=cg.SYNC_CLUSTER)
+    # about 200 KB of shared memory either way: a resident slab, or the ring of
+    # the pipelined kernel
+    small_dirty, small_psf = _inputs(32, 32, (64, 64), "rand", 13)
+    small = cg.Plan(torch.from_numpy(small_psf).cuda(), 32, 32, niter=50, tiles=(2, 2),
+                    feedback_interval=3)
+    small.run(torch.from_numpy(small_dirty).cuda())
+    big.run(d_dirty)
+    r, m, _ = big.get()
+    assert np.array_equal(r.cpu().numpy().view(np.uint32), big_ref.residual.view(np.uint32))
+    big.close()
+    small.close()
