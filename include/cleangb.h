@@ -282,6 +282,47 @@ CLEAN_API int clean_batch_stats(clean_batch_t b, int64_t* rounds_launched,
 /* Frees the batch and its images' state (not the borrowed PSFs). */
 CLEAN_API void clean_batch_destroy(clean_batch_t b);
 
+/* ---- Serving: continuous batching ------------------------------------
+ * A server keeps many deconvolution jobs resident on the device and runs
+ * them together round by round (the batch machinery above); jobs are added
+ * and removed between steps, so a job that arrives while others run starts
+ * at the next step and overlaps with them.  Each job's results equal its own
+ * clean_plan + clean_run bit for bit, alone or in any mix.  Admission policy
+ * (which queued job to add, under which memory budget) belongs to the
+ * caller; clean_server_add fails with CLEAN_ERR_OOM when its slots or the
+ * device memory run out. */
+typedef struct clean_server_s* clean_server_t;
+
+/* A server with room for max_jobs resident jobs. */
+CLEAN_API int clean_server_create(clean_server_t* out, int32_t max_jobs, void* stream);
+
+/* Adds a job: params as for clean_plan (tiled, gather feedback), d_psf
+ * BORROWED until clean_server_remove, d_dirty read by this call's set-up
+ * (stream-ordered) only.  Allocates the job's state and synchronises (PSF
+ * check).  *job_id identifies it from then on. */
+CLEAN_API int clean_server_add(clean_server_t sv, const clean_params* params, const float* d_psf,
+                               const float* d_dirty, int64_t* job_id, void* stream);
+
+/* Runs `rounds` rounds of every unfinished job, then reads their status;
+ * *n_running (may be NULL) receives how many jobs still have work.
+ * Synchronises. */
+CLEAN_API int clean_server_step(clean_server_t sv, int32_t rounds, int32_t* n_running,
+                                void* stream);
+
+/* Ids of finished jobs not yet removed (up to cap; *n_done the count). */
+CLEAN_API int clean_server_done(clean_server_t sv, int64_t* ids, int32_t cap, int32_t* n_done);
+
+/* A job's residual, model and component list, as clean_get. */
+CLEAN_API int clean_server_get(clean_server_t sv, int64_t job_id, float* d_residual,
+                               float* d_model, clean_component* d_comps, int64_t comps_cap,
+                               int64_t* n_comps, void* stream);
+
+/* Frees a job's state (finished or not); synchronises the device. */
+CLEAN_API int clean_server_remove(clean_server_t sv, int64_t job_id);
+
+/* Frees the server and every job still in it. */
+CLEAN_API void clean_server_destroy(clean_server_t sv);
+
 /* Fills *out (host) with the plan's counters.  Synchronises. */
 CLEAN_API int clean_stats(clean_plan_t plan, clean_stats_t* out, void* stream);
 

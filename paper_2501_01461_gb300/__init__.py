@@ -93,6 +93,13 @@ _SIGS = {
     "clean_batch_get": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp, _i64, _vp, _vp]),
     "clean_batch_stats": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "clean_batch_destroy": (None, [_vp]),
+    "clean_server_create": (ctypes.c_int, [_vp, _i32, _vp]),
+    "clean_server_add": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "clean_server_step": (ctypes.c_int, [_vp, _i32, _vp, _vp]),
+    "clean_server_done": (ctypes.c_int, [_vp, _vp, _i32, _vp]),
+    "clean_server_get": (ctypes.c_int, [_vp, ctypes.c_int64, _vp, _vp, _vp, _i64, _vp, _vp]),
+    "clean_server_remove": (ctypes.c_int, [_vp, ctypes.c_int64]),
+    "clean_server_destroy": (None, [_vp]),
 }
 EXPORTED_SYMBOLS = tuple(_SIGS)
 

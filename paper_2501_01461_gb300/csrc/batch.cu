@@ -1,10 +1,14 @@
-// Batched tiled CLEAN: many dirty images of uneven sizes deconvolved
-// together, every round of every image in the same launches (one minor-loop
-// launch per residual placement and one feedback launch), so small images
-// fill the GPU together instead of one after another.  Each image's
-// arithmetic is exactly that of its own plan (clean_plan + clean_run): the
-// batch only changes which CTA serves which tile, so each image's results
-// are identical to its solo run.
+// Many deconvolutions on one GPU at once: fixed batches (clean_batch_*) and
+// continuous batching for serving (clean_server_*).
+//
+// Every resident image's round runs in shared launches: minor-loop launches
+// grouped by CTAs per tile and residual placement (one CTA per small tile,
+// a thread-block cluster of up to 16 CTAs per large one, largest tiles
+// first), then one feedback launch over every image's blocks.  Each image
+// keeps its own round phase (it may have joined later), its own budgets,
+// peaks and component list, so its results are bit for bit those of its own
+// clean_plan + clean_run.  Images that finish leave the work lists; new ones
+// join between rounds.
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -15,62 +19,352 @@
 using namespace cleangb;
 
 namespace {
-constexpr int64_t kBatchResidentMax = 200 * 1024;  // one CTA's tile in shared memory
-}
 
-struct clean_batch_s {
-  int device = 0;
-  int n = 0;
-  std::vector<clean_plan_t> plans;
-  std::vector<PlanDev> dev;        // host copies of the images' plan state
-  PlanDev* d_plans = nullptr;      // device array of PlanDev
-  BatchItem* d_items = nullptr;    // resident items then streamed items
-  int n_res = 0, n_str = 0, res_smem = 0;
-  BatchImage* d_imgs = nullptr;
-  int total_blocks = 0, max_T = 1;
-  CUtensorMap* d_maps = nullptr;   // one PSF tensor map per image (TMA feedback)
+constexpr int64_t kGroupSmemMax = 200 * 1024;  // resident rows per CTA
+
+struct Job {
+  clean_plan_t plan = nullptr;
+  PlanDev dev{};
+  CUtensorMap map{};
   bool tma = false;
-  DevState* d_states = nullptr;    // contiguous control blocks of all images
-  DevState* h_states = nullptr;    // pinned mirror
-  int parity = 0;
-  bool started = false;
+  int64_t id = 0;
+  int slot = 0;
+  bool finished = false;
+};
+
+struct Group {
+  int offset = 0, count = 0;  // into the item array
+  int G = 1, resident = 0, smem = 0;
+};
+
+}  // namespace
+
+// Shared engine behind both APIs.
+struct clean_engine_s {
+  int device = 0;
+  int cap = 0;                          // state slots
+  std::vector<Job> jobs;                // resident jobs (finished ones until removed)
+  std::vector<int> free_slots;
+  DevState* d_states = nullptr;         // [cap] control blocks
+  DevState* h_states = nullptr;         // pinned mirror
+  PlanDev* d_plans = nullptr;           // [cap] device copies, indexed by work position
+  BatchItem* d_items = nullptr;
+  int items_cap = 0;
+  BatchImage* d_imgs = nullptr;         // [cap] feedback geometry (TMA images first)
+  CUtensorMap* d_maps = nullptr;        // [cap]
+  std::vector<Group> groups;
+  int n_work = 0, n_tma = 0, blocks_tma = 0, blocks_plain = 0, max_T = 1;
+  bool dirty = true;                    // work lists need a rebuild
+  int round = 0;                        // rounds launched so far (global)
+  int64_t next_id = 1;
   int poisoned = CLEAN_OK;
   int64_t rounds_launched = 0, kernel_launches = 0;
 };
 
 namespace {
 
-int batch_fail(clean_batch_s* b, int code) {
+int eng_fail(clean_engine_s* e, int code) {
   cudaGetLastError();
-  if (b->poisoned == CLEAN_OK) b->poisoned = code;
-  return b->poisoned;
+  if (e->poisoned == CLEAN_OK) e->poisoned = code;
+  return e->poisoned;
 }
 
-int read_states(clean_batch_s* b, cudaStream_t s) {
-  cudaError_t e = cudaMemcpyAsync(b->h_states, b->d_states, sizeof(DevState) * b->n,
-                                  cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return batch_fail(b, CLEAN_ERR_CUDA);
-  for (int i = 0; i < b->n; ++i)
-    if (b->h_states[i].status & ST_TIMEOUT) return batch_fail(b, CLEAN_ERR_TIMEOUT);
+void engine_free(clean_engine_s* e) {
+  if (!e) return;
+  cudaDeviceSynchronize();
+  for (Job& j : e->jobs) clean_destroy(j.plan);
+  cudaFree(e->d_states);
+  cudaFree(e->d_plans);
+  cudaFree(e->d_items);
+  cudaFree(e->d_imgs);
+  cudaFree(e->d_maps);
+  if (e->h_states) cudaFreeHost(e->h_states);
+  cudaGetLastError();
+  delete e;
+}
+
+int engine_create(clean_engine_s** out, int cap) {
+  clean_engine_s* e = new (std::nothrow) clean_engine_s();
+  if (!e) return CLEAN_ERR_OOM;
+  e->cap = cap;
+  cudaGetDevice(&e->device);
+  if (cudaMalloc(&e->d_states, sizeof(DevState) * cap) != cudaSuccess ||
+      cudaMallocHost(&e->h_states, sizeof(DevState) * cap) != cudaSuccess ||
+      cudaMalloc(&e->d_plans, sizeof(PlanDev) * cap) != cudaSuccess ||
+      cudaMalloc(&e->d_imgs, sizeof(BatchImage) * cap) != cudaSuccess ||
+      cudaMalloc(&e->d_maps, sizeof(CUtensorMap) * cap) != cudaSuccess) {
+    engine_free(e);
+    return CLEAN_ERR_OOM;
+  }
+  std::memset(e->h_states, 0, sizeof(DevState) * cap);
+  for (int i = cap - 1; i >= 0; --i) e->free_slots.push_back(i);
+  *out = e;
+  return CLEAN_OK;
+}
+
+// Starts (or restarts) a job's run from a dirty image: control block and
+// peaks cleared, set-up kernel on `s`; the job's rounds count from now.
+int engine_start(clean_engine_s* e, Job& j, const float* d_dirty, cudaStream_t s) {
+  j.dev.round0 = e->round;
+  j.finished = false;
+  cudaError_t err = cudaMemsetAsync(j.dev.st, 0, sizeof(DevState), s);
+  if (err == cudaSuccess) err = cudaMemsetAsync(j.dev.peak, 0, sizeof(uint64_t) * 2 * j.dev.T, s);
+  if (err == cudaSuccess) err = launch_init(j.dev, d_dirty, plan_niter(j.plan), s);
+  ++e->kernel_launches;
+  if (err != cudaSuccess) return eng_fail(e, CLEAN_ERR_CUDA);
+  std::memset(&e->h_states[j.slot], 0, sizeof(DevState));
+  e->h_states[j.slot].active = 1;  // refreshed at the next status read
+  e->dirty = true;
+  return CLEAN_OK;
+}
+
+// Creates a job's plan (its device state) in a free slot.
+int engine_register(clean_engine_s* e, const clean_params* p, const float* d_psf, Job** out,
+                    cudaStream_t s) {
+  if (e->free_slots.empty()) return CLEAN_ERR_OOM;
+  int rc = clean_params_check(p);
+  if (rc != CLEAN_OK) return rc;
+  if (!d_psf || p->mode != CLEAN_TILED || p->feedback_mode == CLEAN_FB_FFT)
+    return CLEAN_ERR_INVALID_ARG;
+  clean_params q = *p;
+  q.feedback_mode = CLEAN_FB_GATHER;
+  Job j;
+  rc = clean_plan(&j.plan, &q, d_psf, s);
+  if (rc != CLEAN_OK) return rc;
+  j.slot = e->free_slots.back();
+  e->free_slots.pop_back();
+  j.dev = plan_device_state(j.plan);
+  j.dev.st = e->d_states + j.slot;
+  j.tma = plan_psf_tensor_map(j.plan, &j.map);
+  j.id = e->next_id++;
+  j.finished = true;  // not running until started
+  e->jobs.push_back(j);
+  *out = &e->jobs.back();
+  return CLEAN_OK;
+}
+
+// CTAs per tile for a tile of h x w pixels: the fewest (a power of two up to
+// 16) whose row slabs fit in shared memory; 16 streamed CTAs if none does.
+void tile_group(int h, int w, int* G, int* resident, int* smem) {
+  for (int g = 1; g <= 16; g *= 2) {
+    const int64_t slab = (int64_t)((h + g - 1) / g) * w * 4;
+    if (slab <= kGroupSmemMax) {
+      *G = g;
+      *resident = 1;
+      *smem = (int)slab;
+      return;
+    }
+  }
+  *G = 16;
+  *resident = 0;
+  *smem = 0;
+}
+
+// Rebuilds the device work lists from the unfinished jobs.
+int engine_rebuild(clean_engine_s* e, cudaStream_t s) {
+  std::vector<int> work;
+  for (int i = 0; i < (int)e->jobs.size(); ++i)
+    if (!e->jobs[i].finished) work.push_back(i);
+  // TMA-fed images first, so each feedback launch covers a contiguous range
+  std::stable_partition(work.begin(), work.end(), [&](int i) { return e->jobs[i].tma; });
+  e->n_work = (int)work.size();
+  e->n_tma = 0;
+  e->max_T = 1;
+  std::vector<PlanDev> plans;
+  std::vector<CUtensorMap> maps;
+  std::vector<BatchImage> imgs;
+  struct Sized {
+    int64_t px;
+    int G, resident, smem;
+    BatchItem it;
+  };
+  std::vector<Sized> all;
+  int block0 = 0;
+  e->blocks_tma = e->blocks_plain = 0;
+  for (int w = 0; w < (int)work.size(); ++w) {
+    const Job& j = e->jobs[work[w]];
+    plans.push_back(j.dev);
+    maps.push_back(j.map);
+    if (j.tma) ++e->n_tma;
+    e->max_T = std::max(e->max_T, j.dev.T);
+    for (int t = 0; t < j.dev.T; ++t) {
+      const Rect r = tile_rect(t, j.dev.ny, j.dev.nx, j.dev.ty, j.dev.tx);
+      Sized z;
+      z.px = (int64_t)(r.y1 - r.y0) * (r.x1 - r.x0);
+      tile_group(r.y1 - r.y0, r.x1 - r.x0, &z.G, &z.resident, &z.smem);
+      z.it = BatchItem{w, t};
+      all.push_back(z);
+    }
+    int bx = 0, by = 0;
+    feedback_blocks(j.dev, j.tma, &bx, &by);
+    if (!j.tma && w == e->n_tma) block0 = 0;  // plain images restart the block count
+    BatchImage im;
+    im.block0 = block0;
+    im.bx = bx;
+    im.by = by;
+    im.nblocks = bx * by * j.dev.T;
+    block0 += im.nblocks;
+    imgs.push_back(im);
+    (j.tma ? e->blocks_tma : e->blocks_plain) += im.nblocks;
+  }
+  // groups of equal (G, resident), biggest tiles first within each
+  std::stable_sort(all.begin(), all.end(), [](const Sized& a, const Sized& b) {
+    if (a.G != b.G) return a.G > b.G;
+    if (a.resident != b.resident) return a.resident < b.resident;
+    return a.px > b.px;
+  });
+  e->groups.clear();
+  std::vector<BatchItem> items;
+  for (size_t k = 0; k < all.size(); ++k) {
+    if (e->groups.empty() || e->groups.back().G != all[k].G ||
+        e->groups.back().resident != all[k].resident) {
+      Group g;
+      g.offset = (int)items.size();
+      g.G = all[k].G;
+      g.resident = all[k].resident;
+      e->groups.push_back(g);
+    }
+    Group& g = e->groups.back();
+    g.smem = std::max(g.smem, all[k].smem);
+    ++g.count;
+    items.push_back(all[k].it);
+  }
+  // a cluster size the device cannot schedule falls back to smaller groups
+  for (Group& g : e->groups)
+    if (g.G > 1) {
+      const int ok = minor_batch_cluster(g.G, g.resident, g.smem);
+      if (ok != g.G) return CLEAN_ERR_UNSUPPORTED;
+    }
+  if ((int)items.size() > e->items_cap) {
+    cudaFree(e->d_items);
+    e->items_cap = std::max<int>((int)items.size(), 2 * e->items_cap);
+    if (cudaMalloc(&e->d_items, sizeof(BatchItem) * e->items_cap) != cudaSuccess)
+      return eng_fail(e, CLEAN_ERR_OOM);
+  }
+  cudaError_t err = cudaSuccess;
+  if (!plans.empty()) {
+    err = cudaMemcpyAsync(e->d_plans, plans.data(), sizeof(PlanDev) * plans.size(),
+                          cudaMemcpyHostToDevice, s);
+    if (err == cudaSuccess)
+      err = cudaMemcpyAsync(e->d_maps, maps.data(), sizeof(CUtensorMap) * maps.size(),
+                            cudaMemcpyHostToDevice, s);
+    if (err == cudaSuccess)
+      err = cudaMemcpyAsync(e->d_imgs, imgs.data(), sizeof(BatchImage) * imgs.size(),
+                            cudaMemcpyHostToDevice, s);
+  }
+  if (err == cudaSuccess && !items.empty())
+    err = cudaMemcpyAsync(e->d_items, items.data(), sizeof(BatchItem) * items.size(),
+                          cudaMemcpyHostToDevice, s);
+  // the host vectors die here: make the copies complete first
+  if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+  if (err != cudaSuccess) return eng_fail(e, CLEAN_ERR_CUDA);
+  e->dirty = false;
+  return CLEAN_OK;
+}
+
+int engine_read(clean_engine_s* e, cudaStream_t s) {
+  cudaError_t err = cudaMemcpyAsync(e->h_states, e->d_states, sizeof(DevState) * e->cap,
+                                    cudaMemcpyDeviceToHost, s);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+  if (err != cudaSuccess) return eng_fail(e, CLEAN_ERR_CUDA);
+  for (const Job& j : e->jobs)
+    if (e->h_states[j.slot].status & ST_TIMEOUT) return eng_fail(e, CLEAN_ERR_TIMEOUT);
+  return CLEAN_OK;
+}
+
+// Marks jobs whose runs are over; returns how many are still running.
+int engine_mark(clean_engine_s* e) {
+  int running = 0;
+  for (Job& j : e->jobs) {
+    if (j.finished) continue;
+    const DevState& st = e->h_states[j.slot];
+    if (!st.active || (st.status & ST_NONFINITE_DIRTY)) {
+      j.finished = true;
+      e->dirty = true;
+    } else {
+      ++running;
+    }
+  }
+  return running;
+}
+
+// Launches `rounds` rounds of every unfinished job.
+int engine_rounds(clean_engine_s* e, int64_t rounds, cudaStream_t s) {
+  int rc;
+  if (e->dirty && (rc = engine_rebuild(e, s)) != CLEAN_OK) return rc;
+  if (e->n_work == 0) return CLEAN_OK;
+  for (int64_t r = 0; r < rounds; ++r) {
+    cudaError_t err = cudaSuccess;
+    for (const Group& g : e->groups) {
+      err = launch_minor_batch(e->d_plans, e->d_items + g.offset, g.count, g.G, g.resident,
+                               g.smem, e->round, s);
+      ++e->kernel_launches;
+      if (err != cudaSuccess) break;
+    }
+    if (err == cudaSuccess && e->blocks_tma > 0) {
+      err = launch_feedback_batch(e->d_plans, e->d_imgs, e->n_tma, e->blocks_tma, e->max_T,
+                                  e->d_maps, e->round, 1, 2000000000ull, s);
+      ++e->kernel_launches;
+    }
+    if (err == cudaSuccess && e->blocks_plain > 0) {
+      err = launch_feedback_batch(e->d_plans + e->n_tma, e->d_imgs + e->n_tma,
+                                  e->n_work - e->n_tma, e->blocks_plain, e->max_T, nullptr,
+                                  e->round, 1, 2000000000ull, s);
+      ++e->kernel_launches;
+    }
+    if (err != cudaSuccess) return eng_fail(e, CLEAN_ERR_CUDA);
+    ++e->round;
+    ++e->rounds_launched;
+  }
+  return CLEAN_OK;
+}
+
+Job* engine_find(clean_engine_s* e, int64_t id) {
+  for (Job& j : e->jobs)
+    if (j.id == id) return &j;
+  return nullptr;
+}
+
+int engine_get(clean_engine_s* e, const Job& j, float* d_residual, float* d_model,
+               clean_component* d_comps, int64_t comps_cap, int64_t* n_comps, cudaStream_t s) {
+  const size_t img = sizeof(float) * (size_t)j.dev.ny * j.dev.nx;
+  cudaError_t err = cudaSuccess;
+  if (d_residual) err = cudaMemcpyAsync(d_residual, j.dev.R, img, cudaMemcpyDeviceToDevice, s);
+  if (err == cudaSuccess && d_model)
+    err = cudaMemcpyAsync(d_model, j.dev.model, img, cudaMemcpyDeviceToDevice, s);
+  if (err != cudaSuccess) return eng_fail(e, CLEAN_ERR_CUDA);
+  if (d_comps || n_comps) {
+    DevState st;
+    err = cudaMemcpyAsync(&st, j.dev.st, sizeof(DevState), cudaMemcpyDeviceToHost, s);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+    if (err != cudaSuccess) return eng_fail(e, CLEAN_ERR_CUDA);
+    if (n_comps) *n_comps = st.total;
+    const int64_t m = std::min(st.total, comps_cap);
+    if (d_comps && m > 0) {
+      err = cudaMemcpyAsync(d_comps, j.dev.list, sizeof(clean_component) * (size_t)m,
+                            cudaMemcpyDeviceToDevice, s);
+      if (err != cudaSuccess) return eng_fail(e, CLEAN_ERR_CUDA);
+    }
+  }
   return CLEAN_OK;
 }
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// Fixed batches
+// ---------------------------------------------------------------------------
+struct clean_batch_s {
+  clean_engine_s* eng = nullptr;
+  std::vector<int64_t> ids;  // job i of the batch is eng->jobs[i]
+  bool started = false;
+};
+
 extern "C" {
 
 void clean_batch_destroy(clean_batch_t b) {
   if (!b) return;
-  cudaDeviceSynchronize();
-  for (clean_plan_t p : b->plans) clean_destroy(p);
-  cudaFree(b->d_plans);
-  cudaFree(b->d_items);
-  cudaFree(b->d_imgs);
-  cudaFree(b->d_maps);
-  cudaFree(b->d_states);
-  if (b->h_states) cudaFreeHost(b->h_states);
-  cudaGetLastError();
+  engine_free(b->eng);
   delete b;
 }
 
@@ -87,94 +381,20 @@ int clean_batch_create(clean_batch_t* out, int32_t n, const clean_params* params
   }
   clean_batch_s* b = new (std::nothrow) clean_batch_s();
   if (!b) return CLEAN_ERR_OOM;
-  b->n = n;
-  cudaGetDevice(&b->device);
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int rc = engine_create(&b->eng, n);
+  if (rc != CLEAN_OK) {
+    delete b;
+    return rc;
+  }
+  b->eng->jobs.reserve(n);  // Job pointers stay valid while registering
   for (int i = 0; i < n; ++i) {
-    clean_params p = params[i];
-    p.feedback_mode = CLEAN_FB_GATHER;
-    clean_plan_t pl = nullptr;
-    const int rc = clean_plan(&pl, &p, d_psfs[i], stream);
+    Job* j = nullptr;
+    rc = engine_register(b->eng, &params[i], d_psfs[i], &j, reinterpret_cast<cudaStream_t>(stream));
     if (rc != CLEAN_OK) {
       clean_batch_destroy(b);
       return rc;
     }
-    b->plans.push_back(pl);
-  }
-  // contiguous control blocks, read back with one copy per batch of rounds
-  if (cudaMalloc(&b->d_states, sizeof(DevState) * n) != cudaSuccess ||
-      cudaMallocHost(&b->h_states, sizeof(DevState) * n) != cudaSuccess) {
-    clean_batch_destroy(b);
-    return CLEAN_ERR_OOM;
-  }
-  b->tma = true;
-  std::vector<BatchItem> res, str;
-  std::vector<std::pair<int64_t, BatchItem>> res_sized, str_sized;
-  std::vector<BatchImage> imgs(n);
-  std::vector<CUtensorMap> maps(n);
-  int block0 = 0;
-  for (int i = 0; i < n; ++i) {
-    PlanDev d = plan_device_state(b->plans[i]);
-    d.st = b->d_states + i;
-    b->dev.push_back(d);
-    b->tma = b->tma && plan_psf_tensor_map(b->plans[i], &maps[i]);
-    b->max_T = std::max(b->max_T, d.T);
-    for (int t = 0; t < d.T; ++t) {
-      const Rect r = tile_rect(t, d.ny, d.nx, d.ty, d.tx);
-      const int64_t bytes = (int64_t)(r.y1 - r.y0) * (r.x1 - r.x0) * 4;
-      const BatchItem it{i, t};
-      if (bytes <= kBatchResidentMax) {
-        res_sized.push_back({bytes, it});
-        b->res_smem = (int)std::max<int64_t>(b->res_smem, bytes);
-      } else {
-        str_sized.push_back({bytes, it});
-      }
-    }
-  }
-  // largest tiles first, so the last wave is made of the short ones
-  auto by_size = [](const std::pair<int64_t, BatchItem>& a, const std::pair<int64_t, BatchItem>& c) {
-    return a.first > c.first;
-  };
-  std::stable_sort(res_sized.begin(), res_sized.end(), by_size);
-  std::stable_sort(str_sized.begin(), str_sized.end(), by_size);
-  for (auto& x : res_sized) res.push_back(x.second);
-  for (auto& x : str_sized) str.push_back(x.second);
-  b->n_res = (int)res.size();
-  b->n_str = (int)str.size();
-  for (int i = 0; i < n; ++i) {
-    int bx = 0, by = 0;
-    feedback_blocks(b->dev[i], b->tma, &bx, &by);
-    imgs[i].block0 = block0;
-    imgs[i].bx = bx;
-    imgs[i].by = by;
-    imgs[i].nblocks = bx * by * b->dev[i].T;
-    block0 += imgs[i].nblocks;
-  }
-  b->total_blocks = block0;
-  std::vector<BatchItem> items = res;
-  items.insert(items.end(), str.begin(), str.end());
-  if (cudaMalloc(&b->d_plans, sizeof(PlanDev) * n) != cudaSuccess ||
-      cudaMalloc(&b->d_items, sizeof(BatchItem) * std::max<size_t>(items.size(), 1)) != cudaSuccess ||
-      cudaMalloc(&b->d_imgs, sizeof(BatchImage) * n) != cudaSuccess ||
-      cudaMalloc(&b->d_maps, sizeof(CUtensorMap) * n) != cudaSuccess) {
-    clean_batch_destroy(b);
-    return CLEAN_ERR_OOM;
-  }
-  cudaError_t e = cudaMemcpyAsync(b->d_plans, b->dev.data(), sizeof(PlanDev) * n,
-                                  cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess && !items.empty())
-    e = cudaMemcpyAsync(b->d_items, items.data(), sizeof(BatchItem) * items.size(),
-                        cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(b->d_imgs, imgs.data(), sizeof(BatchImage) * n, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess && b->tma)
-    e = cudaMemcpyAsync(b->d_maps, maps.data(), sizeof(CUtensorMap) * n, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_states, 0, sizeof(DevState) * n, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    clean_batch_destroy(b);
-    return CLEAN_ERR_CUDA;
+    b->ids.push_back(j->id);
   }
   *out = b;
   return CLEAN_OK;
@@ -183,101 +403,154 @@ int clean_batch_create(clean_batch_t* out, int32_t n, const clean_params* params
 int clean_batch_run(clean_batch_t b, const float* const* d_dirties, int32_t max_rounds,
                     void* stream) {
   if (!b) return CLEAN_ERR_INVALID_ARG;
-  if (b->poisoned != CLEAN_OK) return b->poisoned;
+  clean_engine_s* e = b->eng;
+  if (e->poisoned != CLEAN_OK) return e->poisoned;
   if (max_rounds < -1) return CLEAN_ERR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int rc;
   if (d_dirties) {
-    for (int i = 0; i < b->n; ++i)
+    for (size_t i = 0; i < b->ids.size(); ++i)
       if (!d_dirties[i]) return CLEAN_ERR_INVALID_ARG;
-    cudaError_t e = cudaMemsetAsync(b->d_states, 0, sizeof(DevState) * b->n, s);
-    for (int i = 0; i < b->n && e == cudaSuccess; ++i) {
-      const PlanDev& d = b->dev[i];
-      e = cudaMemsetAsync(d.peak, 0, sizeof(uint64_t) * 2 * d.T, s);
-      if (e == cudaSuccess) e = launch_init(d, d_dirties[i], plan_niter(b->plans[i]), s);
-      ++b->kernel_launches;
-    }
-    if (e != cudaSuccess) return batch_fail(b, CLEAN_ERR_CUDA);
-    b->parity = 0;
-    b->rounds_launched = 0;
+    // new runs, every image starting at the same round
+    for (size_t i = 0; i < b->ids.size(); ++i)
+      if ((rc = engine_start(e, e->jobs[i], d_dirties[i], s)) != CLEAN_OK) return rc;
     b->started = true;
   } else if (!b->started) {
     return CLEAN_ERR_INVALID_ARG;
   }
-  int rc = read_states(b, s);
-  if (rc != CLEAN_OK) return rc;
-  for (int i = 0; i < b->n; ++i)
-    if (b->h_states[i].status & ST_NONFINITE_DIRTY) {
+  if ((rc = engine_read(e, s)) != CLEAN_OK) return rc;
+  for (const Job& j : e->jobs)
+    if (e->h_states[j.slot].status & ST_NONFINITE_DIRTY) {
       b->started = false;
       return CLEAN_ERR_NONFINITE;
     }
   int64_t done = 0;
   while (max_rounds < 0 || done < max_rounds) {
-    int64_t chunk = 0;
-    for (int i = 0; i < b->n; ++i) {
-      if (!b->h_states[i].active) continue;
-      const int K = b->dev[i].K;
-      const int64_t need = K > 0 ? (b->h_states[i].max_budget + K - 1) / K : 1;
-      chunk = std::max<int64_t>(chunk, std::max<int64_t>(need, 1));
+    if (engine_mark(e) == 0) break;
+    int64_t chunk = 1;
+    for (const Job& j : e->jobs) {
+      if (j.finished) continue;
+      const int K = j.dev.K;
+      const int64_t need = K > 0 ? (e->h_states[j.slot].max_budget + K - 1) / K : 1;
+      chunk = std::max<int64_t>(chunk, need);
     }
-    if (chunk == 0) break;
     if (max_rounds >= 0) chunk = std::min<int64_t>(chunk, max_rounds - done);
-    for (int64_t r = 0; r < chunk; ++r) {
-      cudaError_t e = launch_minor_batch(b->d_plans, b->d_items, b->n_res, 1, b->res_smem,
-                                         b->parity, s);
-      if (e == cudaSuccess)
-        e = launch_minor_batch(b->d_plans, b->d_items + b->n_res, b->n_str, 0, 0, b->parity, s);
-      if (e == cudaSuccess)
-        e = launch_feedback_batch(b->d_plans, b->d_imgs, b->n, b->total_blocks, b->max_T,
-                                  b->tma ? b->d_maps : nullptr, b->parity, 1, 2000000000ull, s);
-      b->kernel_launches += 3;
-      if (e != cudaSuccess) return batch_fail(b, CLEAN_ERR_CUDA);
-      b->parity ^= 1;
-      ++b->rounds_launched;
-    }
+    if ((rc = engine_rounds(e, chunk, s)) != CLEAN_OK) return rc;
     done += chunk;
-    if ((rc = read_states(b, s)) != CLEAN_OK) return rc;
+    if ((rc = engine_read(e, s)) != CLEAN_OK) return rc;
   }
   return CLEAN_OK;
 }
 
 int clean_batch_get(clean_batch_t b, int32_t i, float* d_residual, float* d_model,
                     clean_component* d_comps, int64_t comps_cap, int64_t* n_comps, void* stream) {
-  if (!b || i < 0 || i >= b->n) return CLEAN_ERR_INVALID_ARG;
-  if (b->poisoned != CLEAN_OK) return b->poisoned;
-  if (!b->started) return CLEAN_ERR_INVALID_ARG;
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  const PlanDev& d = b->dev[i];
-  const size_t img = sizeof(float) * (size_t)d.ny * d.nx;
-  cudaError_t e = cudaSuccess;
-  if (d_residual) e = cudaMemcpyAsync(d_residual, d.R, img, cudaMemcpyDeviceToDevice, s);
-  if (e == cudaSuccess && d_model) e = cudaMemcpyAsync(d_model, d.model, img, cudaMemcpyDeviceToDevice, s);
-  if (e != cudaSuccess) return batch_fail(b, CLEAN_ERR_CUDA);
-  if (d_comps || n_comps) {
-    const int rc = read_states(b, s);
-    if (rc != CLEAN_OK) return rc;
-    const int64_t total = b->h_states[i].total;
-    if (n_comps) *n_comps = total;
-    const int64_t m = std::min(total, comps_cap);
-    if (d_comps && m > 0) {
-      e = cudaMemcpyAsync(d_comps, d.list, sizeof(clean_component) * (size_t)m,
-                          cudaMemcpyDeviceToDevice, s);
-      if (e != cudaSuccess) return batch_fail(b, CLEAN_ERR_CUDA);
-    }
-  }
-  return CLEAN_OK;
+  if (!b || i < 0 || i >= (int32_t)b->ids.size()) return CLEAN_ERR_INVALID_ARG;
+  clean_engine_s* e = b->eng;
+  if (e->poisoned != CLEAN_OK) return e->poisoned;
+  Job* j = engine_find(e, b->ids[i]);
+  if (!j) return CLEAN_ERR_INVALID_ARG;
+  return engine_get(e, *j, d_residual, d_model, d_comps, comps_cap, n_comps,
+                    reinterpret_cast<cudaStream_t>(stream));
 }
 
 int clean_batch_stats(clean_batch_t b, int64_t* rounds_launched, int64_t* kernel_launches,
                       int64_t* n_components) {
   if (!b) return CLEAN_ERR_INVALID_ARG;
-  if (rounds_launched) *rounds_launched = b->rounds_launched;
-  if (kernel_launches) *kernel_launches = b->kernel_launches;
+  clean_engine_s* e = b->eng;
+  if (rounds_launched) *rounds_launched = e->rounds_launched;
+  if (kernel_launches) *kernel_launches = e->kernel_launches;
   if (n_components) {
     int64_t t = 0;
-    for (int i = 0; i < b->n; ++i) t += b->h_states[i].total;
+    for (const Job& j : e->jobs) t += e->h_states[j.slot].total;
     *n_components = t;
   }
   return CLEAN_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Continuous batching
+// ---------------------------------------------------------------------------
+int clean_server_create(clean_server_t* out, int32_t max_jobs, void* stream) {
+  (void)stream;
+  if (!out || max_jobs < 1 || max_jobs > (1 << 16)) return CLEAN_ERR_INVALID_ARG;
+  *out = nullptr;
+  clean_engine_s* e = nullptr;
+  const int rc = engine_create(&e, max_jobs);
+  if (rc != CLEAN_OK) return rc;
+  *out = reinterpret_cast<clean_server_t>(e);
+  return CLEAN_OK;
+}
+
+void clean_server_destroy(clean_server_t sv) { engine_free(reinterpret_cast<clean_engine_s*>(sv)); }
+
+int clean_server_add(clean_server_t sv, const clean_params* p, const float* d_psf,
+                     const float* d_dirty, int64_t* job_id, void* stream) {
+  clean_engine_s* e = reinterpret_cast<clean_engine_s*>(sv);
+  if (!e || !p || !d_dirty) return CLEAN_ERR_INVALID_ARG;
+  if (e->poisoned != CLEAN_OK) return e->poisoned;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  Job* j = nullptr;
+  int rc = engine_register(e, p, d_psf, &j, s);
+  if (rc != CLEAN_OK) return rc;
+  if ((rc = engine_start(e, *j, d_dirty, s)) != CLEAN_OK) return rc;
+  if (job_id) *job_id = j->id;
+  return CLEAN_OK;
+}
+
+int clean_server_step(clean_server_t sv, int32_t rounds, int32_t* n_running, void* stream) {
+  clean_engine_s* e = reinterpret_cast<clean_engine_s*>(sv);
+  if (!e || rounds < 0) return CLEAN_ERR_INVALID_ARG;
+  if (e->poisoned != CLEAN_OK) return e->poisoned;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int rc = engine_read(e, s);
+  if (rc != CLEAN_OK) return rc;
+  if (engine_mark(e) > 0 && rounds > 0) {
+    if ((rc = engine_rounds(e, rounds, s)) != CLEAN_OK) return rc;
+    if ((rc = engine_read(e, s)) != CLEAN_OK) return rc;
+  }
+  const int running = engine_mark(e);
+  if (n_running) *n_running = running;
+  return CLEAN_OK;
+}
+
+int clean_server_done(clean_server_t sv, int64_t* ids, int32_t cap, int32_t* n_done) {
+  clean_engine_s* e = reinterpret_cast<clean_engine_s*>(sv);
+  if (!e || (cap > 0 && !ids)) return CLEAN_ERR_INVALID_ARG;
+  int n = 0;
+  for (const Job& j : e->jobs)
+    if (j.finished) {
+      if (n < cap) ids[n] = j.id;
+      ++n;
+    }
+  if (n_done) *n_done = n;
+  return CLEAN_OK;
+}
+
+int clean_server_get(clean_server_t sv, int64_t job_id, float* d_residual, float* d_model,
+                     clean_component* d_comps, int64_t comps_cap, int64_t* n_comps,
+                     void* stream) {
+  clean_engine_s* e = reinterpret_cast<clean_engine_s*>(sv);
+  if (!e) return CLEAN_ERR_INVALID_ARG;
+  if (e->poisoned != CLEAN_OK) return e->poisoned;
+  Job* j = engine_find(e, job_id);
+  if (!j) return CLEAN_ERR_INVALID_ARG;
+  return engine_get(e, *j, d_residual, d_model, d_comps, comps_cap, n_comps,
+                    reinterpret_cast<cudaStream_t>(stream));
+}
+
+int clean_server_remove(clean_server_t sv, int64_t job_id) {
+  clean_engine_s* e = reinterpret_cast<clean_engine_s*>(sv);
+  if (!e) return CLEAN_ERR_INVALID_ARG;
+  for (size_t k = 0; k < e->jobs.size(); ++k)
+    if (e->jobs[k].id == job_id) {
+      cudaDeviceSynchronize();
+      clean_destroy(e->jobs[k].plan);
+      e->free_slots.push_back(e->jobs[k].slot);
+      e->jobs.erase(e->jobs.begin() + (long)k);
+      e->dirty = true;
+      return CLEAN_OK;
+    }
+  return CLEAN_ERR_INVALID_ARG;
 }
 
 }  // extern "C"

@@ -90,6 +90,7 @@ struct PlanDev {
   float gain, thr;
   int32_t K;                // feedback interval (0 = none)
   int32_t cap_round;        // per-tile capacity of the round buffer
+  int32_t round0;           // batched runs: the batch round at which this image started
   int64_t* budget;          // [T] remaining iterations per tile
   uint64_t* peak;           // [2][T] peak key per tile, indexed by round parity
   int32_t* rcount;          // [T] components of the current round per tile
@@ -172,15 +173,19 @@ bool make_box_tensor_map(CUtensorMap* map, const float* base, int rows, int cols
 bool encode_tensor_map_2d(CUtensorMap* map, const float* base, int rows, int cols, int box_w,
                           int box_h);
 cudaError_t minor_prepare(const MinorCfg& c);  // sets function attributes
-// One CTA per item, each reading its image's plan state from `plans` (device
-// arrays); resident: the tile fits `smem` bytes of shared memory.
+// G CTAs per item (G = 1: independent CTAs; G > 1: one thread-block cluster
+// per item), each reading its image's plan state from `plans` (device
+// arrays); resident: each CTA's rows fit `smem` bytes of shared memory.
+// Image i runs its round (round - plans[i].round0).
 cudaError_t launch_minor_batch(const PlanDev* plans, const BatchItem* items, int n_items,
-                               int resident, int smem, int parity, cudaStream_t s);
+                               int G, int resident, int smem, int round, cudaStream_t s);
+// Largest cluster size <= want that can be scheduled for the batched kernel.
+int minor_batch_cluster(int want, int resident, int smem);
 // Feedback for many images in one launch (plain loads, or TMA when maps is
 // non-NULL: one PSF tensor map per image in device memory, 64-byte aligned).
 cudaError_t launch_feedback_batch(const PlanDev* plans, const BatchImage* imgs, int n_images,
                                   int total_blocks, int max_T, const CUtensorMap* maps,
-                                  int parity, int apply, uint64_t limit_ns, cudaStream_t s);
+                                  int round, int apply, uint64_t limit_ns, cudaStream_t s);
 // Feedback block grid of one image (blocks per tile in x and y).
 void feedback_blocks(const PlanDev& d, bool tma, int* bx, int* by);
 int minor_max_cluster_ctas(int G, int resident, int smem, int threads);

@@ -513,28 +513,28 @@ __device__ __forceinline__ int batch_image(const BatchImage* imgs, int n, int b)
 
 __global__ void __launch_bounds__(kThreads)
     feedback_batch_kernel(const PlanDev* __restrict__ plans, const BatchImage* __restrict__ imgs,
-                          int n_images, int parity, int apply) {
+                          int n_images, int round, int apply) {
   const int i = batch_image(imgs, n_images, blockIdx.x);
   const BatchImage im = imgs[i];
   const PlanDev d = plans[i];
   const int local = blockIdx.x - im.block0;
   const int per_tile = im.bx * im.by;
   const int t = local / per_tile, rem = local - t * per_tile;
-  feedback_body(d, parity, apply, t, rem % im.bx, rem / im.bx, im.bx, im.by);
+  feedback_body(d, (round - d.round0) & 1, apply, t, rem % im.bx, rem / im.bx, im.bx, im.by);
 }
 
 __global__ void __launch_bounds__(tma::kThreads)
     feedback_tma_batch_kernel(const PlanDev* __restrict__ plans,
                               const BatchImage* __restrict__ imgs, const CUtensorMap* maps,
-                              int n_images, int parity, int apply, uint64_t limit_ns) {
+                              int n_images, int round, int apply, uint64_t limit_ns) {
   const int i = batch_image(imgs, n_images, blockIdx.x);
   const BatchImage im = imgs[i];
   const PlanDev d = plans[i];
   const int local = blockIdx.x - im.block0;
   const int per_tile = im.bx * im.by;
   const int t = local / per_tile, rem = local - t * per_tile;
-  tma::feedback_tma_body(d, maps + i, parity, apply, t, rem % im.bx, rem / im.bx, im.bx, im.by,
-                         limit_ns);
+  tma::feedback_tma_body(d, maps + i, (round - d.round0) & 1, apply, t, rem % im.bx, rem / im.bx,
+                         im.bx, im.by, limit_ns);
 }
 
 
@@ -703,20 +703,20 @@ void feedback_blocks(const PlanDev& d, bool use_tma, int* bx, int* by) {
 
 cudaError_t launch_feedback_batch(const PlanDev* plans, const BatchImage* imgs, int n_images,
                                   int total_blocks, int max_T, const CUtensorMap* maps,
-                                  int parity, int apply, uint64_t limit_ns, cudaStream_t s) {
+                                  int round, int apply, uint64_t limit_ns, cudaStream_t s) {
   if (n_images <= 0 || total_blocks <= 0) return cudaSuccess;
   if (maps) {
     const size_t smem = tma::smem_bytes(max_T);
     cudaError_t e = allow_max_smem((const void*)feedback_tma_batch_kernel);
     if (e != cudaSuccess) return e;
     feedback_tma_batch_kernel<<<total_blocks, tma::kThreads, smem, s>>>(plans, imgs, maps,
-                                                                         n_images, parity, apply,
+                                                                         n_images, round, apply,
                                                                          limit_ns);
   } else {
     const size_t smem = sizeof(Comp4) * kChunk + sizeof(int32_t) * (2 * (size_t)max_T + 1);
     cudaError_t e = allow_max_smem((const void*)feedback_batch_kernel);
     if (e != cudaSuccess) return e;
-    feedback_batch_kernel<<<total_blocks, kThreads, smem, s>>>(plans, imgs, n_images, parity,
+    feedback_batch_kernel<<<total_blocks, kThreads, smem, s>>>(plans, imgs, n_images, round,
                                                                apply);
   }
   return cudaGetLastError();

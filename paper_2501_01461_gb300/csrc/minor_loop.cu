@@ -308,13 +308,14 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 // Batched launch: one CTA per (image, tile) item, each image's plan state in
 // `plans`.  Tiles are independent within a round, so no CTA waits on another.
-template <bool RES>
+template <int SYNC, bool RES>
 __global__ void __launch_bounds__(kThreads, 1)
     minor_batch_kernel(const PlanDev* __restrict__ plans, const BatchItem* __restrict__ items,
-                       MinorCfg c, int parity) {
-  const BatchItem it = items[blockIdx.x];
+                       MinorCfg c, int round) {
+  const BatchItem it = items[blockIdx.x / c.G];
   const PlanDev d = plans[it.image];
-  minor_body<kSyncNone, RES>(d, c, parity, it.tile, 0);
+  const int rank = (SYNC == CLEAN_SYNC_CLUSTER) ? (int)cluster_rank() : 0;
+  minor_body<SYNC, RES>(d, c, (round - d.round0) & 1, it.tile, rank);
 }
 
 
@@ -643,24 +644,72 @@ void* pick(const MinorCfg& c) {
 
 }  // namespace
 
-cudaError_t launch_minor_batch(const PlanDev* plans, const BatchItem* items, int n_items,
-                               int resident, int smem, int parity, cudaStream_t s) {
+namespace {
+const void* batch_fn(int G, int resident) {
+  if (G > 1)
+    return resident ? (const void*)minor_batch_kernel<CLEAN_SYNC_CLUSTER, true>
+                    : (const void*)minor_batch_kernel<CLEAN_SYNC_CLUSTER, false>;
+  return resident ? (const void*)minor_batch_kernel<kSyncNone, true>
+                  : (const void*)minor_batch_kernel<kSyncNone, false>;
+}
+}  // namespace
+
+int minor_batch_cluster(int want, int resident, int smem) {
+  for (int G = std::min(16, std::max(1, want)); G > 1; G /= 2) {
+    const void* fn = batch_fn(G, resident);
+    if (allow_max_smem(fn) != cudaSuccess) break;
+    if (G > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                     cudaSuccess)
+      continue;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(G, 1, 1);
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = resident ? smem : 0;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = G;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) == cudaSuccess && n >= 1) return G;
+  }
+  cudaGetLastError();
+  return 1;
+}
+
+cudaError_t launch_minor_batch(const PlanDev* plans, const BatchItem* items, int n_items, int G,
+                               int resident, int smem, int round, cudaStream_t s) {
   if (n_items <= 0) return cudaSuccess;
   MinorCfg c{};
-  c.G = 1;
-  c.sync = kSyncNone;
+  c.G = G;
+  c.sync = G > 1 ? CLEAN_SYNC_CLUSTER : kSyncNone;
   c.resident = resident;
-  c.smem = smem;
+  c.smem = resident ? smem : 0;
   c.threads = kThreads;
   c.spin_limit_ns = 2000000000ll;
-  const void* fn = resident ? (const void*)minor_batch_kernel<true> : (const void*)minor_batch_kernel<false>;
+  const void* fn = batch_fn(G, resident);
   cudaError_t e = allow_max_smem(fn);
   if (e != cudaSuccess) return e;
-  if (resident)
-    minor_batch_kernel<true><<<n_items, kThreads, smem, s>>>(plans, items, c, parity);
-  else
-    minor_batch_kernel<false><<<n_items, kThreads, 0, s>>>(plans, items, c, parity);
-  return cudaGetLastError();
+  if (G > 8) {
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)(n_items * G), 1, 1);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = c.smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = G;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = G > 1 ? 1 : 0;
+  void* args[] = {const_cast<PlanDev**>(&plans), const_cast<BatchItem**>(&items), &c, &round};
+  return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
 cudaError_t minor_prepare(const MinorCfg& c) {

@@ -1,0 +1,106 @@
+"""Continuous batching: jobs that arrive while others run join at the next
+step and run in the same launches; each job's result must be identical to
+its solo run (clean_plan + clean_run), bit for bit, alone and in the mix."""
+import numpy as np
+import pytest
+
+import paper_2501_01461_gb300 as cg
+from paper_2501_01461_gb300 import serve
+import synth
+from gpu_helpers import gpu_clean
+
+pytestmark = pytest.mark.gpu
+
+
+def _data(n, seed, n_src=10):
+    rng = np.random.default_rng(seed)
+    psf = synth.make_psf(2 * n, 2 * n, freq_scale=1.0 + (seed % 7) / 7)
+    ys, xs, fl = synth.make_sky(n, n_src, 0.05, 2.1, rng)
+    return psf, synth.make_dirty(psf, n, ys, xs, fl, 1e-3, rng)
+
+
+def _same(result, solo):
+    res, mod, comps = result
+    assert len(comps) == solo["n"]
+    assert np.array_equal(comps["flux"].view(np.uint32), solo["comps"]["flux"].view(np.uint32))
+    assert np.array_equal(comps["y"], solo["comps"]["y"]) and np.array_equal(comps["x"], solo["comps"]["x"])
+    assert np.array_equal(res.cpu().numpy().view(np.uint32), solo["residual"].view(np.uint32))
+    assert np.array_equal(mod.cpu().numpy().view(np.uint32), solo["model"].view(np.uint32))
+
+
+def test_jobs_joining_midway_equal_solo_runs():
+    import torch
+    specs = [(256, (2, 2), 20, 800), (512, (2, 2), 50, 1500), (128, (1, 1), 10, 300),
+             (1024, (4, 4), 50, 2000), (200, (3, 3), 7, 600)]
+    data = [_data(n, 40 + i) for i, (n, *_r) in enumerate(specs)]
+    srv = serve.Server(max_jobs=8)
+    jobs = {}
+    try:
+        # two jobs start; the others join one at a time while they run
+        for i in range(len(specs)):
+            n, tiles, K, niter = specs[i]
+            psf, dirty = data[i]
+            job = serve.Job(psf=torch.from_numpy(psf).cuda(), dirty=torch.from_numpy(dirty).cuda(),
+                            niter=niter, tiles=tiles, feedback_interval=K)
+            jobs[srv.add(job)] = (i, job)
+            if i >= 1:
+                srv.step(1)
+        while srv.step(3) > 0:
+            pass
+        finished = srv.done()
+        assert sorted(finished) == sorted(jobs)
+        for jid in finished:
+            i, job = jobs[jid]
+            n, tiles, K, niter = specs[i]
+            r = srv.get(jid, (n, n))
+            _same(r, gpu_clean(data[i][1], data[i][0], 0.1, niter, 0.0, tiles, K))
+            srv.remove(jid)
+    finally:
+        srv.close()
+
+
+def test_serve_loop_results_and_latencies():
+    import torch
+    rng = np.random.default_rng(5)
+    specs = []
+    for k in range(10):
+        n = int(rng.choice([128, 256, 512]))
+        specs.append((n, (2, 2) if n > 128 else (1, 1), int(rng.integers(5, 40)),
+                      int(rng.integers(200, 1200)), float(k) * 0.002))
+    data = [_data(n, 70 + k) for k, (n, *_r) in enumerate(specs)]
+    jobs = [serve.Job(psf=torch.from_numpy(p).cuda(), dirty=torch.from_numpy(d).cuda(), niter=nit,
+                      tiles=t, feedback_interval=K, arrival=a)
+            for (p, d), (n, t, K, nit, a) in zip(data, specs)]
+    stats = serve.serve(jobs, budget_bytes=2e9, rounds_per_step=2)
+    assert stats["jobs"] == 10 and stats["p99_s"] >= stats["p50_s"] > 0
+    for (p, d), (n, t, K, nit, a), job in zip(data, specs, jobs):
+        assert job.admitted >= a - 1e-9 and job.finished >= job.admitted
+        _same(job.result, gpu_clean(d, p, 0.1, nit, 0.0, t, K))
+
+
+def test_remove_running_job_and_memory_budget_admission():
+    import torch
+    psf, dirty = _data(256, 3)
+    srv = serve.Server(max_jobs=2)
+    try:
+        job = serve.Job(psf=torch.from_numpy(psf).cuda(), dirty=torch.from_numpy(dirty).cuda(),
+                        niter=5000, tiles=(2, 2), feedback_interval=10)
+        a = srv.add(job)
+        srv.step(1)
+        srv.remove(a)                     # leaves mid-run
+        b = srv.add(job)
+        c = srv.add(job)
+        with pytest.raises(cg.CleanError) as e:
+            srv.add(job)                  # no free slot
+        assert e.value.status == 3
+        while srv.step(4) > 0:
+            pass
+        assert sorted(srv.done()) == sorted([b, c])
+    finally:
+        srv.close()
+    # a budget smaller than two jobs admits them one after the other
+    jobs = [serve.Job(psf=torch.from_numpy(psf).cuda(), dirty=torch.from_numpy(dirty).cuda(),
+                      niter=400, tiles=(2, 2), feedback_interval=20, arrival=0.0) for _ in range(3)]
+    serve.serve(jobs, budget_bytes=jobs[0].footprint() * 1.5, keep_results=False)
+    order = sorted(jobs, key=lambda j: j.admitted)
+    assert order[1].admitted >= order[0].finished - 1e-9
