@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fft", action="store_true", help="skip the FFT-feedback comparison run")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 64-image leg")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
     ap.add_argument("--untiled-iters", type=int, default=2000,
                     help="iterations of the untiled whole-GPU comparison run (0: skip)")
     ap.add_argument("--profile", type=int, default=0, metavar="R",
@@ -247,6 +248,54 @@ def batch_leg(cg, torch, stream, n_images=64):
             "vs_one_at_a_time_tiled": ms_solo / ms_batch,
             "vs_one_at_a_time_plain": ms_plain / ms_batch,
             "rounds": st["rounds_launched"], "kernel_launches": st["kernel_launches"]}
+
+
+def serve_leg(cg, torch, n_jobs=60, load=0.7):
+    """Poisson stream of mixed-size jobs through the continuous-batching
+    server vs one-at-a-time plain (untiled) CLEAN on the same arrivals.  The
+    arrival rate is `load` x the one-at-a-time server's capacity (1 / its
+    mean service time, measured here), so the baseline queue is stable."""
+    from paper_2501_01461_gb300 import serve
+    images, specs = synth.serving_jobs(n_jobs)
+    dev = {n: (torch.from_numpy(p).cuda(), torch.from_numpy(d).cuda()) for n, (p, d) in images.items()}
+    # one-at-a-time plain CLEAN: service time of every job, measured alone
+    service = []
+    for sp in specs:
+        psf, dirty = dev[sp["n"]]
+        with cg.Plan(psf, sp["n"], sp["n"], gain=0.1, niter=sp["niter"], threshold=0.0,
+                     mode=cg.UNTILED_GRID) as p:
+            p.run(dirty)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            p.run(dirty)
+            b.record()
+            torch.cuda.synchronize()
+            service.append(a.elapsed_time(b) / 1e3)
+    rate = load / float(np.mean(service))
+    rng = np.random.default_rng(7)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_jobs))
+    arrivals -= arrivals[0]
+    base = serve.fifo_latencies(arrivals, service)
+    jobs = [serve.Job(psf=dev[sp["n"]][0], dirty=dev[sp["n"]][1], niter=sp["niter"],
+                      tiles=sp["tiles"], feedback_interval=sp["K"], arrival=float(t))
+            for sp, t in zip(specs, arrivals)]
+    st = serve.serve(jobs, budget_bytes=150e9, rounds_per_step=2, keep_results=False)
+    # saturated throughput: every job waiting at t = 0
+    for j in jobs:
+        j.arrival, j.admitted, j.finished = 0.0, None, None
+    sat = serve.serve(jobs, budget_bytes=150e9, rounds_per_step=4, keep_results=False)
+    total_iters = sum(sp["niter"] for sp in specs)
+    return {"workload": f"{n_jobs} jobs, sizes 256-4096 (powers of two, log-uniform), "
+                        "1000-20000 iterations, K 50, Poisson arrivals at "
+                        f"{load:.1f} x the one-at-a-time plain-CLEAN capacity, 150 GB budget",
+            "arrival_rate_per_s": rate,
+            "p50_s": st["p50_s"], "p99_s": st["p99_s"], "jobs_per_s": st["jobs_per_s"],
+            "one_at_a_time_plain_p50_s": float(np.percentile(base, 50)),
+            "one_at_a_time_plain_p99_s": float(np.percentile(base, 99)),
+            "saturated_jobs_per_s": sat["jobs_per_s"],
+            "saturated_iters_per_s": total_iters / sat["makespan_s"],
+            "one_at_a_time_plain_jobs_per_s": n_jobs / float(np.sum(service))}
 
 
 def cpu_baseline(w, data):
@@ -490,6 +539,10 @@ def main():
     if not args.no_batch:
         batched = batch_leg(cg, torch, stream)
 
+    served = None
+    if not args.no_serve:
+        served = serve_leg(cg, torch)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(w, data)
@@ -513,6 +566,7 @@ def main():
             "vs_untiled_gpu": (value / untiled["iters_per_s"]) if untiled else None,
             "fft_feedback": fft,
             "batched": batched,
+            "served": served,
             "gpu_launches": int(gpu_launches),
             "clocks": clocks, "wall_s_timed": wall,
             "plan": {k: st[k] for k in ("group_ctas", "group_sync", "resident", "sm_count")},

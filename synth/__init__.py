@@ -300,3 +300,24 @@ def batch_jobs(n_images: int = 64, seed: int = 1003, niter: int = 2000, n_source
         jobs.append(dict(n=n, psf=psf, dirty=dirty, tiles=(2, 2) if n <= 1024 else (4, 4),
                          K=50, niter=niter, gain=0.1))
     return jobs
+
+
+def serving_jobs(n_jobs: int = 60, seed: int = 1004, sizes=(256, 512, 1024, 2048, 4096)):
+    """Serving stream: sizes log-uniform over {256 .. 4096} (uniform over the
+    five powers of two), 10 - 500 sources, 1000 - 20000 iterations, gain 0.1,
+    K 50, tiles 1x1 up to 256, 2x2 up to 1024, 4x4 above.  One PSF and one
+    dirty image per size (each job draws its own source count for the record
+    but shares its size's image, which keeps the generator fast).  Returns
+    (images_by_size, job specs)."""
+    rng = np.random.default_rng(seed)
+    images = {}
+    for n in sizes:
+        psf = make_psf(2 * n, 2 * n)
+        ys, xs, fl = make_sky(n, int(rng.integers(10, 501)), 0.01, 2.1, rng)
+        images[n] = (psf, make_dirty(psf, n, ys, xs, fl, 1e-3, rng))
+    specs = []
+    for _ in range(n_jobs):
+        n = int(rng.choice(sizes))
+        tiles = (1, 1) if n <= 256 else (2, 2) if n <= 1024 else (4, 4)
+        specs.append(dict(n=n, niter=int(rng.integers(1000, 20001)), tiles=tiles, K=50))
+    return images, specs
