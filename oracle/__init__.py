@@ -67,11 +67,11 @@ def _load():
             vp = ctypes.c_void_p
             lib.oracle_clean_f32.restype = i64
             lib.oracle_clean_f32.argtypes = [vp, i32, i32, vp, i32, i32, f64, i64,
-                                             f64, i32, i32, i32, i32, vp, vp, vp,
+                                             f64, i32, i32, i32, f64, i32, vp, vp, vp,
                                              vp, vp, vp, vp, i64, vp]
             lib.oracle_clean_f64.restype = i64
             lib.oracle_clean_f64.argtypes = [vp, i32, i32, vp, i32, i32, f64, i64,
-                                             f64, i32, i32, i32, i32, vp, vp, vp,
+                                             f64, i32, i32, i32, f64, i32, vp, vp, vp,
                                              vp, i64, vp, vp, vp, vp, vp, vp, vp,
                                              i64, vp]
             _lib = lib
@@ -93,22 +93,23 @@ def _f32(v: float) -> float:
 
 
 def clean_f32(dirty, psf, gain, niter, threshold=0.0, tiles=(1, 1), K=0,
-              max_rounds=-1) -> Result:
-    """Float32 oracle.  tiles=(1,1), K=0 is plain (untiled) Hogbom CLEAN."""
+              max_rounds=-1, trigger=0.0) -> Result:
+    """Float32 oracle.  tiles=(1,1), K=0 is plain (untiled) Hogbom CLEAN.
+    trigger in (0, 1): flux-triggered rounds (see clean_oracle.c)."""
     return _run(np.float32, dirty, psf, gain, niter, threshold, tiles, K,
-                max_rounds, None)
+                max_rounds, None, trigger)
 
 
 def clean_f64(dirty, psf, gain, niter, threshold=0.0, tiles=(1, 1), K=0,
-              max_rounds=-1, replay=None) -> Result:
+              max_rounds=-1, replay=None, trigger=0.0) -> Result:
     """Float64 twin.  ``replay`` = a component dict (y, x, tile, round) from a
     float32 run: positions and round structure are forced from it."""
     return _run(np.float64, dirty, psf, gain, niter, threshold, tiles, K,
-                max_rounds, replay)
+                max_rounds, replay, trigger)
 
 
 def _run(dtype, dirty, psf, gain, niter, threshold, tiles, K, max_rounds,
-         replay):
+         replay, trigger=0.0):
     lib = _load()
     dirty = np.ascontiguousarray(dirty, dtype=np.float32)
     psf = np.ascontiguousarray(psf, dtype=np.float32)
@@ -125,7 +126,7 @@ def _run(dtype, dirty, psf, gain, niter, threshold, tiles, K, max_rounds,
     if dtype == np.float32:
         n = lib.oracle_clean_f32(_ptr(dirty), ny, nx, _ptr(psf), pny, pnx,
                                  _f32(gain), int(niter), _f32(threshold), ty, tx,
-                                 int(K), int(max_rounds), _ptr(res), _ptr(model),
+                                 int(K), _f32(trigger), int(max_rounds), _ptr(res), _ptr(model),
                                  _ptr(oy), _ptr(ox), _ptr(of), _ptr(ot), _ptr(orr),
                                  cap, ctypes.byref(rounds))
     else:
@@ -140,7 +141,7 @@ def _run(dtype, dirty, psf, gain, niter, threshold, tiles, K, max_rounds,
             rn = -1
         n = lib.oracle_clean_f64(_ptr(dirty), ny, nx, _ptr(psf), pny, pnx,
                                  _f32(gain), int(niter), _f32(threshold), ty, tx,
-                                 int(K), int(max_rounds), _ptr(ry), _ptr(rx),
+                                 int(K), _f32(trigger), int(max_rounds), _ptr(ry), _ptr(rx),
                                  _ptr(rt), _ptr(rr), rn, _ptr(res), _ptr(model),
                                  _ptr(oy), _ptr(ox), _ptr(of), _ptr(ot), _ptr(orr),
                                  cap, ctypes.byref(rounds))
@@ -176,7 +177,7 @@ def _shifted_psf(psf, ny, nx, py, px, dtype):
 
 
 def brute_clean(dirty, psf, gain, niter, threshold=0.0, tiles=(1, 1), K=0,
-                dtype=np.float32, max_rounds=-1):
+                dtype=np.float32, max_rounds=-1, trigger=0.0):
     """Literal CLEAN for tiny images, independent of the C oracle.
 
     Each subtraction builds the full shifted PSF image and applies
@@ -194,6 +195,8 @@ def brute_clean(dirty, psf, gain, niter, threshold=0.0, tiles=(1, 1), K=0,
     ty, tx = tiles
     T = ty * tx
     g, thr = dt(np.float32(gain)), dt(np.float32(threshold))
+    trig = dt(np.float32(trigger))
+    feedback = (K > 0 or trigger > 0) and ty * tx > 1
     masks = []
     for t in range(T):
         i, j = divmod(t, tx)
@@ -214,13 +217,17 @@ def brute_clean(dirty, psf, gain, niter, threshold=0.0, tiles=(1, 1), K=0,
         if not any(active):
             break
         new = []
+        # flux trigger: the round ends for a tile at trigger x the largest
+        # |peak| among the tiles taking part in the round
+        top = max([abs(peak(t)[1]) for t in range(T) if active[t]], default=dt(0))
+        level = dt(trig * top) if trigger > 0 else dt(0)
         for t in range(T):
             if not active[t]:
                 continue
             kmax = budget[t] if K == 0 else min(K, budget[t])
             for _ in range(kmax):
                 p, v = peak(t)
-                if abs(v) <= thr:
+                if abs(v) <= thr or abs(v) <= level:
                     break
                 f = dt(g * v)
                 py, px = divmod(p, nx)
@@ -230,7 +237,7 @@ def brute_clean(dirty, psf, gain, niter, threshold=0.0, tiles=(1, 1), K=0,
                 comps.append((py, px, f, t, rnd))
                 new.append((py, px, f, t))
                 budget[t] -= 1
-        if K > 0 and T > 1:
+        if feedback:
             # cross-coupling: tile s's components placed on a full-size image
             # and spread by the full PSF, applied to every other tile; per
             # pixel the components are applied in list order

@@ -89,13 +89,16 @@ static void FN(subtract_psf)(REAL* R, int32_t nx, const REAL* P, int32_t pny,
 static int64_t FN(clean_run)(
     const float* dirty, int32_t ny, int32_t nx, const float* psf, int32_t pny,
     int32_t pnx, double gain_in, int64_t niter, double threshold_in,
-    int32_t ty, int32_t tx, int32_t K, int32_t max_rounds,
+    int32_t ty, int32_t tx, int32_t K, double trigger_in, int32_t max_rounds,
     const int32_t* replay_y, const int32_t* replay_x,
     const int32_t* replay_tile, const int32_t* replay_round, int64_t replay_n,
     REAL* residual, REAL* model, int32_t* out_y, int32_t* out_x, REAL* out_f,
     int32_t* out_tile, int32_t* out_round, int64_t cap, int32_t* rounds_out) {
   const REAL g = (REAL)gain_in;
   const REAL thr = (REAL)threshold_in;
+  const REAL trig = (REAL)trigger_in;
+  /* feedback happens after every round when an interval or a trigger is set */
+  const int feedback = (K > 0 || trigger_in > 0) && ty * tx > 1;
   const int32_t T = ty * tx;
   const int64_t npix = (int64_t)ny * nx;
   const int replay = replay_n >= 0;
@@ -154,8 +157,24 @@ static int64_t FN(clean_run)(
       }
       if (!any) break;
 
+      /* flux trigger (Section 3): this round ends for a tile once its
+       * |peak| is at most trigger x the largest |peak| among the tiles taking
+       * part in the round (that tile always makes progress) */
+      REAL level = 0;
+      if (trig > 0) {
+        REAL top = 0;
+        for (int32_t t = 0; t < T; ++t) {
+          if (!active[t]) continue;
+          int32_t y0, y1, x0, x1;
+          FN(tile_bounds)(t, ny, nx, ty, tx, &y0, &y1, &x0, &x1);
+          REAL a = FN(absr)(residual[FN(argmax_abs)(residual, nx, y0, y1, x0, x1)]);
+          if (a > top) top = a;
+        }
+        level = trig * top;
+      }
       /* minor loops: every tile on its own pixels, up to K iterations
-       * (K = 0: no feedback, the whole budget in one round) */
+       * (K = 0: no interval; without a trigger, no feedback and the whole
+       * budget in one round) */
       for (int32_t t = 0; t < T; ++t) {
         if (!active[t]) continue;
         int32_t y0, y1, x0, x1;
@@ -164,7 +183,7 @@ static int64_t FN(clean_run)(
         for (int64_t k = 0; k < kmax; ++k) {
           int64_t p = FN(argmax_abs)(residual, nx, y0, y1, x0, x1);
           REAL v = residual[p];
-          if (FN(absr)(v) <= thr) break;
+          if (FN(absr)(v) <= thr || FN(absr)(v) <= level) break;
           if (ncomp >= cap) goto overflow;
           REAL f = g * v;                            /* first equation */
           int32_t py = (int32_t)(p / nx), px = (int32_t)(p % nx);
@@ -182,7 +201,7 @@ static int64_t FN(clean_run)(
      * with the full PSF, is subtracted from every tile except its own.  Per
      * pixel the components are taken in list order (tile, then iteration),
      * one rounded multiply and one rounded subtract each. */
-    if (K > 0 && T > 1) {
+    if (feedback) {
       for (int64_t c = round_start; c < ncomp; ++c) {
         for (int32_t t = 0; t < T; ++t) {
           if (t == out_tile[c]) continue;

@@ -43,7 +43,7 @@ def test_worked_examples(fn):
     g, psf, dirty = _golden()
     for case in g["cases"]:
         r = fn(dirty, psf, case["gain"], case["niter"], case["threshold"],
-               tuple(case["tiles"]), case["K"])
+               tuple(case["tiles"]), case["K"], trigger=case.get("trigger", 0.0))
         assert _comp_rows(r) == case["components"], case["name"]
         assert np.array_equal(r.residual, np.array(case["residual"])), case["name"]
         assert r.rounds == case["rounds"], case["name"]
@@ -53,7 +53,7 @@ def test_worked_examples_brute():
     g, psf, dirty = _golden()
     for case in g["cases"]:
         r = oracle.brute_clean(dirty, psf, case["gain"], case["niter"], case["threshold"],
-                               tuple(case["tiles"]), case["K"])
+                               tuple(case["tiles"]), case["K"], trigger=case.get("trigger", 0.0))
         assert _comp_rows(r) == case["components"], case["name"]
         assert np.array_equal(r.residual, np.array(case["residual"])), case["name"]
 
@@ -271,3 +271,34 @@ def test_budget_split_and_rounds():
     assert r.rounds == 2
     assert np.bincount(r.comps["tile"], minlength=4).tolist() == [2, 2, 2, 1]
     assert r.comps["tile"].tolist() == [0, 1, 2, 3, 0, 1, 2]
+
+
+@pytest.mark.parametrize("tiles,K,trigger", [((2, 2), 0, 0.5), ((4, 4), 3, 0.3), ((2, 3), 0, 0.9),
+                                             ((1, 1), 0, 0.5)])
+def test_brute_force_flux_trigger(tiles, K, trigger):
+    """Flux-triggered rounds (Section 3): literal restatement agrees."""
+    rng = np.random.default_rng(int(trigger * 100) + K)
+    ny, nx = 16, 15 if tiles == (2, 3) else 16
+    psf = synth.random_psf(2 * ny, 2 * nx, rng)
+    for dirty in (synth.random_image(ny, nx, rng), synth.tie_image(ny, nx, rng)):
+        for dt, fn in ((np.float32, oracle.clean_f32), (np.float64, oracle.clean_f64)):
+            a = fn(dirty, psf, 0.3, 60, 0.02, tiles, K, trigger=trigger)
+            b = oracle.brute_clean(dirty, psf, 0.3, 60, 0.02, tiles, K, dtype=dt, trigger=trigger)
+            assert a.n == b.n and a.rounds == b.rounds
+            assert np.array_equal(a.residual, b.residual)
+            for key in ("y", "x", "flux", "tile", "round"):
+                assert np.array_equal(a.comps[key], b.comps[key]), key
+
+
+def test_flux_trigger_identity_and_progress():
+    """Every round makes progress and the final feedback keeps
+    model * PSF + residual = dirty."""
+    rng = np.random.default_rng(17)
+    n = 40
+    psf = synth.make_psf(2 * n, 2 * n)
+    ys, xs, fl = synth.make_sky(n, 12, 0.05, 2.1, rng)
+    dirty = synth.make_dirty(psf, n, ys, xs, fl, 1e-3, rng)
+    r = oracle.clean_f64(dirty, psf, 0.1, 600, 1e-3, (2, 2), 0, trigger=0.5)
+    assert r.n == 600 or np.abs(r.residual).max() <= np.float32(1e-3) * 1.0000001
+    assert len(np.unique(r.comps["round"])) == r.rounds
+    assert _identity_err(r, dirty, psf) <= 1e-9 * np.abs(dirty).max()
