@@ -27,9 +27,10 @@
  *   - a tile stops while |peak| <= threshold; it is checked again after each
  *     feedback;
  *   - the feedback interval K counts minor iterations per tile; a round is up
- *     to K iterations in every tile, then one feedback; K = 0 means no
- *     feedback (independent tiles, Fig. 1(b)); the last round executed always
- *     ends with its feedback;
+ *     to K iterations in every tile, then one feedback; a flux trigger may
+ *     end a tile's round earlier (clean_params.feedback_trigger); K = 0 with
+ *     no trigger means no feedback (independent tiles, Fig. 1(b)); the last
+ *     round executed always ends with its feedback;
  *   - feedback applies, to each pixel, the other tiles' components of the
  *     round in list order (tile index, then iteration), each as a rounded
  *     float32 multiply followed by a rounded float32 subtract;
@@ -103,7 +104,12 @@ typedef struct {
   int32_t mode;              /* CLEAN_TILED | CLEAN_UNTILED_GRID (needs a 1 x 1 grid) */
   int32_t group_ctas;        /* CTAs per tile in the minor loop; 0 = choose */
   int32_t group_sync;        /* CLEAN_SYNC_*: cluster barrier or bounded grid barrier */
-  int32_t reserved[5];       /* must be 0 */
+  float feedback_trigger;    /* 0, or in (0, 1): a tile's round also ends once its
+                                |peak| <= feedback_trigger x the largest |peak| among
+                                the tiles taking part in the round (Section 3: a flux
+                                threshold starts the feedback); with K = 0 the rounds
+                                end on flux alone */
+  int32_t reserved[4];       /* must be 0 */
 } clean_params;
 
 typedef struct clean_plan_s* clean_plan_t;

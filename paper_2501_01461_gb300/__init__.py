@@ -53,7 +53,8 @@ class Params(ctypes.Structure):
                 ("tiles_y", ctypes.c_int32), ("tiles_x", ctypes.c_int32),
                 ("feedback_interval", ctypes.c_int32), ("feedback_mode", ctypes.c_int32),
                 ("mode", ctypes.c_int32), ("group_ctas", ctypes.c_int32),
-                ("group_sync", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("group_sync", ctypes.c_int32), ("feedback_trigger", ctypes.c_float),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class Stats(ctypes.Structure):
@@ -160,7 +161,7 @@ def _dptr(t, shape=None, what="tensor"):
 
 def make_params(ny, nx, psf_shape, gain=0.1, niter=0, threshold=0.0, tiles=(1, 1),
                 feedback_interval=0, feedback_mode=FB_GATHER, mode=TILED,
-                group_ctas=0, group_sync=SYNC_AUTO) -> Params:
+                group_ctas=0, group_sync=SYNC_AUTO, feedback_trigger=0.0) -> Params:
     p = Params()
     lib().clean_params_default(ctypes.byref(p))
     p.ny, p.nx = int(ny), int(nx)
@@ -170,6 +171,7 @@ def make_params(ny, nx, psf_shape, gain=0.1, niter=0, threshold=0.0, tiles=(1, 1
     p.feedback_interval = int(feedback_interval)
     p.feedback_mode, p.mode = int(feedback_mode), int(mode)
     p.group_ctas, p.group_sync = int(group_ctas), int(group_sync)
+    p.feedback_trigger = float(feedback_trigger)
     return p
 
 
@@ -183,7 +185,8 @@ class Plan:
 
     def __init__(self, psf, ny, nx, gain=0.1, niter=0, threshold=0.0, tiles=(1, 1),
                  feedback_interval=0, feedback_mode=FB_GATHER, mode=TILED,
-                 group_ctas=0, group_sync=SYNC_AUTO, psf_shape=None, stream=None):
+                 group_ctas=0, group_sync=SYNC_AUTO, psf_shape=None, stream=None,
+                 feedback_trigger=0.0):
         if psf is not None:
             psf_shape = tuple(psf.shape)
             ptr = _dptr(psf, what="psf")
@@ -193,7 +196,7 @@ class Plan:
             ptr = None
         self.params = make_params(ny, nx, psf_shape, gain, niter, threshold, tiles,
                                   feedback_interval, feedback_mode, mode, group_ctas,
-                                  group_sync)
+                                  group_sync, feedback_trigger)
         self.ny, self.nx, self.niter = int(ny), int(nx), int(niter)
         self._psf = psf
         self._h = ctypes.c_void_p()

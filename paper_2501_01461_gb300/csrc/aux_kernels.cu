@@ -143,7 +143,29 @@ __global__ void beam_table_kernel(float* beam, int r, float smaj, float smin, fl
   }
 }
 
+// The flux-trigger level of the first round: trigger x the largest |peak|
+// among the tiles that can run (budget left, |peak| > threshold).
+__global__ void first_level_kernel(PlanDev d) {
+  __shared__ uint32_t s_top;
+  if (threadIdx.x == 0) s_top = 0u;
+  __syncthreads();
+  uint32_t top = 0u;
+  for (int s = threadIdx.x; s < d.T; s += blockDim.x) {
+    const uint64_t pk = d.peak[s];
+    if (d.budget[s] > 0 && pk != 0ull && key_abs(pk) > d.thr) top = max(top, (uint32_t)(pk >> 32));
+  }
+  if (top) atomicMax(&s_top, top);
+  __syncthreads();
+  if (threadIdx.x == 0) d.st->level = __fmul_rn(d.trigger, __uint_as_float(s_top));
+}
+
 }  // namespace
+
+cudaError_t launch_first_level(const PlanDev& d, cudaStream_t s) {
+  if (!(d.trigger > 0.f)) return cudaSuccess;
+  first_level_kernel<<<1, 256, 0, s>>>(d);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_init(const PlanDev& d, const float* dirty, int64_t niter, cudaStream_t s) {
   int maxH = 0;

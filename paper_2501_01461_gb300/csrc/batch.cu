@@ -111,6 +111,7 @@ int engine_start(clean_engine_s* e, Job& j, const float* d_dirty, cudaStream_t s
   if (err == cudaSuccess) err = cudaMemsetAsync(j.dev.peak, 0, sizeof(uint64_t) * 2 * j.dev.T, s);
   if (err == cudaSuccess) err = launch_init(j.dev, d_dirty, plan_niter(j.plan), s);
   ++e->kernel_launches;
+  if (err == cudaSuccess) err = launch_first_level(j.dev, s);
   if (err != cudaSuccess) return eng_fail(e, CLEAN_ERR_CUDA);
   std::memset(&e->h_states[j.slot], 0, sizeof(DevState));
   e->h_states[j.slot].active = 1;  // refreshed at the next status read

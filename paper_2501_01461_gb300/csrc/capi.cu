@@ -237,7 +237,7 @@ cudaError_t launch_fft_feedback(clean_plan_s* pl, cudaStream_t s) {
 }
 
 int launch_round_feedback(clean_plan_s* pl, cudaStream_t s) {
-  const int apply = (pl->d.K > 0 && pl->d.T > 1) ? 1 : 0;
+  const int apply = feedback_on(pl->d) ? 1 : 0;
   if (apply && pl->fft) {
     const int ev = timed_begin(pl, 1, s);
     cudaError_t e = launch_fft_feedback(pl, s);
@@ -288,6 +288,10 @@ int start_run(clean_plan_s* pl, const float* d_dirty, cudaStream_t s) {
   if (e == cudaSuccess) e = cudaMemsetAsync(pl->d.st, 0, sizeof(DevState), s);
   if (e == cudaSuccess) e = launch_init(pl->d, d_dirty, pl->p.niter, s);
   ++pl->kernel_launches;
+  if (e == cudaSuccess && pl->d.trigger > 0.f) {
+    e = launch_first_level(pl->d, s);
+    ++pl->kernel_launches;
+  }
   if (e == cudaSuccess && pl->fft)
     e = cudaMemcpyAsync(pl->R0, pl->d.R, sizeof(float) * (size_t)pl->d.ny * pl->d.nx,
                         cudaMemcpyDeviceToDevice, s);
@@ -402,7 +406,10 @@ int clean_params_check(const clean_params* p) {
       p->group_sync != CLEAN_SYNC_GRID)
     return CLEAN_ERR_INVALID_ARG;
   if (p->group_sync == CLEAN_SYNC_CLUSTER && p->group_ctas > 16) return CLEAN_ERR_INVALID_ARG;
-  for (int i = 0; i < 5; ++i)
+  if (!std::isfinite(p->feedback_trigger) || !(p->feedback_trigger >= 0.f) ||
+      !(p->feedback_trigger < 1.f))
+    return CLEAN_ERR_INVALID_ARG;
+  for (int i = 0; i < 4; ++i)
     if (p->reserved[i] != 0) return CLEAN_ERR_INVALID_ARG;
   return CLEAN_OK;
 }
@@ -542,12 +549,14 @@ int clean_plan(clean_plan_t* out, const clean_params* p, const float* d_psf, voi
   // convolution never wraps onto an image pixel.  AUTO takes it when a round's
   // gather (about 0.26 ns per pixel-component update on GB300) would cost more
   // than the transforms (estimated 16 ps per grid cell plus 60 us of launches).
-  const bool feedback_on = p->feedback_interval > 0 && T > 1;
+  const bool fb_on = (p->feedback_interval > 0 || p->feedback_trigger > 0.f) && T > 1;
   pl->Ly = fft_size(2 * p->ny - 1);
   pl->Lx = fft_size(2 * p->nx - 1);
-  if (feedback_on && p->feedback_mode == CLEAN_FB_FFT) pl->fft = true;
-  if (feedback_on && p->feedback_mode == CLEAN_FB_AUTO) {
-    const double comps = (double)std::min<int64_t>(p->feedback_interval, per_tile_max) * T;
+  if (fb_on && p->feedback_mode == CLEAN_FB_FFT) pl->fft = true;
+  if (fb_on && p->feedback_mode == CLEAN_FB_AUTO) {
+    const double comps =
+        (double)(p->feedback_interval > 0 ? std::min<int64_t>(p->feedback_interval, per_tile_max)
+                                          : per_tile_max) * T;
     const double gather_s = comps * ((double)npix - (double)npix / T) * 0.26e-9;
     const double fft_s = (double)pl->Ly * pl->Lx * 16e-12 + 60e-6;
     pl->fft = fft_s < gather_s;
@@ -615,6 +624,7 @@ int clean_plan(clean_plan_t* out, const clean_params* p, const float* d_psf, voi
   d.gain = p->gain;
   d.thr = p->threshold;
   d.K = p->feedback_interval;
+  d.trigger = p->feedback_trigger;
   d.cap_round = (int32_t)cap_round;
 
   if (pl->fft) {

@@ -78,6 +78,8 @@ struct DevState {
   int64_t round_comps;   // components of the last closed round
   int64_t max_budget;    // max over tiles of the remaining budget
   int64_t timeout_where; // diagnostic: tile * 2^32 + barrier index of a timeout
+  float level;           // flux-trigger level of the next round (0: none)
+  int32_t pad1;
 };
 
 // Pointers and sizes every kernel of a plan sees.
@@ -89,6 +91,7 @@ struct PlanDev {
   int32_t ty, tx, T;        // tile grid and tile count
   float gain, thr;
   int32_t K;                // feedback interval (0 = none)
+  float trigger;            // flux trigger (0 = none)
   int32_t cap_round;        // per-tile capacity of the round buffer
   int32_t round0;           // batched runs: the batch round at which this image started
   int64_t* budget;          // [T] remaining iterations per tile
@@ -162,6 +165,13 @@ inline cudaError_t allow_max_smem(const void* fn) {
 cudaError_t launch_init(const PlanDev& d, const float* dirty, int64_t niter,
                         cudaStream_t s);
 cudaError_t launch_validate_psf(const PlanDev& d, cudaStream_t s);
+// Flux-trigger level of a run's first round (after launch_init); no-op
+// without a trigger.
+cudaError_t launch_first_level(const PlanDev& d, cudaStream_t s);
+// Whether rounds of this plan end with a feedback.
+__host__ __device__ __forceinline__ bool feedback_on(const PlanDev& d) {
+  return (d.K > 0 || d.trigger > 0.f) && d.T > 1;
+}
 // r_map / p_map: 2-D tensor maps of the residual and the PSF with the box
 // (c.box_w x c.chunk_h) of a pipelined configuration (ignored otherwise).
 cudaError_t launch_minor(const PlanDev& d, const MinorCfg& c, int parity,

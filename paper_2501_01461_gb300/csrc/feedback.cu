@@ -121,17 +121,26 @@ __device__ void close_round_if_last(const PlanDev& d, int parity, int total_bloc
     d.list[total0 + g] = cc;
     if (clear_grid) clear_grid[(int64_t)cc.y * clear_pitch + cc.x] = 0.f;
   }
-  // any tile that can run next round; largest remaining budget
+  // any tile that can run next round; largest remaining budget; the largest
+  // |peak| among those tiles (the flux trigger's reference)
   int act = 0;
   int64_t mb = 0;
+  uint32_t top = 0u;  // |peak| bits: non-negative floats order like integers
   for (int s = threadIdx.x; s < d.T; s += nthr) {
     const int64_t b = ((volatile int64_t*)d.budget)[s];
     const uint64_t pk = ((volatile unsigned long long*)d.peak)[(parity ^ 1) * d.T + s];
-    if (b > 0 && pk != 0ull && key_abs(pk) > d.thr) act = 1;
+    if (b > 0 && pk != 0ull && key_abs(pk) > d.thr) {
+      act = 1;
+      top = max(top, (uint32_t)(pk >> 32));
+    }
     mb = b > mb ? b : mb;
     d.gbar[s] = 0u;
   }
   act = __syncthreads_or(act);
+  __shared__ uint32_t s_top;
+  if (threadIdx.x == 0) s_top = 0u;
+  __syncthreads();
+  if (top) atomicMax(&s_top, top);
   for (int o = 16; o > 0; o >>= 1) {
     const int64_t other = __shfl_xor_sync(0xffffffffu, mb, o);
     mb = other > mb ? other : mb;
@@ -149,6 +158,7 @@ __device__ void close_round_if_last(const PlanDev& d, int parity, int total_bloc
     d.st->round_comps = n_all;
     d.st->active = act;
     d.st->max_budget = m;
+    d.st->level = d.trigger > 0.f ? __fmul_rn(d.trigger, __uint_as_float(s_top)) : 0.f;
     d.st->fb_done = 0u;
   }
 }
@@ -179,7 +189,7 @@ __device__ __forceinline__ void feedback_body(const PlanDev& d, int parity, int 
 
   if (live) {
     // the other tiles' components of this round, in list order
-    const bool fb = apply && d.K > 0 && d.T > 1;  // this image feeds back at all
+    const bool fb = apply && feedback_on(d);  // this image feeds back at all
     for (int s = threadIdx.x; s < d.T; s += kThreads) s_cnt[s] = (s == t || !fb) ? 0 : d.rcount[s];
     block_prefix(s_cnt, s_pre, d.T);
     const int n_other = s_pre[d.T];
@@ -357,7 +367,7 @@ __device__ __forceinline__ void feedback_tma_body(const PlanDev& d, const CUtens
     }
     if (producer && lane == 0) ptx::prefetch_tensormap(psf_map);
     for (int s = threadIdx.x; s < d.T; s += kThreads)
-      s_cnt[s] = (s == t || !(apply && d.K > 0 && d.T > 1)) ? 0 : d.rcount[s];
+      s_cnt[s] = (s == t || !(apply && feedback_on(d))) ? 0 : d.rcount[s];
     block_prefix(s_cnt, s_pre, d.T);  // also orders the barrier set-up
     const int n_other = s_pre[d.T];
 

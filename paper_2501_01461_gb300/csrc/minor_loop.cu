@@ -238,6 +238,7 @@ __device__ __forceinline__ void minor_body(const PlanDev& d, const MinorCfg& c, 
   uint64_t key = d.peak[parity * d.T + t];
   const int64_t budget = d.budget[t];
   const int64_t kmax = (d.K > 0 && (int64_t)d.K < budget) ? (int64_t)d.K : budget;
+  const float level = d.trigger > 0.f ? *(volatile float*)&d.st->level : 0.f;
   if (threadIdx.x == 0) {
     s_abort = 0;
     // the feedback of this round accumulates the tile's next peak here
@@ -256,7 +257,7 @@ __device__ __forceinline__ void minor_body(const PlanDev& d, const MinorCfg& c, 
   int64_t k = 0;
   while (k < kmax && key != 0ull) {
     const float v = key_value(key);
-    if (!(fabsf(v) > d.thr)) break;
+    if (!(fabsf(v) > d.thr) || !(fabsf(v) > level)) break;  // threshold, flux trigger
     const int idx = key_index(key);
     const float f = __fmul_rn(d.gain, v);  // first equation
     const int py = idx / d.nx, px = idx - py * d.nx;
@@ -462,6 +463,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
   uint64_t key = d.peak[parity * d.T + t];
   const int64_t budget = d.budget[t];
   const int64_t kmax = (d.K > 0 && (int64_t)d.K < budget) ? (int64_t)d.K : budget;
+  const float level = d.trigger > 0.f ? *(volatile float*)&d.st->level : 0.f;
   if (threadIdx.x == 0) {
     s_abort = 0;
     s_dead = 0;
@@ -502,7 +504,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
   int64_t k = 0;
   while (k < kmax && key != 0ull) {
     const float v = key_value(key);
-    if (!(fabsf(v) > d.thr)) break;
+    if (!(fabsf(v) > d.thr) || !(fabsf(v) > level)) break;  // threshold, flux trigger
     const int idx = key_index(key);
     const float f = __fmul_rn(d.gain, v);  // first equation
     const int py = idx / d.nx, px = idx - py * d.nx;

@@ -118,6 +118,7 @@ extern "C" CLEAN_API int clean_hogbom_noalloc(const float* d_dirty, const float*
   d.gain = gain;
   d.thr = threshold;
   d.K = 0;
+  d.trigger = 0.f;
   d.cap_round = (int32_t)(niter > 0 ? niter : 1);
   d.budget = reinterpret_cast<int64_t*>(base + kOffBudget);
   d.peak = reinterpret_cast<uint64_t*>(base + kOffPeak);

@@ -8,14 +8,15 @@ import paper_2501_01461_gb300 as cg
 
 def gpu_clean(dirty, psf, gain, niter, threshold=0.0, tiles=(1, 1), K=0, max_rounds=-1,
               mode=cg.TILED, group_ctas=0, group_sync=cg.SYNC_AUTO, feedback_path=0, minor_path=0,
-              feedback_mode=cg.FB_GATHER):
+              feedback_mode=cg.FB_GATHER, trigger=0.0):
     import torch
     d_psf = torch.from_numpy(np.ascontiguousarray(psf, np.float32)).cuda()
     d_dirty = torch.from_numpy(np.ascontiguousarray(dirty, np.float32)).cuda()
     ny, nx = dirty.shape
     with cg.Plan(d_psf, ny, nx, gain=gain, niter=niter, threshold=threshold, tiles=tiles,
                  feedback_interval=K, mode=mode, group_ctas=group_ctas,
-                 group_sync=group_sync, feedback_mode=feedback_mode) as plan:
+                 group_sync=group_sync, feedback_mode=feedback_mode,
+                 feedback_trigger=trigger) as plan:
         if feedback_path:
             plan.debug_set(cg.DEBUG_FEEDBACK_PATH, feedback_path)
         if minor_path:

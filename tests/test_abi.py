@@ -59,7 +59,8 @@ def test_params_check_accepts_valid(lib):
     dict(ny=4, tiles=(5, 1)), dict(feedback_interval=-1), dict(feedback_mode=7),
     dict(mode=3), dict(mode=cg.UNTILED_GRID, tiles=(2, 1)), dict(group_ctas=-2),
     dict(group_sync=9), dict(group_sync=cg.SYNC_CLUSTER, group_ctas=32),
-    dict(ny=50000, nx=50000),
+    dict(ny=50000, nx=50000), dict(feedback_trigger=1.0), dict(feedback_trigger=-0.1),
+    dict(feedback_trigger=float("nan")),
 ])
 def test_params_check_rejects(lib, bad):
     assert lib.clean_params_check(ctypes.byref(_params(**bad))) == 1

@@ -89,3 +89,19 @@ def test_batch_rejects_fft_and_untiled():
         cg.Batch([dict(psf=psf, ny=64, nx=64, niter=10, feedback_mode=cg.FB_FFT)])
     with pytest.raises(cg.CleanError):
         cg.Batch([dict(psf=psf, ny=64, nx=64, niter=10, mode=cg.UNTILED_GRID)])
+
+
+def test_batch_with_flux_trigger_equals_oracle():
+    import torch
+    data = [_job(n, 1.0, 300 + n) for n in (96, 160)]
+    jobs = [dict(psf=torch.from_numpy(p).cuda(), ny=p.shape[0] // 2, nx=p.shape[0] // 2,
+                 gain=0.1, niter=500, threshold=0.0, tiles=(2, 2), feedback_interval=0,
+                 feedback_trigger=0.5) for p, _ in data]
+    with cg.Batch(jobs) as b:
+        b.run([torch.from_numpy(d).cuda() for _, d in data])
+        for i, (psf, dirty) in enumerate(data):
+            o = oracle.clean_f32(dirty, psf, 0.1, 500, 0.0, (2, 2), 0, trigger=0.5)
+            res, mod, comps = b.get(i)
+            assert len(comps) == o.n
+            assert np.array_equal(comps["flux"].view(np.uint32), o.comps["flux"].view(np.uint32))
+            assert np.array_equal(res.cpu().numpy().view(np.uint32), o.residual.view(np.uint32))

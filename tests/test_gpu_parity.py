@@ -275,3 +275,26 @@ def test_plans_with_different_shared_memory_coexist():
     assert np.array_equal(r.cpu().numpy().view(np.uint32), big_ref.residual.view(np.uint32))
     big.close()
     small.close()
+
+
+TRIGGER_CASES = [
+    # (n, tiles, K, niter, threshold, trigger)
+    (128, (2, 2), 0, 600, 1e-3, 0.5),     # rounds end on flux alone
+    (250, (4, 4), 20, 1500, 0.0, 0.3),    # interval and trigger, ragged tiles
+    (512, (2, 2), 0, 800, 0.0, 0.8),      # streamed slabs
+]
+
+
+@pytest.mark.parametrize("case", TRIGGER_CASES, ids=[f"{c[0]}-t{c[1][0]}x{c[1][1]}-K{c[2]}-trig{c[5]}"
+                                                     for c in TRIGGER_CASES])
+def test_flux_trigger_bit_exact(case):
+    """Flux-triggered feedback rounds (Section 3) equal the oracle."""
+    n, tiles, K, niter, thr, trig = case
+    dirty, psf = _inputs(n, n, (2 * n, 2 * n), "sky", n + K)
+    o = oracle.clean_f32(dirty, psf, 0.1, niter, thr, tiles, K, trigger=trig)
+    assert o.rounds > 1
+    g = gpu_clean(dirty, psf, 0.1, niter, thr, tiles, K, trigger=trig)
+    assert_bit_exact(g, o, str(case))
+    g = gpu_clean(dirty, psf, 0.1, niter, thr, tiles, K, trigger=trig, feedback_path=1,
+                  minor_path=1)
+    assert_bit_exact(g, o, str(case) + " plain paths")
