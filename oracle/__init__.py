@@ -58,24 +58,33 @@ def build(force: bool = False) -> str:
     return _SO
 
 
+def load_library(path: str):
+    """ctypes handle of an oracle shared library at `path` (signatures set)."""
+    lib = ctypes.CDLL(path)
+    _declare(lib)
+    return lib
+
+
 def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
-            i32, i64, f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
-            vp = ctypes.c_void_p
-            lib.oracle_clean_f32.restype = i64
-            lib.oracle_clean_f32.argtypes = [vp, i32, i32, vp, i32, i32, f64, i64,
-                                             f64, i32, i32, i32, f64, i32, vp, vp, vp,
-                                             vp, vp, vp, vp, i64, vp]
-            lib.oracle_clean_f64.restype = i64
-            lib.oracle_clean_f64.argtypes = [vp, i32, i32, vp, i32, i32, f64, i64,
-                                             f64, i32, i32, i32, f64, i32, vp, vp, vp,
-                                             vp, i64, vp, vp, vp, vp, vp, vp, vp,
-                                             i64, vp]
-            _lib = lib
+            _lib = load_library(build())
     return _lib
+
+
+def _declare(lib):
+    i32, i64, f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    vp = ctypes.c_void_p
+    lib.oracle_clean_f32.restype = i64
+    lib.oracle_clean_f32.argtypes = [vp, i32, i32, vp, i32, i32, f64, i64,
+                                     f64, i32, i32, i32, f64, i32, vp, vp, vp,
+                                     vp, vp, vp, vp, i64, vp]
+    lib.oracle_clean_f64.restype = i64
+    lib.oracle_clean_f64.argtypes = [vp, i32, i32, vp, i32, i32, f64, i64,
+                                     f64, i32, i32, i32, f64, i32, vp, vp, vp,
+                                     vp, i64, vp, vp, vp, vp, vp, vp, vp,
+                                     i64, vp]
 
 
 def _ptr(a):
@@ -109,8 +118,8 @@ def clean_f64(dirty, psf, gain, niter, threshold=0.0, tiles=(1, 1), K=0,
 
 
 def _run(dtype, dirty, psf, gain, niter, threshold, tiles, K, max_rounds,
-         replay, trigger=0.0):
-    lib = _load()
+         replay, trigger=0.0, lib=None):
+    lib = lib or _load()
     dirty = np.ascontiguousarray(dirty, dtype=np.float32)
     psf = np.ascontiguousarray(psf, dtype=np.float32)
     ny, nx = dirty.shape
