@@ -140,10 +140,33 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def build_inputs(args):
-    w = synth.workload(args.workload, feedback_interval=args.K)
+def rank_workload(name: str, K: int, rank: int):
+    """The workload a rank deconvolves: the same PSF and sizes on every rank,
+    its own sky (seed offset by the rank), so the ranks solve independent
+    problems.  Rank 0's image is the single-GPU one."""
+    import dataclasses
+    w = synth.workload(name, feedback_interval=K)
+    return dataclasses.replace(w, seed=w.seed + 7919 * rank) if rank else w
+
+
+def build_inputs(args, rank: int = 0):
+    w = rank_workload(args.workload, args.K, rank)
     data = w.build(threshold=0.0)
     return w, data
+
+
+def aggregate(dist, ms: float, units: float, device=None):
+    """Whole-job figures over the ranks: the slowest rank's time (max) and
+    the units all ranks processed (sum).  dist is torch.distributed or None
+    (one process)."""
+    if dist is None:
+        return float(ms), float(units)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
 
 
 def minor_bytes_per_run(w) -> int:
@@ -370,7 +393,7 @@ def main():
         dist.init_process_group("nccl")
     cg.lib()
 
-    w, data = build_inputs(args)
+    w, data = build_inputs(args, rank)
     psf, dirty = data["psf"], data["dirty"]
     d_psf = torch.from_numpy(psf).cuda()
     d_dirty = torch.from_numpy(dirty).cuda()
@@ -405,12 +428,8 @@ def main():
     st = plan.stats()
     gpu_launches = st["kernel_launches"] - launches0
     n_comp = plan.n_components()
-    total_ms = float(sum(step_ms))
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * n_comp * args.steps / (total_ms / 1e3)
+    total_ms, all_comp = aggregate(dist, float(sum(step_ms)), n_comp * args.steps, "cuda")
+    value = all_comp / (total_ms / 1e3)
 
     # ---- roofline of the dominant kernel ----
     peaks, peak_src = measured_peaks()
@@ -484,13 +503,15 @@ def main():
         for _ in range(max(1, args.warmup)):
             host_step()
         torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
         t0 = time.perf_counter()
         ne = 0
         for _ in range(args.steps):
             ne += host_step()
-        te = time.perf_counter() - t0
+        te_ms, ne = aggregate(dist, (time.perf_counter() - t0) * 1e3, ne, "cuda")
         hp.close()
-        e2e = {"value": world * ne / te, "unit": UNIT,
+        e2e = {"value": ne / (te_ms / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": int(dirty.nbytes + psf.nbytes),
                "d2h_bytes_per_step": int(2 * dirty.nbytes + 16 * w.niter)}
 
