@@ -332,7 +332,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 // expires stops working but keeps joining the group exchange, so every CTA
 // of a cluster executes the same barriers.
 // ---------------------------------------------------------------------------
-constexpr int kPipeConsumers = 512;
+// 15 consumer warps + the producer: 4 warps per scheduler, so up to 128
+// registers a thread
+constexpr int kPipeConsumers = 480;
 constexpr int kPipeThreads = kPipeConsumers + 32;
 constexpr int kPipeMaxStages = 8;
 
@@ -372,55 +374,90 @@ __device__ __forceinline__ void take_peak(float r, int idx, float& best_a, int& 
   }
 }
 
-// PSF values for pixels 4g .. 4g+3 of a staged row whose first pixel sits
-// OFF floats into the 16-byte-aligned row: two aligned 16-byte loads and a
-// fixed shift (consecutive lanes read consecutive 16 bytes: no bank
-// conflicts).
-template <int OFF>
-__device__ __forceinline__ float4 psf4(const float4* rowP4, int g) {
-  const float4 a = rowP4[g];
-  if (OFF == 0) return a;
-  const float4 b = rowP4[g + 1];
-  if (OFF == 1) return make_float4(a.y, a.z, a.w, b.x);
-  if (OFF == 2) return make_float4(a.z, a.w, b.x, b.y);
-  return make_float4(a.w, b.x, b.y, b.z);
-}
+// Vector path over one chunk.  The chunk's rows form slabs of 32 / LPR rows
+// (LPR = 1 << lpr_log2 lanes per row, 4 pixels per lane, so a slab row is
+// CW = 4 LPR pixels wide); slab s goes to consumer warp (s + rot) mod 15,
+// continuing the round-robin of the previous chunk so the warps stay
+// balanced across a ragged last slab.  Each warp step loads kSlabUnroll
+// slabs' residual and PSF vectors before any arithmetic, then subtracts and
+// stores (global or the resident slab).  The step has no branches: rows past
+// the chunk are read from a valid staged row and masked.  The peak is kept
+// per 4-pixel group: the largest group maximum |R|, ties to the lower group
+// base index.  Groups are aligned runs of 4 pixels of one row, so the lowest
+// index holding the largest |R| lies in that group; resolve_group() finds it
+// once per iteration.
+constexpr int kSlabUnroll = 4;
 
-// Vector path over one chunk for this thread: rows r0 + vrow, + rpp4, ...;
-// 4-pixel groups vcol, + tpr4, ...  Subtracts, stores (global or resident
-// slab) and keeps the peak.
 template <bool RES, int OFF>
-__device__ __forceinline__ void chunk_vec(const PlanDev& d, float* sRes, int WR, int ya,
-                                          const float* stgR, const float* stgP, int BW,
-                                          int r0, int r1, int c0, int c1, int x0, float f,
-                                          int vrow, int rpp4, int vcol, int tpr4,
-                                          float& best_a, int& best_i, float& best_v) {
-  for (int y = r0 + vrow; y < r1; y += rpp4) {
-    const float4* rowP4 = reinterpret_cast<const float4*>(stgP + (y - r0) * BW);
-    float4* rowR4 = RES ? reinterpret_cast<float4*>(sRes + (y - ya) * WR + (c0 - x0))
-                        : reinterpret_cast<float4*>(const_cast<float*>(stgR) + (y - r0) * BW);
-    float4* gR4 = reinterpret_cast<float4*>(d.R + (int64_t)y * d.nx + c0);
-    for (int g = vcol; 4 * g < c1 - c0; g += tpr4) {
-      float4 r = rowR4[g];
-      const float4 p = psf4<OFF>(rowP4, g);
+__device__ __forceinline__ void chunk_slabs(const PlanDev& d, float* sRes, int WR, int ya,
+                                            const float* stgR, const float* stgP, int BW,
+                                            int r0, int r1, int c0, int c1, int x0, float f,
+                                            int lpr_log2, int s_first, float& best_a,
+                                            int& best_base) {
+  constexpr int kWarps = kPipeConsumers / 32;
+  const int lane = threadIdx.x & 31;
+  const int g = lane & ((1 << lpr_log2) - 1);
+  const int rps = 32 >> lpr_log2;  // rows per slab
+  const int sub = lane >> lpr_log2;
+  const int x = c0 + 4 * g;
+  if (x >= c1) return;
+  const int nslabs = (r1 - r0 + rps - 1) / rps;
+  for (int s = s_first; s < nslabs; s += kSlabUnroll * kWarps) {
+    float4 rv[kSlabUnroll], pa[kSlabUnroll], pb[kSlabUnroll];
+#pragma unroll
+    for (int u = 0; u < kSlabUnroll; ++u) {
+      const int y = r0 + (s + u * kWarps) * rps + sub;
+      const int ly = y < r1 ? y - r0 : 0;  // masked rows read staged row 0
+      const float4* rowP4 = reinterpret_cast<const float4*>(stgP + ly * BW);
+      pa[u] = rowP4[g];
+      if (OFF != 0) pb[u] = rowP4[g + 1];
+      rv[u] = RES ? *reinterpret_cast<const float4*>(sRes + (r0 + ly - ya) * WR + (x - x0))
+                  : reinterpret_cast<const float4*>(stgR + ly * BW)[g];
+    }
+#pragma unroll
+    for (int u = 0; u < kSlabUnroll; ++u) {
+      const int y = r0 + (s + u * kWarps) * rps + sub;
+      const bool valid = y < r1;
+      const float4 a = pa[u];
+      float4 p;
+      if (OFF == 0) {
+        p = a;
+      } else {
+        const float4 b = pb[u];
+        p = OFF == 1 ? make_float4(a.y, a.z, a.w, b.x)
+                     : OFF == 2 ? make_float4(a.z, a.w, b.x, b.y) : make_float4(a.w, b.x, b.y, b.z);
+      }
+      float4 r = rv[u];
       fms2(r.x, r.y, p.x, p.y, f);
       fms2(r.z, r.w, p.z, p.w, f);
-      if (RES)
-        rowR4[g] = r;
-      else
-        gR4[g] = r;
-      const float m = fmaxf(fmaxf(fabsf(r.x), fabsf(r.y)), fmaxf(fabsf(r.z), fabsf(r.w)));
-      const int base = y * d.nx + c0 + 4 * g;
-      if (m > best_a || (m == best_a && base < best_i)) {
-        const int k4 = fabsf(r.x) == m ? 0 : fabsf(r.y) == m ? 1 : fabsf(r.z) == m ? 2 : 3;
-        if (m > best_a || base + k4 < best_i) {
-          best_a = m;
-          best_i = base + k4;
-          best_v = k4 == 0 ? r.x : k4 == 1 ? r.y : k4 == 2 ? r.z : r.w;
-        }
+      if (valid) {
+        if (RES)
+          *reinterpret_cast<float4*>(sRes + (y - ya) * WR + (x - x0)) = r;
+        else
+          *reinterpret_cast<float4*>(d.R + (int64_t)y * d.nx + x) = r;
       }
+      const float m0 = fmaxf(fmaxf(fabsf(r.x), fabsf(r.y)), fmaxf(fabsf(r.z), fabsf(r.w)));
+      const float m = valid ? m0 : -1.f;
+      const int base = y * d.nx + x;
+      const bool better = m > best_a || (m == best_a && base < best_base);
+      best_a = better ? m : best_a;
+      best_base = better ? base : best_base;
     }
   }
+}
+
+// The pixel of the best 4-pixel group that holds |R| = best_a first (lowest
+// index), and its signed value, read back from where this thread stored it.
+template <bool RES>
+__device__ __forceinline__ void resolve_group(const PlanDev& d, const float* sRes, int WR,
+                                              int ya, int x0, float best_a, int base,
+                                              int& best_i, float& best_v) {
+  const int y = base / d.nx, x = base - y * d.nx;
+  const float4 r = RES ? *reinterpret_cast<const float4*>(sRes + (y - ya) * WR + (x - x0))
+                       : *reinterpret_cast<const float4*>(d.R + (int64_t)y * d.nx + x);
+  const int k4 = fabsf(r.x) == best_a ? 0 : fabsf(r.y) == best_a ? 1 : fabsf(r.z) == best_a ? 2 : 3;
+  best_i = base + k4;
+  best_v = k4 == 0 ? r.x : k4 == 1 ? r.y : k4 == 2 ? r.z : r.w;
 }
 
 template <int SYNC, bool RES>
@@ -487,20 +524,24 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
   }
   __syncthreads();
 
-  // consumer geometry within a chunk: 4-pixel groups (vector path) or single
-  // pixels, threads per row a power of two
-  const bool vec_cols = (x0 % 4) == 0 && (W % 4) == 0 && (CW % 4) == 0;
-  int tpr4 = 1;
-  while (tpr4 < CW / 4 && tpr4 < kPipeConsumers) tpr4 <<= 1;
-  const int rpp4 = kPipeConsumers / tpr4;
-  const int vrow = threadIdx.x / tpr4, vcol = threadIdx.x % tpr4;
+  // consumer geometry within a chunk: row slabs of 4-pixel groups (vector
+  // path, CW = 32, 64 or 128) or single pixels, threads per row a power of two
+  const bool vec_cols = (x0 % 4) == 0 && (W % 4) == 0 && (CW == 32 || CW == 64 || CW == 128);
+  const int lpr_log2 = CW == 128 ? 5 : CW == 64 ? 4 : 3;
+  const int slabs = (BH + (32 >> lpr_log2) - 1) / (32 >> lpr_log2);  // per full chunk
   int tpr = 1;
   while (tpr < CW && tpr < kPipeConsumers) tpr <<= 1;
   const int rpp = kPipeConsumers / tpr;
   const int crow = threadIdx.x / tpr, ccol = threadIdx.x % tpr;
 
-  int64_t gchunk = 0;  // ring position: chunks of all earlier iterations
-  int64_t jnext = 0;   // producer: next chunk to issue
+  // ring state, advanced chunk by chunk (no division in the loop): the
+  // producer's next stage and phase, the consumers' likewise, and the slab
+  // rotation of the consumers
+  constexpr int kW = kPipeConsumers / 32;
+  const int rot_step = slabs % kW;
+  int p_st = 0, c_st = 0, rot = 0;
+  uint32_t p_ph = 0, c_ph = 0;
+  int64_t jnext = 0;   // producer: chunks issued so far
   int64_t k = 0;
   while (k < kmax && key != 0ull) {
     const float v = key_value(key);
@@ -527,55 +568,73 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
     int best_i = 0x7fffffff;
     if (producer) {
       if (lane == 0) {
+        int rb = 0, cb = 0;
         for (int ch = 0; ch < nch && !*(volatile int*)&s_dead; ++ch) {
-          const int64_t j = gchunk + ch;
-          const int st = (int)(j % S);
-          if (j >= S && !pipe_wait(&empty_bar[st], (uint32_t)((j / S) - 1) & 1u, limit, &s_dead,
-                                   &d.st->status))
+          if (jnext >= S && !pipe_wait(&empty_bar[p_st], p_ph ^ 1u, limit, &s_dead,
+                                       &d.st->status))
             break;
-          const int r0 = ya + (ch / ncb) * BH, c0 = x0 + (ch % ncb) * CW;
-          float* stg = sStage + (size_t)st * stage_floats;
-          ptx::mbar_arrive_expect_tx(&full_bar[st], stage_bytes);
-          if (!RES) ptx::tma_load_2d(stg, &r_map, c0 & ~3, r0, &full_bar[st]);
+          const int r0 = ya + rb * BH, c0 = x0 + cb * CW;
+          float* stg = sStage + (size_t)p_st * stage_floats;
+          ptx::mbar_arrive_expect_tx(&full_bar[p_st], stage_bytes);
+          if (!RES) ptx::tma_load_2d(stg, &r_map, c0 & ~3, r0, &full_bar[p_st]);
           ptx::tma_load_2d(stg + (RES ? 0 : box_floats), &p_map, (c0 + dx) & ~3, r0 + dy,
-                           &full_bar[st]);
-          jnext = j + 1;
+                           &full_bar[p_st]);
+          ++jnext;
+          if (++p_st == S) {
+            p_st = 0;
+            p_ph ^= 1u;
+          }
+          if (++cb == ncb) {
+            cb = 0;
+            ++rb;
+          }
         }
       }
     } else {
+      int best_base = 0x7fffffff;
+      int rb = 0, cb = 0;
       for (int ch = 0; ch < nch; ++ch) {
-        const int64_t j = gchunk + ch;
-        const int st = (int)(j % S);
+        const int st = c_st;
         if (*(volatile int*)&s_dead ||
-            !pipe_wait(&full_bar[st], (uint32_t)(j / S) & 1u, limit, &s_dead, &d.st->status))
+            !pipe_wait(&full_bar[st], c_ph, limit, &s_dead, &d.st->status))
           break;
-        const int r0 = ya + (ch / ncb) * BH, r1 = min(yb, r0 + BH);
-        const int c0 = x0 + (ch % ncb) * CW, c1 = min(x1, c0 + CW);
+        if (++c_st == S) {
+          c_st = 0;
+          c_ph ^= 1u;
+        }
+        const int r0 = ya + rb * BH, r1 = min(yb, r0 + BH);
+        const int c0 = x0 + cb * CW, c1 = min(x1, c0 + CW);
+        if (++cb == ncb) {
+          cb = 0;
+          ++rb;
+        }
         const float* stg = sStage + (size_t)st * stage_floats;
         const float* stgR = stg;                            // streamed residual box
         const float* stgP = stg + (RES ? 0 : box_floats);   // PSF box
         const int offR = c0 - (c0 & ~3), offP = (c0 + dx) - ((c0 + dx) & ~3);
         if (fast) {
+          // continue the slab round-robin where the previous chunk ended
+          const int s_first = warp >= rot ? warp - rot : warp + kW - rot;
           switch (offP) {
             case 0:
-              chunk_vec<RES, 0>(d, sRes, WR, ya, stgR, stgP, BW, r0, r1, c0, c1, x0, f, vrow,
-                                rpp4, vcol, tpr4, best_a, best_i, best_v);
+              chunk_slabs<RES, 0>(d, sRes, WR, ya, stgR, stgP, BW, r0, r1, c0, c1, x0, f,
+                                  lpr_log2, s_first, best_a, best_base);
               break;
             case 1:
-              chunk_vec<RES, 1>(d, sRes, WR, ya, stgR, stgP, BW, r0, r1, c0, c1, x0, f, vrow,
-                                rpp4, vcol, tpr4, best_a, best_i, best_v);
+              chunk_slabs<RES, 1>(d, sRes, WR, ya, stgR, stgP, BW, r0, r1, c0, c1, x0, f,
+                                  lpr_log2, s_first, best_a, best_base);
               break;
             case 2:
-              chunk_vec<RES, 2>(d, sRes, WR, ya, stgR, stgP, BW, r0, r1, c0, c1, x0, f, vrow,
-                                rpp4, vcol, tpr4, best_a, best_i, best_v);
+              chunk_slabs<RES, 2>(d, sRes, WR, ya, stgR, stgP, BW, r0, r1, c0, c1, x0, f,
+                                  lpr_log2, s_first, best_a, best_base);
               break;
             default:
-              chunk_vec<RES, 3>(d, sRes, WR, ya, stgR, stgP, BW, r0, r1, c0, c1, x0, f, vrow,
-                                rpp4, vcol, tpr4, best_a, best_i, best_v);
+              chunk_slabs<RES, 3>(d, sRes, WR, ya, stgR, stgP, BW, r0, r1, c0, c1, x0, f,
+                                  lpr_log2, s_first, best_a, best_base);
               break;
           }
         } else {
-          for (int y = r0 + crow; y < r1; y += rpp) {
+          for (int y = r0 + crow; crow < rpp && y < r1; y += rpp) {
             const bool yin = (unsigned)(y + dy) < (unsigned)d.pny;
             const float* rowP = stgP + (y - r0) * BW + offP - c0;  // index by x
             const float* rowR = stgR + (y - r0) * BW + offR - c0;  // index by x (streamed)
@@ -592,14 +651,17 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
             }
           }
         }
+        rot += rot_step;
+        if (rot >= kW) rot -= kW;
         __syncwarp();
         if (lane == 0) ptx::mbar_arrive(&empty_bar[st]);
       }
+      if (fast && best_a >= 0.f)
+        resolve_group<RES>(d, sRes, WR, ya, x0, best_a, best_base, best_i, best_v);
       // residual rows written through the generic proxy are read back by TMA
       // (async proxy) in the next iteration
       if (!RES) asm volatile("fence.proxy.async.global;" ::: "memory");
     }
-    gchunk += nch;
     uint64_t mine = (best_a >= 0.f) ? make_key(best_v, best_i) : 0ull;
     mine = block_max_key(mine, s_warp);
     key = exchange_keys<SYNC>(d, c, t, rank, k, mine, s_part, &s_best, &s_abort);
@@ -739,12 +801,16 @@ bool minor_pipe_geometry(MinorCfg& c, int max_rows, int max_w, int chunk_px, int
   // busy; streamed slabs take 8192-pixel chunks, resident ones 4096
   if (chunk_px <= 0) chunk_px = c.resident ? 4096 : 8192;
   if (max_stages <= 0 || max_stages > kPipeMaxStages) max_stages = kPipeMaxStages;
-  // columns: the tile width split into equal blocks of at most 252 (the box,
-  // 4 floats wider, stays within TMA's 256); rows: up to the CTA's row count
-  const int nblk = (max_w + 251) / 252;
-  c.chunk_w = ((max_w + nblk - 1) / nblk + 3) & ~3;
-  c.box_w = c.chunk_w + 4;                       // covers any 4-float misalignment
-  c.chunk_h = std::max(1, std::min(std::min(256, max_rows), chunk_px / c.chunk_w));
+  // columns: 128 (one warp per row, 4 pixels per lane), or 64 / 32 for narrow
+  // tiles; the box is 4 floats wider to cover any misalignment of the PSF
+  // window; rows: up to the CTA's row count
+  c.chunk_w = max_w > 64 ? 128 : max_w > 32 ? 64 : 32;
+  c.box_w = c.chunk_w + 4;
+  // rows: a whole number of warp steps (15 warps x kSlabUnroll slabs of
+  // 128 / CW rows), so every consumer warp gets the same share of a chunk
+  const int unit = (kPipeConsumers / 32) * kSlabUnroll * (128 / c.chunk_w);
+  const int h = std::max(unit, (chunk_px / c.chunk_w) / unit * unit);
+  c.chunk_h = std::max(1, std::min(std::min(256, max_rows), h));
   const int64_t stage = (int64_t)(c.resident ? 1 : 2) * ((c.box_w * c.chunk_h + 31) & ~31) * 4;
   c.res_floats = c.resident ? max_rows * ((max_w + 3) & ~3) : 0;
   c.res_floats = (c.res_floats + 31) & ~31;  // keep the stages 128-byte aligned

@@ -108,6 +108,9 @@ MINOR_CASES = [
     (96, 160, (64, 80), (2, 2), 5, 400, 2, cg.SYNC_CLUSTER),     # clipped PSF rows/columns
     (1024, 1024, (2048, 2048), (2, 2), 20, 600, 1, cg.SYNC_CLUSTER),  # streamed slabs
     (300, 600, (600, 1200), (1, 1), 0, 500, 16, cg.SYNC_GRID),   # untiled-style group
+    (96, 96, (192, 192), (3, 3), 6, 500, 2, cg.SYNC_GRID),       # 32-pixel-wide tiles
+    (90, 152, (180, 304), (2, 3), 4, 400, 2, cg.SYNC_CLUSTER),   # 50-51 wide: per-pixel path
+    (520, 1000, (1040, 2000), (1, 2), 13, 400, 3, cg.SYNC_GRID), # ragged 128-column chunks
 ]
 
 
