@@ -348,7 +348,8 @@ CLEAN_API const char* clean_strerror(int status);
  *   CLEAN_DEBUG_FEEDBACK_PATH  feedback kernel: 0 automatic (TMA when the
  *                              PSF is 16-byte aligned with a row pitch that is
  *                              a multiple of 4 floats), 1 plain loads, 2 TMA
- *                              when possible (same results, bit for bit)
+ *                              when possible, 3 pipelined global loads (same
+ *                              results, bit for bit)
  *   CLEAN_DEBUG_MINOR_PATH     minor-loop kernel: 0 automatic (bulk-copy
  *                              pipeline when image and PSF rows are 16-byte
  *                              aligned), 1 plain loads, 2 pipeline when

@@ -249,10 +249,12 @@ int launch_round_feedback(clean_plan_s* pl, cudaStream_t s) {
     ++pl->rounds_launched;
     return CLEAN_OK;
   }
-  const bool use_tma = pl->psf_map_ok && pl->feedback_path != 1;
+  const bool use_tma = pl->psf_map_ok && pl->feedback_path != 1 && pl->feedback_path != 3;
   const int ev = timed_begin(pl, 1, s);
-  cudaError_t e = launch_feedback(pl->d, use_tma ? &pl->psf_map : nullptr, pl->parity, apply,
-                                  (uint64_t)pl->mc.spin_limit_ns, s);
+  cudaError_t e = pl->feedback_path == 3
+                      ? launch_feedback_ldg(pl->d, pl->parity, apply, s)
+                      : launch_feedback(pl->d, use_tma ? &pl->psf_map : nullptr, pl->parity,
+                                        apply, (uint64_t)pl->mc.spin_limit_ns, s);
   timed_end(pl, ev, s);
   ++pl->kernel_launches;
   if (e != cudaSuccess) return cuda_fail(pl, e);
@@ -829,7 +831,8 @@ int clean_stats(clean_plan_t pl, clean_stats_t* out, void* stream) {
   out->resident = pipe ? pl->mc_pipe.resident : pl->mc.resident;
   out->minor_pipe = pipe ? 1 : 0;
   out->feedback_mode = pl->fft ? CLEAN_FB_FFT : CLEAN_FB_GATHER;
-  out->feedback_tma = (pl->psf_map_ok && pl->feedback_path != 1) ? 1 : 0;
+  out->feedback_tma =
+      (pl->psf_map_ok && pl->feedback_path != 1 && pl->feedback_path != 3) ? 1 : 0;
   out->sm_count = pl->sm_count;
   out->rounds_launched = pl->rounds_launched;
   out->kernel_launches = pl->kernel_launches;
@@ -887,7 +890,7 @@ int clean_debug_set(clean_plan_t pl, int32_t what, int64_t value) {
       return CLEAN_OK;
     }
     case CLEAN_DEBUG_FEEDBACK_PATH:
-      if (value < 0 || value > 2) return CLEAN_ERR_INVALID_ARG;
+      if (value < 0 || value > 3) return CLEAN_ERR_INVALID_ARG;
       pl->feedback_path = (int)value;
       return CLEAN_OK;
     case CLEAN_DEBUG_TIMING:

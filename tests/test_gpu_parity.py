@@ -239,19 +239,21 @@ FB_CASES = [
     (130, 200, (100, 120), (3, 2), 6, 400),     # PSF smaller than the image: clipped windows
     (256, 256, (512, 512), (2, 2), 300, 1200),  # more components than one staged chunk
     (300, 260, (600, 520), (5, 3), 40, 3000),
+    (256, 256, (512, 512), (3, 3), 200, 3600),  # more than 1024 components a round
 ]
 
 
 @pytest.mark.parametrize("case", FB_CASES, ids=[f"{c[0]}x{c[1]}-psf{c[2][0]}x{c[2][1]}-t{c[3][0]}x{c[3][1]}-K{c[4]}"
                                                 for c in FB_CASES])
 def test_feedback_paths_bit_exact(case):
-    """Plain-load and TMA feedback kernels give the oracle's bits."""
+    """Plain-load, TMA and pipelined-load feedback kernels give the oracle's
+    bits."""
     ny, nx, ps, tiles, K, niter = case
     rng = np.random.default_rng(sum(case[:2]))
     psf = synth.make_psf(*ps) if ps[0] >= 2 * ny else synth.random_psf(*ps, rng)
     dirty = synth.random_image(ny, nx, rng)
     o = oracle.clean_f32(dirty, psf, 0.1, niter, 0.0, tiles, K)
-    for path in (1, 2):
+    for path in (1, 2, 3):
         g = gpu_clean(dirty, psf, 0.1, niter, 0.0, tiles, K, feedback_path=path)
         assert g["stats"]["feedback_tma"] == (1 if path == 2 else 0)
         assert_bit_exact(g, o, f"{case} path={path}")
