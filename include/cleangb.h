@@ -132,6 +132,7 @@ typedef struct {
   int64_t feedback_launches; /* feedback launches timed (CLEAN_DEBUG_TIMING) */
   double minor_ms;           /* summed CUDA-event time of the timed minor launches */
   double feedback_ms;        /* summed CUDA-event time of the timed feedback launches */
+  int64_t graph_launches;    /* two-round CUDA graphs launched (CLEAN_DEBUG_GRAPHS) */
 } clean_stats_t;
 
 /* Fills *p with defaults: gain 0.1, threshold 0, 1 x 1 tiles, K 0, gather
@@ -285,6 +286,13 @@ CLEAN_API int clean_batch_get(clean_batch_t b, int32_t i, float* d_residual, flo
 CLEAN_API int clean_batch_stats(clean_batch_t b, int64_t* rounds_launched,
                                 int64_t* kernel_launches, int64_t* n_components);
 
+/* Round replay from CUDA graphs (on by default): each run of two rounds is
+ * one launch of a graph captured after the work lists last changed; results
+ * are identical either way.  enable: 1 on, 0 off, -1 leave as is.
+ * *graph_launches (may be NULL) receives the graph launches so far.  This
+ * is a launch mechanism of this library; the paper has no counterpart. */
+CLEAN_API int clean_batch_graphs(clean_batch_t b, int32_t enable, int64_t* graph_launches);
+
 /* Frees the batch and its images' state (not the borrowed PSFs). */
 CLEAN_API void clean_batch_destroy(clean_batch_t b);
 
@@ -350,6 +358,11 @@ CLEAN_API const char* clean_strerror(int status);
  *                              a multiple of 4 floats), 1 plain loads, 2 TMA
  *                              when possible, 3 pipelined global loads (same
  *                              results, bit for bit)
+ *   CLEAN_DEBUG_GRAPHS         1 (default): clean_run replays each two rounds
+ *                              from a CUDA graph captured once per launch
+ *                              configuration (not while timing, not for the
+ *                              FFT feedback); 0: launch every kernel directly.
+ *                              Same results, bit for bit.
  *   CLEAN_DEBUG_MINOR_PATH     minor-loop kernel: 0 automatic (bulk-copy
  *                              pipeline when image and PSF rows are 16-byte
  *                              aligned), 1 plain loads, 2 pipeline when
@@ -372,7 +385,8 @@ enum {
   CLEAN_DEBUG_FEEDBACK_PATH = 4,
   CLEAN_DEBUG_MINOR_PATH = 5,
   CLEAN_DEBUG_PIPE_CHUNK_PX = 6,
-  CLEAN_DEBUG_PIPE_STAGES = 7
+  CLEAN_DEBUG_PIPE_STAGES = 7,
+  CLEAN_DEBUG_GRAPHS = 8
 };
 CLEAN_API int clean_debug_set(clean_plan_t plan, int32_t what, int64_t value);
 CLEAN_API void clean_debug_alloc_limit(int64_t bytes);

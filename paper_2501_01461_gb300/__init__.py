@@ -23,7 +23,7 @@ __all__ = ["CleanError", "Plan", "Batch", "lib", "library_path", "build", "STATU
            "FB_GATHER", "FB_FFT", "FB_AUTO", "TILED", "UNTILED_GRID",
            "SYNC_AUTO", "SYNC_CLUSTER", "SYNC_GRID", "COMPONENT_DTYPE",
            "DEBUG_SPIN_LIMIT_NS", "DEBUG_FORCE_TIMEOUT", "DEBUG_TIMING", "DEBUG_FEEDBACK_PATH", "DEBUG_MINOR_PATH",
-           "DEBUG_PIPE_CHUNK_PX", "DEBUG_PIPE_STAGES",
+           "DEBUG_PIPE_CHUNK_PX", "DEBUG_PIPE_STAGES", "DEBUG_GRAPHS",
            "EXPORTED_SYMBOLS"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -32,6 +32,7 @@ TILED, UNTILED_GRID = 0, 1
 SYNC_AUTO, SYNC_CLUSTER, SYNC_GRID = 0, 1, 2
 DEBUG_SPIN_LIMIT_NS, DEBUG_FORCE_TIMEOUT, DEBUG_TIMING = 1, 2, 3
 DEBUG_FEEDBACK_PATH, DEBUG_MINOR_PATH, DEBUG_PIPE_CHUNK_PX, DEBUG_PIPE_STAGES = 4, 5, 6, 7
+DEBUG_GRAPHS = 8
 STATUS = {0: "CLEAN_OK", 1: "CLEAN_ERR_INVALID_ARG", 2: "CLEAN_ERR_NONFINITE",
           3: "CLEAN_ERR_OOM", 4: "CLEAN_ERR_CUDA", 5: "CLEAN_ERR_TIMEOUT",
           6: "CLEAN_ERR_UNSUPPORTED"}
@@ -65,7 +66,8 @@ class Stats(ctypes.Structure):
                 ("feedback_tma", ctypes.c_int32), ("minor_pipe", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("kernel_launches", ctypes.c_int64),
                 ("minor_launches", ctypes.c_int64), ("feedback_launches", ctypes.c_int64),
-                ("minor_ms", ctypes.c_double), ("feedback_ms", ctypes.c_double)]
+                ("minor_ms", ctypes.c_double), ("feedback_ms", ctypes.c_double),
+                ("graph_launches", ctypes.c_int64)]
 
 
 # name -> (restype, argtypes); the C ABI of include/cleangb.h
@@ -93,6 +95,7 @@ _SIGS = {
     "clean_batch_run": (ctypes.c_int, [_vp, _vp, _i32, _vp]),
     "clean_batch_get": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp, _i64, _vp, _vp]),
     "clean_batch_stats": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "clean_batch_graphs": (ctypes.c_int, [_vp, _i32, _vp]),
     "clean_batch_destroy": (None, [_vp]),
     "clean_server_create": (ctypes.c_int, [_vp, _i32, _vp]),
     "clean_server_add": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
@@ -392,6 +395,14 @@ class Batch:
         arr["y"], arr["x"], arr["tile"] = host[:, 0], host[:, 1], host[:, 3]
         arr["flux"] = host[:, 2].view(np.float32)
         return res, mod, arr
+
+    def graphs(self, enable=None) -> int:
+        """Turns CUDA-graph round replay on or off (None: leave as is);
+        returns the number of graph launches so far."""
+        n = ctypes.c_int64(0)
+        e = -1 if enable is None else int(bool(enable))
+        _check(lib().clean_batch_graphs(self._h, e, ctypes.byref(n)), "clean_batch_graphs")
+        return int(n.value)
 
     def stats(self):
         r, k, c = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)

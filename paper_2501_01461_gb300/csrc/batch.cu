@@ -9,6 +9,14 @@
 // peaks and component list, so its results are bit for bit those of its own
 // clean_plan + clean_run.  Images that finish leave the work lists; new ones
 // join between rounds.
+//
+// Rounds are replayed from CUDA graphs: after each rebuild of the work lists
+// the launches of two consecutive rounds are captured once per starting
+// round parity (kernels only use the round's parity relative to each image's
+// first round), and a run of n rounds becomes n / 2 graph launches plus at
+// most one directly launched round.  Rounds past an image's end are no-ops,
+// so the host can launch an upper bound of rounds between reads.  If the
+// capture is refused the engine launches the kernels directly.
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -59,6 +67,13 @@ struct clean_engine_s {
   int64_t next_id = 1;
   int poisoned = CLEAN_OK;
   int64_t rounds_launched = 0, kernel_launches = 0;
+  // CUDA graphs of two rounds, indexed by the parity of the first round
+  cudaStream_t cap_stream = nullptr;    // private stream used only for capture
+  cudaGraphExec_t pair[2] = {nullptr, nullptr};
+  int pair_kernels = 0;                 // kernels in one pair graph
+  bool use_graphs = true;
+  bool graphs_refused = false;
+  int64_t graph_launches = 0;
 };
 
 namespace {
@@ -69,9 +84,19 @@ int eng_fail(clean_engine_s* e, int code) {
   return e->poisoned;
 }
 
+void drop_graphs(clean_engine_s* e) {
+  for (cudaGraphExec_t& g : e->pair)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+}
+
 void engine_free(clean_engine_s* e) {
   if (!e) return;
   cudaDeviceSynchronize();
+  drop_graphs(e);
+  if (e->cap_stream) cudaStreamDestroy(e->cap_stream);
   for (Job& j : e->jobs) clean_destroy(j.plan);
   cudaFree(e->d_states);
   cudaFree(e->d_plans);
@@ -259,6 +284,7 @@ int engine_rebuild(clean_engine_s* e, cudaStream_t s) {
   // the host vectors die here: make the copies complete first
   if (err == cudaSuccess) err = cudaStreamSynchronize(s);
   if (err != cudaSuccess) return eng_fail(e, CLEAN_ERR_CUDA);
+  drop_graphs(e);  // the captured launches name the old work lists
   e->dirty = false;
   return CLEAN_OK;
 }
@@ -290,29 +316,79 @@ int engine_mark(clean_engine_s* e) {
 }
 
 // Launches `rounds` rounds of every unfinished job.
+// The kernels of one round (round index `round`) on stream s; *n counts them.
+cudaError_t launch_round(clean_engine_s* e, int round, cudaStream_t s, int* n) {
+  cudaError_t err = cudaSuccess;
+  for (const Group& g : e->groups) {
+    err = launch_minor_batch(e->d_plans, e->d_items + g.offset, g.count, g.G, g.resident,
+                             g.smem, round, s);
+    ++*n;
+    if (err != cudaSuccess) return err;
+  }
+  if (e->blocks_tma > 0) {
+    err = launch_feedback_batch(e->d_plans, e->d_imgs, e->n_tma, e->blocks_tma, e->max_T,
+                                e->d_maps, round, 1, 2000000000ull, s);
+    ++*n;
+    if (err != cudaSuccess) return err;
+  }
+  if (e->blocks_plain > 0) {
+    err = launch_feedback_batch(e->d_plans + e->n_tma, e->d_imgs + e->n_tma,
+                                e->n_work - e->n_tma, e->blocks_plain, e->max_T, nullptr,
+                                round, 1, 2000000000ull, s);
+    ++*n;
+  }
+  return err;
+}
+
+// Captures two rounds starting at a round of parity `par` into e->pair[par].
+// Returns false (and leaves no capture open) if the runtime refuses.
+bool capture_pair(clean_engine_s* e, int par) {
+  if (!e->cap_stream &&
+      cudaStreamCreateWithFlags(&e->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  cudaGraph_t graph = nullptr;
+  int n = 0;
+  cudaError_t err = cudaStreamBeginCapture(e->cap_stream, cudaStreamCaptureModeRelaxed);
+  if (err == cudaSuccess) {
+    cudaError_t l = launch_round(e, par, e->cap_stream, &n);
+    if (l == cudaSuccess) l = launch_round(e, par + 1, e->cap_stream, &n);
+    err = cudaStreamEndCapture(e->cap_stream, &graph);
+    if (l != cudaSuccess) err = l;
+  }
+  if (err == cudaSuccess) err = cudaGraphInstantiate(&e->pair[par], graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (err != cudaSuccess) {
+    e->pair[par] = nullptr;
+    cudaGetLastError();
+    return false;
+  }
+  e->pair_kernels = n;
+  return true;
+}
+
 int engine_rounds(clean_engine_s* e, int64_t rounds, cudaStream_t s) {
   int rc;
   if (e->dirty && (rc = engine_rebuild(e, s)) != CLEAN_OK) return rc;
   if (e->n_work == 0) return CLEAN_OK;
+  while (rounds >= 2 && e->use_graphs && !e->graphs_refused) {
+    const int par = e->round & 1;
+    if (!e->pair[par] && !capture_pair(e, par)) {
+      e->graphs_refused = true;
+      break;
+    }
+    if (cudaGraphLaunch(e->pair[par], s) != cudaSuccess) return eng_fail(e, CLEAN_ERR_CUDA);
+    e->kernel_launches += e->pair_kernels;
+    ++e->graph_launches;
+    e->round += 2;
+    e->rounds_launched += 2;
+    rounds -= 2;
+  }
   for (int64_t r = 0; r < rounds; ++r) {
-    cudaError_t err = cudaSuccess;
-    for (const Group& g : e->groups) {
-      err = launch_minor_batch(e->d_plans, e->d_items + g.offset, g.count, g.G, g.resident,
-                               g.smem, e->round, s);
-      ++e->kernel_launches;
-      if (err != cudaSuccess) break;
-    }
-    if (err == cudaSuccess && e->blocks_tma > 0) {
-      err = launch_feedback_batch(e->d_plans, e->d_imgs, e->n_tma, e->blocks_tma, e->max_T,
-                                  e->d_maps, e->round, 1, 2000000000ull, s);
-      ++e->kernel_launches;
-    }
-    if (err == cudaSuccess && e->blocks_plain > 0) {
-      err = launch_feedback_batch(e->d_plans + e->n_tma, e->d_imgs + e->n_tma,
-                                  e->n_work - e->n_tma, e->blocks_plain, e->max_T, nullptr,
-                                  e->round, 1, 2000000000ull, s);
-      ++e->kernel_launches;
-    }
+    int n = 0;
+    const cudaError_t err = launch_round(e, e->round, s, &n);
+    e->kernel_launches += n;
     if (err != cudaSuccess) return eng_fail(e, CLEAN_ERR_CUDA);
     ++e->round;
     ++e->rounds_launched;
@@ -465,6 +541,17 @@ int clean_batch_stats(clean_batch_t b, int64_t* rounds_launched, int64_t* kernel
     for (const Job& j : e->jobs) t += e->h_states[j.slot].total;
     *n_components = t;
   }
+  return CLEAN_OK;
+}
+
+int clean_batch_graphs(clean_batch_t b, int32_t enable, int64_t* graph_launches) {
+  if (!b || enable < -1 || enable > 1) return CLEAN_ERR_INVALID_ARG;
+  clean_engine_s* e = b->eng;
+  if (enable >= 0) {
+    e->use_graphs = enable != 0;
+    e->graphs_refused = false;
+  }
+  if (graph_launches) *graph_launches = e->graph_launches;
   return CLEAN_OK;
 }
 

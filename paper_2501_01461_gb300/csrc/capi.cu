@@ -71,7 +71,21 @@ struct clean_plan_s {
   void* fft_X = nullptr;     // spectrum work, Ly x (Lx/2+1) complex
   void* fft_Kh = nullptr;    // PSF kernel spectrum, Ly x (Lx/2+1) complex
   float* R0 = nullptr;       // residual at the start of the current round
-  int feedback_path = 0;  // 0 auto, 1 plain loads, 2 TMA
+  int feedback_path = 0;  // 0 auto, 1 plain loads, 2 TMA, 3 pipelined loads
+  // two rounds (minor + feedback, twice) captured as a CUDA graph, one per
+  // starting parity, together with the launch configuration they captured
+  struct GraphKey {
+    PlanDev d;
+    MinorCfg mc;
+    CUtensorMap r_map, p_map, psf_map;
+    int32_t pipe, fb_path, tma, apply;
+  };
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t pair[2] = {nullptr, nullptr};
+  GraphKey pair_key[2];
+  bool use_graphs = true;
+  bool graphs_refused = false;
+  int64_t graph_launches = 0;
 };
 
 namespace {
@@ -285,6 +299,95 @@ int launch_round_minor(clean_plan_s* pl, cudaStream_t s) {
   return CLEAN_OK;
 }
 
+// ---- CUDA-graph replay of two rounds --------------------------------------
+
+void drop_graphs(clean_plan_s* pl) {
+  for (cudaGraphExec_t& g : pl->pair)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+}
+
+clean_plan_s::GraphKey graph_key(const clean_plan_s* pl) {
+  clean_plan_s::GraphKey k;
+  std::memset(&k, 0, sizeof(k));
+  const bool pipe = use_pipe(pl);
+  k.d = pl->d;
+  k.mc = pipe ? pl->mc_pipe : pl->mc;
+  k.r_map = pl->r_map;
+  k.p_map = pl->p_map_minor;
+  k.psf_map = pl->psf_map;
+  k.pipe = pipe ? 1 : 0;
+  k.fb_path = pl->feedback_path;
+  k.tma = (pl->psf_map_ok && pl->feedback_path != 1 && pl->feedback_path != 3) ? 1 : 0;
+  k.apply = feedback_on(pl->d) ? 1 : 0;
+  return k;
+}
+
+// One round (minor loop of parity q, then its feedback) on stream s.
+cudaError_t launch_round_pair_part(const clean_plan_s* pl, const clean_plan_s::GraphKey& k,
+                                   int q, cudaStream_t s) {
+  cudaError_t e = launch_minor(k.d, k.mc, q, &k.r_map, &k.p_map, s);
+  if (e != cudaSuccess) return e;
+  if (k.fb_path == 3) return launch_feedback_ldg(k.d, q, k.apply, s);
+  return launch_feedback(k.d, k.tma ? &k.psf_map : nullptr, q, k.apply,
+                         (uint64_t)pl->mc.spin_limit_ns, s);
+}
+
+bool capture_pair(clean_plan_s* pl, int par, const clean_plan_s::GraphKey& k) {
+  if (!pl->cap_stream &&
+      cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(pl->cap_stream, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    cudaError_t l = launch_round_pair_part(pl, k, par, pl->cap_stream);
+    if (l == cudaSuccess) l = launch_round_pair_part(pl, k, par ^ 1, pl->cap_stream);
+    e = cudaStreamEndCapture(pl->cap_stream, &graph);
+    if (l != cudaSuccess) e = l;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&pl->pair[par], graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    pl->pair[par] = nullptr;
+    cudaGetLastError();
+    return false;
+  }
+  pl->pair_key[par] = k;
+  return true;
+}
+
+bool graphs_usable(const clean_plan_s* pl) {
+  return pl->use_graphs && !pl->graphs_refused && !pl->timing && !pl->fft && !pl->pending;
+}
+
+// Two rounds from the graph of the current parity (captured, or recaptured
+// when the launch configuration changed).  Returns CLEAN_OK, an error, or
+// -1 when graphs are refused (the caller launches directly).
+int launch_pair(clean_plan_s* pl, cudaStream_t s) {
+  const clean_plan_s::GraphKey k = graph_key(pl);
+  const int par = pl->parity;
+  if (!pl->pair[par] || std::memcmp(&k, &pl->pair_key[par], sizeof(k)) != 0) {
+    if (pl->pair[par]) {
+      cudaGraphExecDestroy(pl->pair[par]);
+      pl->pair[par] = nullptr;
+    }
+    if (!capture_pair(pl, par, k)) {
+      pl->graphs_refused = true;
+      return -1;
+    }
+  }
+  const cudaError_t e = cudaGraphLaunch(pl->pair[par], s);
+  if (e != cudaSuccess) return cuda_fail(pl, e);
+  pl->kernel_launches += 4;
+  pl->rounds_launched += 2;
+  ++pl->graph_launches;
+  return CLEAN_OK;
+}
+
 int start_run(clean_plan_s* pl, const float* d_dirty, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(pl->d.peak, 0, sizeof(uint64_t) * 2 * pl->d.T, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(pl->d.st, 0, sizeof(DevState), s);
@@ -343,9 +446,18 @@ int run_rounds(clean_plan_s* pl, int32_t max_rounds, cudaStream_t s) {
     if (pl->d.K > 0) chunk = (pl->h_st->max_budget + pl->d.K - 1) / pl->d.K;
     chunk = std::max<int64_t>(chunk, 1);
     if (max_rounds >= 0) chunk = std::min<int64_t>(chunk, max_rounds - done);
-    for (int64_t i = 0; i < chunk; ++i) {
+    for (int64_t i = 0; i < chunk;) {
+      if (chunk - i >= 2 && graphs_usable(pl)) {
+        rc = launch_pair(pl, s);
+        if (rc == CLEAN_OK) {
+          i += 2;
+          continue;
+        }
+        if (rc != -1) return rc;
+      }
       if ((rc = launch_round_minor(pl, s)) != CLEAN_OK) return rc;
       if ((rc = launch_round_feedback(pl, s)) != CLEAN_OK) return rc;
+      ++i;
     }
     done += chunk;
     if ((rc = read_state(pl, s)) != CLEAN_OK) return rc;
@@ -427,6 +539,8 @@ void clean_destroy(clean_plan_t pl) {
       cufftDestroy(pl->fft_r2c);
       cufftDestroy(pl->fft_c2r);
     }
+    drop_graphs(pl);
+    if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
     for (void* a : pl->allocs) cudaFree(a);
     for (cudaEvent_t e : pl->ev_pool) cudaEventDestroy(e);
     if (pl->h_st) cudaFreeHost(pl->h_st);
@@ -847,6 +961,7 @@ int clean_stats(clean_plan_t pl, clean_stats_t* out, void* stream) {
   out->feedback_launches = pl->feedback_launches;
   out->minor_ms = pl->minor_ms;
   out->feedback_ms = pl->feedback_ms;
+  out->graph_launches = pl->graph_launches;
   return CLEAN_OK;
 }
 
@@ -892,6 +1007,11 @@ int clean_debug_set(clean_plan_t pl, int32_t what, int64_t value) {
     case CLEAN_DEBUG_FEEDBACK_PATH:
       if (value < 0 || value > 3) return CLEAN_ERR_INVALID_ARG;
       pl->feedback_path = (int)value;
+      return CLEAN_OK;
+    case CLEAN_DEBUG_GRAPHS:
+      if (value < 0 || value > 1) return CLEAN_ERR_INVALID_ARG;
+      pl->use_graphs = value != 0;
+      pl->graphs_refused = false;
       return CLEAN_OK;
     case CLEAN_DEBUG_TIMING:
       pl->timing = value != 0;

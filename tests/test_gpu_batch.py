@@ -41,8 +41,12 @@ def test_batch_equals_solo_runs():
     jobs = [dict(psf=d_psfs[i], ny=n, nx=n, gain=0.1, niter=niter, threshold=thr, tiles=tiles,
                  feedback_interval=K) for i, (n, tiles, K, niter, thr, fs) in enumerate(JOBS)]
     with cg.Batch(jobs) as b:
-        for rep in range(2):          # a second run must start clean
+        # rounds replayed from CUDA graphs, then launched one by one; the
+        # second run must also start clean
+        for rep, graphs in enumerate((True, False)):
+            before = b.graphs(graphs)
             b.run(d_dirties)
+            assert (b.graphs() > before) == graphs
             for i, (n, tiles, K, niter, thr, fs) in enumerate(JOBS):
                 res, mod, comps = b.get(i)
                 solo = gpu_clean(data[i][1], data[i][0], 0.1, niter, thr, tiles, K)
