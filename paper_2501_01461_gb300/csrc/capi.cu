@@ -391,6 +391,9 @@ int launch_pair(clean_plan_s* pl, cudaStream_t s) {
 int start_run(clean_plan_s* pl, const float* d_dirty, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(pl->d.peak, 0, sizeof(uint64_t) * 2 * pl->d.T, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(pl->d.st, 0, sizeof(DevState), s);
+  // grid-barrier key slots start with mark bit 63 set (see exchange_keys)
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(pl->d.gkeys, 0x80, sizeof(uint64_t) * 2 * (size_t)pl->d.T * pl->mc.G, s);
   if (e == cudaSuccess) e = launch_init(pl->d, d_dirty, pl->p.niter, s);
   ++pl->kernel_launches;
   if (e == cudaSuccess && pl->d.trigger > 0.f) {

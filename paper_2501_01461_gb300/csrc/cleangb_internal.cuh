@@ -101,7 +101,7 @@ struct PlanDev {
   clean_component* list;    // [niter] all components, list order
   int64_t* round_off;       // [niter + 1] list offset of each recorded round
   uint64_t* gkeys;          // [2][T * G] per-CTA partial keys (grid sync)
-  uint32_t* gbar;           // [T] grid-barrier arrival counters
+  uint32_t* gbar;           // [T] grid-barrier exchanges done per tile in this run
   DevState* st;
 };
 

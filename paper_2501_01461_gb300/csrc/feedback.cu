@@ -134,7 +134,6 @@ __device__ void close_round_if_last(const PlanDev& d, int parity, int total_bloc
       top = max(top, (uint32_t)(pk >> 32));
     }
     mb = b > mb ? b : mb;
-    d.gbar[s] = 0u;
   }
   act = __syncthreads_or(act);
   __shared__ uint32_t s_top;

@@ -66,16 +66,6 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
   return t;
 }
 
-__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
-  uint32_t v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ void red_release_add_u32(uint32_t* p, uint32_t v) {
-  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
 __device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t* p) {
   uint64_t v;
   asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
@@ -161,13 +151,24 @@ __device__ __forceinline__ uint64_t block_max_key(uint64_t k, uint64_t* s_warp) 
 
 // Step 4: every CTA of the tile group publishes its partial key `mine`
 // (valid in thread 0) and gets the group maximum back, identical in every
-// CTA.  Called by all threads; ends with a CTA barrier.  In grid mode an
-// expired barrier wait sets ST_TIMEOUT and *s_abort.
+// CTA.  Called by all threads; ends with a CTA barrier.
+//
+// Cluster groups read the partial keys through distributed shared memory
+// after a cluster barrier.  Grid groups exchange through global memory with
+// no counter and no fence: exchange g (g = seq0 + k counts the tile's
+// exchanges since the run started) writes slot set g & 1 and marks each key
+// with bit 63 = (g >> 1) & 1, a bit no key uses (|R| is non-negative).  The
+// previous write to a slot (exchange g - 2) carries the other mark, so a
+// reader polls the G slots until all carry the current mark.  A writer can
+// reach exchange g + 2 only after every CTA published exchange g + 1, which
+// each does after reading exchange g, so no slot is overwritten early.
+// Slots start with mark 1 (the run's first two exchanges expect 0).  An
+// expired wait sets ST_TIMEOUT and *s_abort.
 template <int SYNC>
 __device__ __forceinline__ uint64_t exchange_keys(const PlanDev& d, const MinorCfg& c, int t,
-                                                  int rank, int64_t k, uint64_t mine,
-                                                  uint64_t* s_part, uint64_t* s_best,
-                                                  int* s_abort) {
+                                                  int rank, int64_t k, uint32_t seq0,
+                                                  uint64_t mine, uint64_t* s_part,
+                                                  uint64_t* s_best, int* s_abort) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int G = c.G;
   if (SYNC == kSyncNone) {
@@ -182,31 +183,35 @@ __device__ __forceinline__ uint64_t exchange_keys(const PlanDev& d, const MinorC
     }
   } else {
     if (warp == 0) {
-      uint64_t* slot = d.gkeys + (int64_t)t * G + (k & 1) * ((int64_t)d.T * G);
+      const uint32_t g = seq0 + (uint32_t)k;
+      uint64_t* slot = d.gkeys + (int64_t)t * G + (int64_t)(g & 1u) * ((int64_t)d.T * G);
+      const uint64_t mark = (uint64_t)((g >> 1) & 1u) << 63;
+      // a forced timeout waits for a mark no CTA writes
+      const uint64_t want = c.force_timeout ? (mark ^ (1ull << 63)) : mark;
+      if (lane == 0) st_relaxed_u64(slot + rank, mine | mark);
+      uint64_t kk = 0ull;
       int abort = 0;
-      if (lane == 0) {
-        st_relaxed_u64(slot + rank, mine);
-        red_release_add_u32(d.gbar + t, 1u);
-        const uint32_t target = (uint32_t)((k + 1) * G) + (uint32_t)(c.force_timeout ? 1 : 0);
-        const uint64_t t0 = globaltimer_ns();
-        while (ld_acquire_u32(d.gbar + t) < target) {
+      const uint64_t t0 = globaltimer_ns();
+      for (int j = lane; j < G && !abort; j += 32) {
+        uint64_t v = ld_relaxed_u64(slot + j);
+        while ((v & (1ull << 63)) != want) {
           if (globaltimer_ns() - t0 > (uint64_t)c.spin_limit_ns) {
-            atomicOr(&d.st->status, ST_TIMEOUT);
-            d.st->timeout_where = ((int64_t)t << 32) | (int64_t)k;
             abort = 1;
             break;
           }
+          v = ld_relaxed_u64(slot + j);
         }
+        kk = umax64(kk, v & ~(1ull << 63));
       }
-      abort = __shfl_sync(0xffffffffu, abort, 0);
-      __syncwarp();
-      uint64_t kk = 0ull;
-      if (!abort)
-        for (int j = lane; j < G; j += 32) kk = umax64(kk, ld_relaxed_u64(slot + j));
+      abort = __any_sync(0xffffffffu, abort);
       kk = warp_max_key(kk);
       if (lane == 0) {
-        *s_best = kk;
-        if (abort) *s_abort = 1;
+        *s_best = abort ? 0ull : kk;
+        if (abort) {
+          atomicOr(&d.st->status, ST_TIMEOUT);
+          d.st->timeout_where = ((int64_t)t << 32) | (int64_t)k;
+          *s_abort = 1;
+        }
       }
     }
   }
@@ -239,6 +244,7 @@ __device__ __forceinline__ void minor_body(const PlanDev& d, const MinorCfg& c, 
   const int64_t budget = d.budget[t];
   const int64_t kmax = (d.K > 0 && (int64_t)d.K < budget) ? (int64_t)d.K : budget;
   const float level = d.trigger > 0.f ? *(volatile float*)&d.st->level : 0.f;
+  const uint32_t seq0 = d.gbar[t];  // the tile's exchanges so far in this run
   if (threadIdx.x == 0) {
     s_abort = 0;
     // the feedback of this round accumulates the tile's next peak here
@@ -277,7 +283,7 @@ __device__ __forceinline__ void minor_body(const PlanDev& d, const MinorCfg& c, 
     uint64_t mine = (best_a >= 0.f) ? make_key(best_v, best_i) : 0ull;
     mine = block_max_key(mine, s_warp);
 
-    key = exchange_keys<SYNC>(d, c, t, rank, k, mine, s_part, &s_best, &s_abort);
+    key = exchange_keys<SYNC>(d, c, t, rank, k, seq0, mine, s_part, &s_best, &s_abort);
     if (s_abort) break;
     ++k;
   }
@@ -296,6 +302,7 @@ __device__ __forceinline__ void minor_body(const PlanDev& d, const MinorCfg& c, 
   if (rank == 0 && threadIdx.x == 0) {
     d.rcount[t] = (int32_t)k;
     d.budget[t] = budget - k;
+    d.gbar[t] = seq0 + (uint32_t)k;
   }
 }
 
@@ -501,6 +508,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
   const int64_t budget = d.budget[t];
   const int64_t kmax = (d.K > 0 && (int64_t)d.K < budget) ? (int64_t)d.K : budget;
   const float level = d.trigger > 0.f ? *(volatile float*)&d.st->level : 0.f;
+  const uint32_t seq0 = d.gbar[t];  // the tile's exchanges so far in this run
   if (threadIdx.x == 0) {
     s_abort = 0;
     s_dead = 0;
@@ -664,7 +672,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
     }
     uint64_t mine = (best_a >= 0.f) ? make_key(best_v, best_i) : 0ull;
     mine = block_max_key(mine, s_warp);
-    key = exchange_keys<SYNC>(d, c, t, rank, k, mine, s_part, &s_best, &s_abort);
+    key = exchange_keys<SYNC>(d, c, t, rank, k, seq0, mine, s_part, &s_best, &s_abort);
     if (s_abort) break;
     ++k;
   }
@@ -689,6 +697,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
   if (rank == 0 && threadIdx.x == 0) {
     d.rcount[t] = (int32_t)k;
     d.budget[t] = budget - k;
+    d.gbar[t] = seq0 + (uint32_t)k;
   }
 }
 

@@ -141,9 +141,11 @@ extern "C" CLEAN_API int clean_hogbom_noalloc(const float* d_dirty, const float*
 
   // the peak keys are atomic-max targets and the control block collects
   // status bits: both must start at zero (the array keeps the last call's
-  // contents); set-up zeroes the barrier counter and sets the budget
+  // contents); set-up zeroes the exchange count and sets the budget
   cudaError_t e = cudaMemsetAsync(d.st, 0, sizeof(DevState), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(d.peak, 0, 2 * sizeof(uint64_t), s);
+  // grid-barrier key slots start with mark bit 63 set (see the minor loop)
+  if (e == cudaSuccess) e = cudaMemsetAsync(d.gkeys, 0x80, 2 * sizeof(uint64_t) * (size_t)G, s);
   if (e == cudaSuccess) e = minor_prepare(mc);
   if (e == cudaSuccess) e = launch_validate_psf(d, s);
   if (e == cudaSuccess) e = launch_init(d, d_dirty, niter, s);
