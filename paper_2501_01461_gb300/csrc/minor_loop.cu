@@ -360,7 +360,7 @@ __device__ __forceinline__ bool pipe_wait(uint64_t* bar, uint32_t parity, uint64
   if (ptx::mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = ptx::globaltimer_ns();
   for (;;) {
-    if (ptx::mbar_try_wait(bar, parity)) return true;
+    if (ptx::mbar_try_wait_hint(bar, parity, ptx::kWaitHintNs)) return true;
     if (*abort) return false;
     if (ptx::globaltimer_ns() - t0 > limit) {
       *abort = 1;
