@@ -203,8 +203,9 @@ def measured_peaks():
 
 
 def ncu_traffic() -> dict:
-    """DRAM bytes per launch from the committed ncu capture, per kernel, kept
-    only while the kernel's source file is unchanged since the capture."""
+    """Per kernel, the committed ncu capture's record (DRAM bytes per launch,
+    L2 throughput), kept only while the kernel's source file is unchanged
+    since the capture."""
     import hashlib
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     out = {}
@@ -219,7 +220,7 @@ def ncu_traffic() -> dict:
         if os.path.exists(src):
             h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
             if h == r.get("sha256_16"):
-                out[name] = r["bytes_per_launch"]
+                out[name] = r
     return out
 
 
@@ -443,7 +444,9 @@ def main():
     fb_l2_tbs = 4.0 * fb_upd / (fb_avg / 1e3) / 1e12
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak = st["sm_count"] * 128 * sm_mhz * 1e6 / 1e12
-    traffic = ncu_traffic()
+    rec = ncu_traffic()
+    traffic = {k: v["bytes_per_launch"] for k, v in rec.items()}
+    fb_lts = rec.get("feedback_tma_kernel", {}).get("lts_pct")
     if st["feedback_ms"] >= st["minor_ms"]:
         roof = {"kernel": "feedback_tma_kernel" if st["feedback_tma"] else "feedback_kernel",
                 "bound": "alu", "achieved": fb_tflops, "peak": alu_peak, "unit": "TFLOP/s",
@@ -454,8 +457,9 @@ def main():
                                "(no fused multiply-add on this path)",
                 "flops_per_launch": 2.0 * fb_upd,
                 "note": "2 flops per pixel-component update; the kernel is L2-bandwidth bound: "
-                        f"{fb_l2_tbs:.1f} TB/s of PSF windows from L2 (ncu: lts__throughput "
-                        "72.7 % of peak, profiles/feedback_tma_kernel_tiled-4096.md)"}
+                        f"{fb_l2_tbs:.1f} TB/s of PSF windows from L2"
+                        + (f" (ncu: lts__throughput {fb_lts:.1f} % of peak, "
+                           "profiles/feedback_tma_kernel_tiled-4096.md)" if fb_lts else "")}
     else:
         roof = {"kernel": "minor_pipe_kernel" if st["minor_pipe"] else "minor_kernel",
                 "bound": "hbm", "achieved": minor_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
