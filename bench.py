@@ -258,7 +258,7 @@ def batch_leg(cg, torch, stream, n_images=64):
     for p in solo:
         p.close()
     plain = [cg.Plan(psfs[i], j["n"], j["n"], gain=j["gain"], niter=j["niter"], threshold=0.0,
-                     mode=cg.UNTILED_GRID) for i, j in enumerate(jobs)]
+                     tiles=(1, 1)) for i, j in enumerate(jobs)]
     ms_plain = timed(lambda: [p.run(dirties[i]) for i, p in enumerate(plain)], reps=1)
     for p in plain:
         p.close()
@@ -287,7 +287,7 @@ def serve_leg(cg, torch, n_jobs=60, load=0.7):
     for sp in specs:
         psf, dirty = dev[sp["n"]]
         with cg.Plan(psf, sp["n"], sp["n"], gain=0.1, niter=sp["niter"], threshold=0.0,
-                     mode=cg.UNTILED_GRID) as p:
+                     tiles=(1, 1)) as p:
             p.run(dirty)
             torch.cuda.synchronize()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -523,7 +523,7 @@ def main():
     untiled = None
     if args.untiled_iters > 0:
         up = cg.Plan(d_psf, w.n, w.n, gain=w.gain, niter=args.untiled_iters, threshold=0.0,
-                     mode=cg.UNTILED_GRID)
+                     tiles=(1, 1))
         up.run(d_dirty)
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

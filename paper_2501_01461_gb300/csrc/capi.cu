@@ -594,13 +594,25 @@ int clean_plan(clean_plan_t* out, const clean_params* p, const float* d_psf, voi
     if (G == 0) G = sms;
   } else {
     const int per = std::max(1, sms / T);
-    // A grid-synchronised group needs all T * G CTAs resident (one per SM);
-    // measured on GB300 it beats clusters of up to 16 CTAs for every tile
-    // size tried, so clusters serve only grids with more tiles than SMs.
-    if (sync == CLEAN_SYNC_AUTO) sync = (T <= sms) ? CLEAN_SYNC_GRID : CLEAN_SYNC_CLUSTER;
+    const int64_t tile_px = (int64_t)maxH * maxW;
+    // A grid-synchronised group needs all T * G CTAs resident (one per SM).
+    // Measured on GB300 (plain Hogbom, 256^2 to 4096^2): tiles of up to 2^17
+    // pixels run fastest as one 16-CTA cluster (256^2: 3.3 us per iteration
+    // vs 5.8 with 152 grid CTAs, the exchange dominating); larger tiles on a
+    // grid group of about one CTA per 8192 pixels, at most SMs / T (512^2:
+    // 32 CTAs, 5.3 us; 1024^2 and up: all SMs).  Grids with more tiles than
+    // SMs use clusters.
+    if (sync == CLEAN_SYNC_AUTO) {
+      if (T > sms)
+        sync = CLEAN_SYNC_CLUSTER;
+      else if (tile_px <= (int64_t)1 << 17 && 16 * T <= sms && G == 0)
+        sync = CLEAN_SYNC_CLUSTER;
+      else
+        sync = CLEAN_SYNC_GRID;
+    }
     if (G == 0) {
       if (sync == CLEAN_SYNC_GRID) {
-        G = per;
+        G = (int)std::min<int64_t>(per, std::max<int64_t>(1, (tile_px + 8191) / 8192));
       } else {
         G = 1;
         while (G * 2 <= std::min(per, 16)) G *= 2;

@@ -192,16 +192,40 @@ __device__ __forceinline__ uint64_t exchange_keys(const PlanDev& d, const MinorC
       uint64_t kk = 0ull;
       int abort = 0;
       const uint64_t t0 = globaltimer_ns();
-      for (int j = lane; j < G && !abort; j += 32) {
-        uint64_t v = ld_relaxed_u64(slot + j);
-        while ((v & (1ull << 63)) != want) {
-          if (globaltimer_ns() - t0 > (uint64_t)c.spin_limit_ns) {
+      constexpr int kPoll = 8;  // slots per lane polled with all loads in flight
+      if (G <= 32 * kPoll) {
+        unsigned pend = 0u;
+#pragma unroll
+        for (int i = 0; i < kPoll; ++i)
+          if (lane + 32 * i < G) pend |= 1u << i;
+        while (pend) {
+          uint64_t v[kPoll];
+#pragma unroll
+          for (int i = 0; i < kPoll; ++i)
+            v[i] = (pend >> i) & 1u ? ld_relaxed_u64(slot + lane + 32 * i) : 0ull;
+#pragma unroll
+          for (int i = 0; i < kPoll; ++i)
+            if (((pend >> i) & 1u) && (v[i] & (1ull << 63)) == want) {
+              kk = umax64(kk, v[i] & ~(1ull << 63));
+              pend &= ~(1u << i);
+            }
+          if (pend && globaltimer_ns() - t0 > (uint64_t)c.spin_limit_ns) {
             abort = 1;
             break;
           }
-          v = ld_relaxed_u64(slot + j);
         }
-        kk = umax64(kk, v & ~(1ull << 63));
+      } else {
+        for (int j = lane; j < G && !abort; j += 32) {
+          uint64_t v = ld_relaxed_u64(slot + j);
+          while ((v & (1ull << 63)) != want) {
+            if (globaltimer_ns() - t0 > (uint64_t)c.spin_limit_ns) {
+              abort = 1;
+              break;
+            }
+            v = ld_relaxed_u64(slot + j);
+          }
+          kk = umax64(kk, v & ~(1ull << 63));
+        }
       }
       abort = __any_sync(0xffffffffu, abort);
       kk = warp_max_key(kk);
@@ -385,15 +409,65 @@ __device__ __forceinline__ void take_peak(float r, int idx, float& best_a, int& 
 // (LPR = 1 << lpr_log2 lanes per row, 4 pixels per lane, so a slab row is
 // CW = 4 LPR pixels wide); slab s goes to consumer warp (s + rot) mod 15,
 // continuing the round-robin of the previous chunk so the warps stay
-// balanced across a ragged last slab.  Each warp step loads kSlabUnroll
-// slabs' residual and PSF vectors before any arithmetic, then subtracts and
-// stores (global or the resident slab).  The step has no branches: rows past
-// the chunk are read from a valid staged row and masked.  The peak is kept
+// balanced across a ragged last slab.  A warp step loads the residual and
+// PSF vectors of four slabs (two or one for a chunk's tail) before any
+// arithmetic, then subtracts and stores (global or the resident slab).  The
+// step has no branches: rows past the chunk are read from a valid staged row
+// and masked.  The peak is kept
 // per 4-pixel group: the largest group maximum |R|, ties to the lower group
 // base index.  Groups are aligned runs of 4 pixels of one row, so the lowest
 // index holding the largest |R| lies in that group; resolve_group() finds it
 // once per iteration.
 constexpr int kSlabUnroll = 4;
+
+// U slabs s, s + 15, ... of one chunk for this lane (rows past r1 masked).
+template <bool RES, int OFF, int U>
+__device__ __forceinline__ void slab_step(const PlanDev& d, float* sRes, int WR, int ya,
+                                          const float* stgR, const float* stgP, int BW, int r0,
+                                          int r1, int x, int x0, int g, int rps, int sub, int s,
+                                          float f, float& best_a, int& best_base) {
+  constexpr int kWarps = kPipeConsumers / 32;
+  float4 rv[U], pa[U], pb[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int y = r0 + (s + u * kWarps) * rps + sub;
+    const int ly = y < r1 ? y - r0 : 0;  // masked rows read staged row 0
+    const float4* rowP4 = reinterpret_cast<const float4*>(stgP + ly * BW);
+    pa[u] = rowP4[g];
+    if (OFF != 0) pb[u] = rowP4[g + 1];
+    rv[u] = RES ? *reinterpret_cast<const float4*>(sRes + (r0 + ly - ya) * WR + (x - x0))
+                : reinterpret_cast<const float4*>(stgR + ly * BW)[g];
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int y = r0 + (s + u * kWarps) * rps + sub;
+    const bool valid = y < r1;
+    const float4 a = pa[u];
+    float4 p;
+    if (OFF == 0) {
+      p = a;
+    } else {
+      const float4 b = pb[u];
+      p = OFF == 1 ? make_float4(a.y, a.z, a.w, b.x)
+                   : OFF == 2 ? make_float4(a.z, a.w, b.x, b.y) : make_float4(a.w, b.x, b.y, b.z);
+    }
+    float4 r = rv[u];
+    fms2(r.x, r.y, p.x, p.y, f);
+    fms2(r.z, r.w, p.z, p.w, f);
+    if (valid) {
+      if (RES)
+        *reinterpret_cast<float4*>(sRes + (y - ya) * WR + (x - x0)) = r;
+      else
+        *reinterpret_cast<float4*>(d.R + (int64_t)y * d.nx + x) = r;
+    }
+    const float m0 = fmaxf(fmaxf(fabsf(r.x), fabsf(r.y)), fmaxf(fabsf(r.z), fabsf(r.w)));
+    const float m = valid ? m0 : -1.f;
+    const int base = y * d.nx + x;
+    const bool better = m > best_a || (m == best_a && base < best_base);
+    best_a = better ? m : best_a;
+    best_base = better ? base : best_base;
+  }
+}
 
 template <bool RES, int OFF>
 __device__ __forceinline__ void chunk_slabs(const PlanDev& d, float* sRes, int WR, int ya,
@@ -409,48 +483,21 @@ __device__ __forceinline__ void chunk_slabs(const PlanDev& d, float* sRes, int W
   const int x = c0 + 4 * g;
   if (x >= c1) return;
   const int nslabs = (r1 - r0 + rps - 1) / rps;
-  for (int s = s_first; s < nslabs; s += kSlabUnroll * kWarps) {
-    float4 rv[kSlabUnroll], pa[kSlabUnroll], pb[kSlabUnroll];
-#pragma unroll
-    for (int u = 0; u < kSlabUnroll; ++u) {
-      const int y = r0 + (s + u * kWarps) * rps + sub;
-      const int ly = y < r1 ? y - r0 : 0;  // masked rows read staged row 0
-      const float4* rowP4 = reinterpret_cast<const float4*>(stgP + ly * BW);
-      pa[u] = rowP4[g];
-      if (OFF != 0) pb[u] = rowP4[g + 1];
-      rv[u] = RES ? *reinterpret_cast<const float4*>(sRes + (r0 + ly - ya) * WR + (x - x0))
-                  : reinterpret_cast<const float4*>(stgR + ly * BW)[g];
-    }
-#pragma unroll
-    for (int u = 0; u < kSlabUnroll; ++u) {
-      const int y = r0 + (s + u * kWarps) * rps + sub;
-      const bool valid = y < r1;
-      const float4 a = pa[u];
-      float4 p;
-      if (OFF == 0) {
-        p = a;
-      } else {
-        const float4 b = pb[u];
-        p = OFF == 1 ? make_float4(a.y, a.z, a.w, b.x)
-                     : OFF == 2 ? make_float4(a.z, a.w, b.x, b.y) : make_float4(a.w, b.x, b.y, b.z);
-      }
-      float4 r = rv[u];
-      fms2(r.x, r.y, p.x, p.y, f);
-      fms2(r.z, r.w, p.z, p.w, f);
-      if (valid) {
-        if (RES)
-          *reinterpret_cast<float4*>(sRes + (y - ya) * WR + (x - x0)) = r;
-        else
-          *reinterpret_cast<float4*>(d.R + (int64_t)y * d.nx + x) = r;
-      }
-      const float m0 = fmaxf(fmaxf(fabsf(r.x), fabsf(r.y)), fmaxf(fabsf(r.z), fabsf(r.w)));
-      const float m = valid ? m0 : -1.f;
-      const int base = y * d.nx + x;
-      const bool better = m > best_a || (m == best_a && base < best_base);
-      best_a = better ? m : best_a;
-      best_base = better ? base : best_base;
-    }
+  // warp-uniform step sizes: whole 4-slab steps, then at most one 2-slab and
+  // one 1-slab step, so a chunk whose slab count is not a multiple of 60
+  // wastes no work on absent slabs
+  int s = s_first;
+  for (; s + (kSlabUnroll - 1) * kWarps < nslabs; s += kSlabUnroll * kWarps)
+    slab_step<RES, OFF, kSlabUnroll>(d, sRes, WR, ya, stgR, stgP, BW, r0, r1, x, x0, g, rps,
+                                     sub, s, f, best_a, best_base);
+  if (s + kWarps < nslabs) {
+    slab_step<RES, OFF, 2>(d, sRes, WR, ya, stgR, stgP, BW, r0, r1, x, x0, g, rps, sub, s, f,
+                           best_a, best_base);
+    s += 2 * kWarps;
   }
+  if (s < nslabs)
+    slab_step<RES, OFF, 1>(d, sRes, WR, ya, stgR, stgP, BW, r0, r1, x, x0, g, rps, sub, s, f,
+                           best_a, best_base);
 }
 
 // The pixel of the best 4-pixel group that holds |R| = best_a first (lowest

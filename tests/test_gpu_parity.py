@@ -146,6 +146,25 @@ def test_untiled_grid_256():
     assert_bit_exact(g, o, "untiled-256")
 
 
+def test_automatic_group_choice():
+    """One tile of up to 2^17 pixels runs as a 16-CTA cluster, larger tiles
+    on a grid group of about one CTA per 8192 pixels (at most all SMs); the
+    256^2 workload still matches the oracle bit for bit."""
+    w = synth.workload("untiled-256").build()
+    o = oracle.clean_f32(w["dirty"], w["psf"], 0.1, 2000, 5e-3)
+    g = gpu_clean(w["dirty"], w["psf"], 0.1, 2000, 5e-3)
+    assert g["stats"]["group_sync"] == cg.SYNC_CLUSTER and g["stats"]["group_ctas"] == 16
+    assert_bit_exact(g, o, "untiled-256 auto")
+    import torch
+    for n, want in ((512, 32), (1024, 128)):
+        psf = torch.zeros((2 * n, 2 * n), dtype=torch.float32, device="cuda")
+        psf[n, n] = 1.0
+        with cg.Plan(psf, n, n, gain=0.1, niter=10) as p:
+            st = p.stats()
+        sms = st["sm_count"]
+        assert st["group_sync"] == cg.SYNC_GRID and st["group_ctas"] == min(want, sms), (n, st)
+
+
 @pytest.mark.slow
 @pytest.mark.parametrize("thr", [0.0, 5e-3])
 def test_tiled_1024(thr):
