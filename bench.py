@@ -456,6 +456,8 @@ def main():
                                "one separately rounded multiply or subtract per lane per clock "
                                "(no fused multiply-add on this path)",
                 "flops_per_launch": 2.0 * fb_upd,
+                "l2": {"psf_bytes_per_launch": 4.0 * fb_upd, "achieved_TBps": fb_l2_tbs,
+                       "ncu_lts_throughput_pct_of_peak": fb_lts},
                 "note": "2 flops per pixel-component update; the kernel is L2-bandwidth bound: "
                         f"{fb_l2_tbs:.1f} TB/s of PSF windows from L2"
                         + (f" (ncu: lts__throughput {fb_lts:.1f} % of peak, "

@@ -74,7 +74,10 @@ typedef enum {
   CLEAN_ERR_UNSUPPORTED = 6  /* valid request this build cannot serve */
 } clean_status;
 
-/* feedback_mode */
+/* feedback_mode.  The environment variable CLEANGB_FORCE_FEEDBACK
+ * (gather, fft or auto), when set, overrides it for every plan created
+ * afterwards; clean_stats reports the path in use.  clean_run marks each
+ * chunk of rounds with an NVTX range "clean_rounds" for profilers. */
 enum { CLEAN_FB_GATHER = 0, CLEAN_FB_FFT = 1, CLEAN_FB_AUTO = 2 };
 /* mode */
 enum { CLEAN_TILED = 0, CLEAN_UNTILED_GRID = 1 };

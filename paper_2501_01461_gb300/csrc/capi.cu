@@ -9,6 +9,7 @@
 #include <vector>
 
 #include <cufft.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "cleangb_internal.cuh"
 
@@ -103,6 +104,23 @@ struct DeviceGuard {
 };
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// NVTX range for profilers (a no-op unless a tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+
+// CLEANGB_FORCE_FEEDBACK=gather|fft|auto overrides a plan's feedback_mode
+// (for experiments without code changes); anything else leaves it alone.
+int forced_feedback_mode(int mode) {
+  const char* v = std::getenv("CLEANGB_FORCE_FEEDBACK");
+  if (!v) return mode;
+  if (std::strcmp(v, "gather") == 0) return CLEAN_FB_GATHER;
+  if (std::strcmp(v, "fft") == 0) return CLEAN_FB_FFT;
+  if (std::strcmp(v, "auto") == 0) return CLEAN_FB_AUTO;
+  return mode;
+}
 
 int poison(clean_plan_s* pl, int code) {
   if (pl->poisoned == CLEAN_OK) pl->poisoned = code;
@@ -449,6 +467,7 @@ int run_rounds(clean_plan_s* pl, int32_t max_rounds, cudaStream_t s) {
     if (pl->d.K > 0) chunk = (pl->h_st->max_budget + pl->d.K - 1) / pl->d.K;
     chunk = std::max<int64_t>(chunk, 1);
     if (max_rounds >= 0) chunk = std::min<int64_t>(chunk, max_rounds - done);
+    NvtxRange range("clean_rounds");
     for (int64_t i = 0; i < chunk;) {
       if (chunk - i >= 2 && graphs_usable(pl)) {
         rc = launch_pair(pl, s);
@@ -678,17 +697,18 @@ int clean_plan(clean_plan_t* out, const clean_params* p, const float* d_psf, voi
   };
   // FFT feedback: a grid of at least (2 ny - 1) x (2 nx - 1) so the circular
   // convolution never wraps onto an image pixel.  AUTO takes it when a round's
-  // gather (about 0.26 ns per pixel-component update on GB300) would cost more
+  // gather (about 0.23 ns per pixel-component update on GB300) would cost more
   // than the transforms (estimated 16 ps per grid cell plus 60 us of launches).
   const bool fb_on = (p->feedback_interval > 0 || p->feedback_trigger > 0.f) && T > 1;
+  const int fb_mode = forced_feedback_mode(p->feedback_mode);
   pl->Ly = fft_size(2 * p->ny - 1);
   pl->Lx = fft_size(2 * p->nx - 1);
-  if (fb_on && p->feedback_mode == CLEAN_FB_FFT) pl->fft = true;
-  if (fb_on && p->feedback_mode == CLEAN_FB_AUTO) {
+  if (fb_on && fb_mode == CLEAN_FB_FFT) pl->fft = true;
+  if (fb_on && fb_mode == CLEAN_FB_AUTO) {
     const double comps =
         (double)(p->feedback_interval > 0 ? std::min<int64_t>(p->feedback_interval, per_tile_max)
                                           : per_tile_max) * T;
-    const double gather_s = comps * ((double)npix - (double)npix / T) * 0.26e-9;
+    const double gather_s = comps * ((double)npix - (double)npix / T) * 0.23e-9;
     const double fft_s = (double)pl->Ly * pl->Lx * 16e-12 + 60e-6;
     pl->fft = fft_s < gather_s;
   }

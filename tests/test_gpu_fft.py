@@ -88,3 +88,16 @@ def test_auto_picks_fft_for_large_rounds_and_gather_for_small():
     with cg.Plan(psf, 128, 128, niter=2000, tiles=(2, 2), feedback_interval=1,
                  feedback_mode=cg.FB_AUTO) as p:
         assert p.stats()["feedback_mode"] == cg.FB_GATHER
+
+
+def test_force_feedback_environment(monkeypatch):
+    """CLEANGB_FORCE_FEEDBACK overrides a plan's feedback mode."""
+    import torch
+    psf = torch.zeros((256, 256), dtype=torch.float32, device="cuda")
+    psf[128, 128] = 1.0
+    for env, want in (("fft", cg.FB_FFT), ("gather", cg.FB_GATHER)):
+        monkeypatch.setenv("CLEANGB_FORCE_FEEDBACK", env)
+        mode = cg.FB_GATHER if env == "fft" else cg.FB_FFT
+        with cg.Plan(psf, 128, 128, gain=0.1, niter=100, tiles=(2, 2), feedback_interval=5,
+                     feedback_mode=mode) as p:
+            assert p.stats()["feedback_mode"] == want
