@@ -215,6 +215,22 @@ CLEAN_API int clean_get(clean_plan_t plan, float* d_residual_out, float* d_model
 CLEAN_API int clean_get_rounds(clean_plan_t plan, int64_t* h_offsets, int64_t cap,
                      int64_t* n_rounds, void* stream);
 
+/* Checkpoint / resume of a run between rounds (the paper has no
+ * counterpart).  clean_checkpoint copies the plan's run state
+ * -- residual, model, component list, round offsets, per-tile budgets,
+ * peaks and counts, the control block, the round parity -- into the host
+ * buffer h_buf (capacity bytes) and stores its size in *bytes; with h_buf
+ * NULL it only reports the size.  The plan must have started a run and not
+ * be in the middle of a round (after clean_run or clean_step).  clean_resume
+ * loads such a checkpoint into a plan created with identical clean_params
+ * and a PSF set (the PSF is not part of the checkpoint); clean_run(plan,
+ * NULL, ...) then continues the run, with results identical bit for bit to
+ * an uninterrupted run.  A checkpoint of another problem or a corrupt one
+ * gives CLEAN_ERR_INVALID_ARG.  Both synchronise `stream`. */
+CLEAN_API int clean_checkpoint(clean_plan_t plan, void* h_buf, int64_t capacity,
+                               int64_t* bytes, void* stream);
+CLEAN_API int clean_resume(clean_plan_t plan, const void* h_buf, int64_t bytes, void* stream);
+
 /* One whole deconvolution with host buffers: copies h_dirty (and h_psf if
  * not NULL; the plan must own its PSF then) to the device, runs to
  * completion, copies residual, model and components back.  Outputs may be

@@ -84,6 +84,8 @@ _SIGS = {
     "clean_get": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, _vp, _vp]),
     "clean_get_rounds": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp]),
     "clean_deconvolve_host": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp]),
+    "clean_checkpoint": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp]),
+    "clean_resume": (ctypes.c_int, [_vp, _vp, _i64, _vp]),
     "clean_stats": (ctypes.c_int, [_vp, _vp, _vp]),
     "clean_destroy": (None, [_vp]),
     "clean_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -318,6 +320,21 @@ class Plan:
                                            p(comps), cap, ctypes.byref(n), _stream_ptr(stream)),
                "clean_deconvolve_host")
         return int(n.value)
+
+    def checkpoint(self, stream=None) -> bytes:
+        """The run's state between rounds as bytes (clean_checkpoint)."""
+        n = ctypes.c_int64(0)
+        _check(lib().clean_checkpoint(self._h, None, 0, ctypes.byref(n), _stream_ptr(stream)),
+               "clean_checkpoint")
+        buf = ctypes.create_string_buffer(n.value)
+        _check(lib().clean_checkpoint(self._h, buf, n.value, ctypes.byref(n), _stream_ptr(stream)),
+               "clean_checkpoint")
+        return buf.raw[:n.value]
+
+    def resume(self, blob: bytes, stream=None):
+        """Loads a checkpoint of a plan with identical parameters; run(None)
+        continues it (clean_resume)."""
+        _check(lib().clean_resume(self._h, blob, len(blob), _stream_ptr(stream)), "clean_resume")
 
     def debug_set(self, what: int, value: int):
         _check(lib().clean_debug_set(self._h, int(what), int(value)), "clean_debug_set")

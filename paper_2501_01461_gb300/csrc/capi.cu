@@ -6,6 +6,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include <cufft.h>
@@ -934,6 +935,131 @@ int clean_get_rounds(clean_plan_t pl, int64_t* h_offsets, int64_t cap, int64_t* 
     if (e != cudaSuccess) return cuda_fail(pl, e);
   }
   return CLEAN_OK;
+}
+
+// ---- checkpoint / resume ---------------------------------------------------
+
+namespace {
+
+constexpr uint64_t kCkptMagic = 0x31544b50424c4743ull;  // bytes "CGLBPKT1"
+constexpr int32_t kCkptVersion = 1;
+
+struct CkptHeader {
+  uint64_t magic;
+  int32_t version;
+  int32_t parity;
+  clean_params params;
+  int64_t rounds_launched;
+  int64_t total;     // components in the list
+  int64_t n_rounds;  // recorded rounds (list offsets)
+  int64_t npix;
+  int64_t T;
+  int64_t bytes;     // the whole checkpoint
+};
+
+int64_t ckpt_bytes(int64_t npix, int64_t T, int64_t total, int64_t n_rounds) {
+  return (int64_t)sizeof(CkptHeader) + 2 * npix * (int64_t)sizeof(float) +
+         total * (int64_t)sizeof(clean_component) + n_rounds * (int64_t)sizeof(int64_t) +
+         T * (int64_t)(sizeof(int64_t) + 2 * sizeof(uint64_t) + sizeof(int32_t)) +
+         (int64_t)sizeof(DevState);
+}
+
+// (device pointer, bytes) of each checkpoint section after the header, in order.
+std::vector<std::pair<void*, size_t>> ckpt_sections(clean_plan_s* pl, int64_t total,
+                                                    int64_t n_rounds) {
+  const size_t npix = (size_t)pl->d.ny * pl->d.nx, T = (size_t)pl->d.T;
+  return {{pl->d.R, sizeof(float) * npix},
+          {pl->d.model, sizeof(float) * npix},
+          {pl->d.list, sizeof(clean_component) * (size_t)total},
+          {pl->d.round_off, sizeof(int64_t) * (size_t)n_rounds},
+          {pl->d.budget, sizeof(int64_t) * T},
+          {pl->d.peak, sizeof(uint64_t) * 2 * T},
+          {pl->d.rcount, sizeof(int32_t) * T},
+          {pl->d.st, sizeof(DevState)}};
+}
+
+}  // namespace
+
+int clean_checkpoint(clean_plan_t pl, void* h_buf, int64_t capacity, int64_t* bytes,
+                     void* stream) {
+  if (!pl || !bytes || (h_buf && capacity < 0)) return CLEAN_ERR_INVALID_ARG;
+  if (pl->poisoned != CLEAN_OK) return pl->poisoned;
+  if (!pl->started || pl->pending) return CLEAN_ERR_INVALID_ARG;
+  DeviceGuard g(pl->device);
+  cudaStream_t s = as_stream(stream);
+  int rc = read_state(pl, s);
+  if (rc != CLEAN_OK) return rc;
+  const DevState st = *pl->h_st;
+  const int64_t npix = (int64_t)pl->d.ny * pl->d.nx;
+  const int64_t need = ckpt_bytes(npix, pl->d.T, st.total, st.n_rounds);
+  *bytes = need;
+  if (!h_buf) return CLEAN_OK;
+  if (capacity < need) return CLEAN_ERR_INVALID_ARG;
+  CkptHeader h;
+  std::memset(&h, 0, sizeof(h));
+  h.magic = kCkptMagic;
+  h.version = kCkptVersion;
+  h.parity = pl->parity;
+  h.params = pl->p;
+  h.rounds_launched = pl->rounds_launched;
+  h.total = st.total;
+  h.n_rounds = st.n_rounds;
+  h.npix = npix;
+  h.T = pl->d.T;
+  h.bytes = need;
+  std::memcpy(h_buf, &h, sizeof(h));
+  unsigned char* out = static_cast<unsigned char*>(h_buf) + sizeof(h);
+  cudaError_t e = cudaSuccess;
+  for (const auto& sec : ckpt_sections(pl, st.total, st.n_rounds)) {
+    if (sec.second && e == cudaSuccess)
+      e = cudaMemcpyAsync(out, sec.first, sec.second, cudaMemcpyDeviceToHost, s);
+    out += sec.second;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(pl, e);
+  return CLEAN_OK;
+}
+
+int clean_resume(clean_plan_t pl, const void* h_buf, int64_t bytes, void* stream) {
+  if (!pl || !h_buf || bytes < (int64_t)sizeof(CkptHeader)) return CLEAN_ERR_INVALID_ARG;
+  if (pl->poisoned != CLEAN_OK) return pl->poisoned;
+  CkptHeader h;
+  std::memcpy(&h, h_buf, sizeof(h));
+  const int64_t npix = (int64_t)pl->d.ny * pl->d.nx;
+  if (h.magic != kCkptMagic || h.version != kCkptVersion || h.npix != npix ||
+      h.T != pl->d.T || std::memcmp(&h.params, &pl->p, sizeof(clean_params)) != 0 ||
+      h.total < 0 || h.total > pl->p.niter || h.n_rounds < 0 || h.n_rounds > h.total ||
+      (h.parity != 0 && h.parity != 1) || h.bytes != bytes ||
+      ckpt_bytes(npix, h.T, h.total, h.n_rounds) != bytes)
+    return CLEAN_ERR_INVALID_ARG;
+  if (!pl->psf_set) return CLEAN_ERR_INVALID_ARG;
+  if (pl->psf_status != CLEAN_OK) return pl->psf_status;
+  DeviceGuard g(pl->device);
+  cudaStream_t s = as_stream(stream);
+  const unsigned char* in = static_cast<const unsigned char*>(h_buf) + sizeof(h);
+  cudaError_t e = cudaSuccess;
+  for (const auto& sec : ckpt_sections(pl, h.total, h.n_rounds)) {
+    if (sec.second && e == cudaSuccess)
+      e = cudaMemcpyAsync(sec.first, in, sec.second, cudaMemcpyHostToDevice, s);
+    in += sec.second;
+  }
+  // the grid exchange restarts its count; its key slots start marked
+  if (e == cudaSuccess) e = cudaMemsetAsync(pl->d.gbar, 0, sizeof(uint32_t) * pl->d.T, s);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(pl->d.gkeys, 0x80, sizeof(uint64_t) * 2 * (size_t)pl->d.T * pl->mc.G, s);
+  if (e == cudaSuccess && pl->fft) {
+    e = cudaMemcpyAsync(pl->R0, pl->d.R, sizeof(float) * (size_t)npix, cudaMemcpyDeviceToDevice,
+                        s);
+    if (e == cudaSuccess)
+      e = cudaMemsetAsync(pl->fft_A, 0, sizeof(float) * (size_t)pl->Ly * pl->Lx, s);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the host buffer may go now
+  if (e != cudaSuccess) return cuda_fail(pl, e);
+  pl->started = true;
+  pl->pending = false;
+  pl->parity = h.parity;
+  pl->rounds_launched = h.rounds_launched;
+  return read_state(pl, s);
 }
 
 int clean_deconvolve_host(clean_plan_t pl, const float* h_dirty, const float* h_psf,

@@ -87,6 +87,12 @@ def test_null_plan_calls(lib):
     lib.clean_destroy(None)
 
 
+def test_checkpoint_resume_reject_without_a_plan(lib):
+    n = ctypes.c_int64(0)
+    assert lib.clean_checkpoint(None, None, 0, ctypes.byref(n), None) == 1
+    assert lib.clean_resume(None, b"x" * 64, 64, None) == 1
+
+
 def test_no_oracle_in_product():
     """The product package never imports, links or reads the oracle."""
     pkg = os.path.dirname(cg.__file__)

@@ -348,3 +348,47 @@ def test_graph_replay_equals_direct_launches():
     assert np.array_equal(out[1][2], out[0][2])
     o = oracle.clean_f32(dirty, psf, 0.1, 2400, 0.0, (3, 3), 7)
     assert np.array_equal(out[1][0].view(np.uint32), o.residual.view(np.uint32))
+
+
+@pytest.mark.parametrize("mode", [cg.FB_GATHER, cg.FB_FFT])
+def test_checkpoint_resume_equals_uninterrupted_run(mode):
+    """A run stopped after three rounds, checkpointed to host memory and
+    resumed in a new plan ends exactly as the uninterrupted run."""
+    import torch
+    rng = np.random.default_rng(99)
+    n = 260
+    psf = synth.make_psf(2 * n, 2 * n)
+    ys, xs, fl = synth.make_sky(n, 15, 0.05, 2.1, rng)
+    dirty = synth.make_dirty(psf, n, ys, xs, fl, 1e-3, rng)
+    d_psf, d_dirty = torch.from_numpy(psf).cuda(), torch.from_numpy(dirty).cuda()
+    kw = dict(gain=0.1, niter=3000, threshold=1e-3, tiles=(3, 3), feedback_interval=9,
+              feedback_mode=mode)
+
+    def result(p):
+        r, m, _ = p.get()
+        return r.cpu().numpy(), m.cpu().numpy(), p.components_with_rounds()
+
+    with cg.Plan(d_psf, n, n, **kw) as p:
+        p.run(d_dirty)
+        want = result(p)
+    with cg.Plan(d_psf, n, n, **kw) as p:
+        p.run(d_dirty, max_rounds=3)
+        blob = p.checkpoint()
+    with cg.Plan(d_psf, n, n, **kw) as q:
+        q.resume(blob)
+        q.run(None)
+        got = result(q)
+        with pytest.raises(cg.CleanError):
+            q.resume(blob[:-4])                 # truncated
+        bad = bytearray(blob)
+        bad[0] ^= 1
+        with pytest.raises(cg.CleanError):
+            q.resume(bytes(bad))                # not a checkpoint
+    with cg.Plan(d_psf, n, n, **dict(kw, niter=2999)) as other:
+        with pytest.raises(cg.CleanError):
+            other.resume(blob)                  # another problem
+    for a, b in zip(got[:2], want[:2]):
+        assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+    for k in ("y", "x", "tile", "round"):
+        assert np.array_equal(got[2][k], want[2][k])
+    assert np.array_equal(got[2]["flux"].view(np.uint32), want[2]["flux"].view(np.uint32))
