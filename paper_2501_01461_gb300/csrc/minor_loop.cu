@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 // per chunk, one 2-D TMA box of the residual (unless the rows are resident in
 // shared memory) and one box of the PSF window, each box_w x chunk_h floats
 // at an x rounded down to 4 floats, into a ring of mbarrier-guarded stages;
-// 16 consumer warps apply the subtraction from shared memory, write the
+// 15 consumer warps apply the subtraction from shared memory, write the
 // residual (to global memory with 16-byte stores, or to the resident slab)
 // and track the peak.  Each mbarrier wait is bounded; a CTA whose wait
 // expires stops working but keeps joining the group exchange, so every CTA
