@@ -336,6 +336,21 @@ def cpu_baseline(w, data):
                       f"{dt:.1f} s single-threaded C (float32, -O2)"}
 
 
+def cpu_parallel_baseline(w, data):
+    """The multi-core CPU baseline (the oracle's arithmetic with the tiles of
+    a round on all host cores, OpenMP) on the same first round."""
+    import oracle
+    oracle.build_parallel()
+    cores = oracle.parallel_threads(os.cpu_count() or 1)
+    t0 = time.perf_counter()
+    r = oracle.parallel_clean_f32(data["dirty"], data["psf"], w.gain, w.niter, 0.0, w.tiles,
+                                  w.feedback_interval, max_rounds=1)
+    dt = time.perf_counter() - t0
+    return {"value": r.n / dt, "unit": UNIT, "cores": cores, "kind": "oracle_parallel",
+            "sample": f"first round of {w.name}: {r.n} minor iterations + their feedback, "
+                      f"{dt:.1f} s on {cores} threads (float32, -O2, OpenMP over tiles)"}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -570,10 +585,11 @@ def main():
     if not args.no_serve:
         served = serve_leg(cg, torch)
 
-    cpu = None
+    cpu = cpu_par = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(w, data)
         cpu["cores"] = 1
+        cpu_par = cpu_parallel_baseline(w, data)
 
     if rank == 0:
         ty, tx = w.tiles
@@ -589,7 +605,8 @@ def main():
             "px_iter_per_s": value * px_iter,
             "feedback_px_comp_per_s": world * feedback_updates_per_run(w) * args.steps / (total_ms / 1e3),
             "roofline": roof, "kernels": kernels,
-            "cpu_baseline": cpu, "e2e": e2e, "untiled_gpu": untiled,
+            "cpu_baseline": cpu, "cpu_parallel_baseline": cpu_par,
+            "e2e": e2e, "untiled_gpu": untiled,
             "vs_untiled_gpu": (value / untiled["iters_per_s"]) if untiled else None,
             "fft_feedback": fft,
             "batched": batched,

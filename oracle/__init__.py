@@ -1,7 +1,7 @@
 """CPU oracle for tiled Hogbom CLEAN with feedback (arXiv 2501.01461).
 
 TEST INFRASTRUCTURE ONLY.  Only the tests, the package's ``smoke()`` check and
-the benchmark's CPU-baseline leg import this module.  The product (the CUDA
+the benchmark's CPU-baseline legs import this module.  The product (the CUDA
 library and its Python binding) never imports, links or calls it, and the two
 share no code: they share only the seeded inputs from ``synth``.
 
@@ -18,6 +18,10 @@ Contents
                 residual, float64 NumPy
   psf_convolve  model image convolved with the PSF (float64 FFT), used to
                 check residual + model * PSF = dirty
+  parallel_clean_f32
+                multi-core CPU baseline (clean_parallel.c, OpenMP over the
+                tiles of a round), equal to clean_f32 bit for bit; timed by
+                the benchmark beside the single-threaded oracle
 
 Paper passages (Section 3): a component is the peak residual times the gain
 (first equation); the residual loses gain x peak x PSF shifted to the peak
@@ -56,6 +60,72 @@ def build(force: bool = False) -> str:
     subprocess.run([cc, *CFLAGS, "-o", tmp, *src], check=True)
     os.replace(tmp, _SO)
     return _SO
+
+
+_PAR_SO = os.path.join(_HERE, "_build", "liboracle_parallel.so")
+_par_lib = None
+
+
+def build_parallel(force: bool = False) -> str:
+    """Compile the multi-core CPU baseline (OpenMP) with gcc."""
+    src = os.path.join(_HERE, "clean_parallel.c")
+    if not force and os.path.exists(_PAR_SO) and os.path.getmtime(_PAR_SO) >= os.path.getmtime(src):
+        return _PAR_SO
+    os.makedirs(os.path.dirname(_PAR_SO), exist_ok=True)
+    tmp = _PAR_SO + f".{os.getpid()}.tmp"
+    cc = os.environ.get("CC", "gcc")
+    subprocess.run([cc, *CFLAGS, "-fopenmp", "-o", tmp, src], check=True)
+    os.replace(tmp, _PAR_SO)
+    return _PAR_SO
+
+
+def _load_parallel():
+    global _par_lib
+    with _lock:
+        if _par_lib is None:
+            lib = ctypes.CDLL(build_parallel())
+            i32, i64, f64, vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+            lib.parallel_clean_f32.restype = i64
+            lib.parallel_clean_f32.argtypes = [vp, i32, i32, vp, i32, i32, f64, i64, f64, i32,
+                                               i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, i64,
+                                               vp]
+            lib.parallel_threads.restype = ctypes.c_int
+            lib.parallel_threads.argtypes = [ctypes.c_int]
+            _par_lib = lib
+    return _par_lib
+
+
+def parallel_threads(n: int = 0) -> int:
+    """Sets the multi-core baseline's OpenMP thread count (n > 0) and returns it."""
+    return int(_load_parallel().parallel_threads(int(n)))
+
+
+def parallel_clean_f32(dirty, psf, gain, niter, threshold=0.0, tiles=(1, 1), K=0,
+                       max_rounds=-1) -> Result:
+    """Multi-core CPU baseline (clean_parallel.c): the float32 oracle's
+    arithmetic with the tiles of a round on OpenMP threads; equal to
+    clean_f32 bit for bit (no flux trigger)."""
+    lib = _load_parallel()
+    dirty = np.ascontiguousarray(dirty, dtype=np.float32)
+    psf = np.ascontiguousarray(psf, dtype=np.float32)
+    ny, nx = dirty.shape
+    pny, pnx = psf.shape
+    cap = max(int(niter), 1)
+    res = np.empty((ny, nx), np.float32)
+    model = np.empty((ny, nx), np.float32)
+    oy = np.empty(cap, np.int32); ox = np.empty(cap, np.int32)
+    of = np.empty(cap, np.float32); ot = np.empty(cap, np.int32); orr = np.empty(cap, np.int32)
+    rounds = ctypes.c_int32(0)
+    n = lib.parallel_clean_f32(_ptr(dirty), ny, nx, _ptr(psf), pny, pnx, _f32(gain), int(niter),
+                               _f32(threshold), tiles[0], tiles[1], int(K), int(max_rounds),
+                               _ptr(res), _ptr(model), _ptr(oy), _ptr(ox), _ptr(of), _ptr(ot),
+                               _ptr(orr), cap, ctypes.byref(rounds))
+    if n < 0:
+        raise ValueError({-1: "invalid arguments", -2: "out of memory",
+                          -3: "component capacity exceeded"}.get(n, str(n)))
+    comps = dict(y=oy[:n].copy(), x=ox[:n].copy(), flux=of[:n].copy(),
+                 tile=ot[:n].copy(), round=orr[:n].copy())
+    return Result(residual=res, model=model, comps=comps, rounds=rounds.value, n=int(n))
 
 
 def load_library(path: str):
