@@ -2,9 +2,11 @@
 // continuous batching for serving (clean_server_*).
 //
 // Every resident image's round runs in shared launches: minor-loop launches
-// grouped by CTAs per tile and residual placement (one CTA per small tile,
-// a thread-block cluster of up to 16 CTAs per large one, largest tiles
-// first), then one feedback launch over every image's blocks.  Each image
+// grouped by kernel, CTAs per tile and residual placement (one CTA per small
+// tile, a thread-block cluster of up to 16 CTAs per large one, largest tiles
+// first; images whose residual and PSF allow 2-D TMA boxes take the TMA
+// pipeline, the others plain loads), then one feedback launch over every
+// image's blocks.  Each image
 // keeps its own round phase (it may have joined later), its own budgets,
 // peaks and component list, so its results are bit for bit those of its own
 // clean_plan + clean_run.  Images that finish leave the work lists; new ones
@@ -35,6 +37,9 @@ struct Job {
   PlanDev dev{};
   CUtensorMap map{};
   bool tma = false;
+  // residual and PSF box maps of the batched minor-loop pipeline
+  CUtensorMap rmap{}, pmap{};
+  bool pipe = false;
   int64_t id = 0;
   int slot = 0;
   bool finished = false;
@@ -43,6 +48,9 @@ struct Job {
 struct Group {
   int offset = 0, count = 0;  // into the item array
   int G = 1, resident = 0, smem = 0;
+  int pipe = 0;               // 1: TMA pipeline (cfg), 0: plain loads
+  int max_rows = 0, max_w = 0;
+  MinorCfg cfg{};
 };
 
 }  // namespace
@@ -60,6 +68,8 @@ struct clean_engine_s {
   int items_cap = 0;
   BatchImage* d_imgs = nullptr;         // [cap] feedback geometry (TMA images first)
   CUtensorMap* d_maps = nullptr;        // [cap]
+  CUtensorMap* d_rmaps = nullptr;       // [cap] minor-loop residual boxes
+  CUtensorMap* d_pmaps = nullptr;       // [cap] minor-loop PSF boxes
   std::vector<Group> groups;
   int n_work = 0, n_tma = 0, blocks_tma = 0, blocks_plain = 0, max_T = 1;
   bool dirty = true;                    // work lists need a rebuild
@@ -103,6 +113,8 @@ void engine_free(clean_engine_s* e) {
   cudaFree(e->d_items);
   cudaFree(e->d_imgs);
   cudaFree(e->d_maps);
+  cudaFree(e->d_rmaps);
+  cudaFree(e->d_pmaps);
   if (e->h_states) cudaFreeHost(e->h_states);
   cudaGetLastError();
   delete e;
@@ -117,7 +129,9 @@ int engine_create(clean_engine_s** out, int cap) {
       cudaMallocHost(&e->h_states, sizeof(DevState) * cap) != cudaSuccess ||
       cudaMalloc(&e->d_plans, sizeof(PlanDev) * cap) != cudaSuccess ||
       cudaMalloc(&e->d_imgs, sizeof(BatchImage) * cap) != cudaSuccess ||
-      cudaMalloc(&e->d_maps, sizeof(CUtensorMap) * cap) != cudaSuccess) {
+      cudaMalloc(&e->d_maps, sizeof(CUtensorMap) * cap) != cudaSuccess ||
+      cudaMalloc(&e->d_rmaps, sizeof(CUtensorMap) * cap) != cudaSuccess ||
+      cudaMalloc(&e->d_pmaps, sizeof(CUtensorMap) * cap) != cudaSuccess) {
     engine_free(e);
     return CLEAN_ERR_OOM;
   }
@@ -162,6 +176,11 @@ int engine_register(clean_engine_s* e, const clean_params* p, const float* d_psf
   j.dev = plan_device_state(j.plan);
   j.dev.st = e->d_states + j.slot;
   j.tma = plan_psf_tensor_map(j.plan, &j.map);
+  // the minor-loop pipeline needs box maps over the residual and the PSF
+  j.pipe = p->ny >= kBatchBoxRows && p->psf_ny >= kBatchBoxRows && p->nx >= kBatchBoxW &&
+           p->psf_nx >= kBatchBoxW &&
+           make_box_tensor_map(&j.pmap, d_psf, p->psf_ny, p->psf_nx, kBatchBoxW, kBatchBoxRows) &&
+           make_box_tensor_map(&j.rmap, j.dev.R, p->ny, p->nx, kBatchBoxW, kBatchBoxRows);
   j.id = e->next_id++;
   j.finished = true;  // not running until started
   e->jobs.push_back(j);
@@ -186,6 +205,26 @@ void tile_group(int h, int w, int* G, int* resident, int* smem) {
   *smem = 0;
 }
 
+// CTAs per tile for the batched pipeline: the fewest power-of-two CTAs
+// (<= 16) whose row slabs fit in shared memory beside a ring of at least two
+// PSF boxes, else 16 CTAs streaming their rows.  The group's geometry is
+// checked once the group's largest slab is known.
+void pipe_tile_group(int h, int w, int* G, int* resident, int* rows) {
+  for (int g = 1; g <= 16; g *= 2) {
+    MinorCfg c;
+    const int r = (h + g - 1) / g;
+    if (minor_pipe_batch_geometry(c, g, 1, r, w)) {
+      *G = g;
+      *resident = 1;
+      *rows = r;
+      return;
+    }
+  }
+  *G = 16;
+  *resident = 0;
+  *rows = (h + 15) / 16;
+}
+
 // Rebuilds the device work lists from the unfinished jobs.
 int engine_rebuild(clean_engine_s* e, cudaStream_t s) {
   std::vector<int> work;
@@ -197,11 +236,11 @@ int engine_rebuild(clean_engine_s* e, cudaStream_t s) {
   e->n_tma = 0;
   e->max_T = 1;
   std::vector<PlanDev> plans;
-  std::vector<CUtensorMap> maps;
+  std::vector<CUtensorMap> maps, rmaps, pmaps;
   std::vector<BatchImage> imgs;
   struct Sized {
     int64_t px;
-    int G, resident, smem;
+    int pipe, G, resident, smem, rows, w;
     BatchItem it;
   };
   std::vector<Sized> all;
@@ -211,13 +250,23 @@ int engine_rebuild(clean_engine_s* e, cudaStream_t s) {
     const Job& j = e->jobs[work[w]];
     plans.push_back(j.dev);
     maps.push_back(j.map);
+    rmaps.push_back(j.rmap);
+    pmaps.push_back(j.pmap);
     if (j.tma) ++e->n_tma;
     e->max_T = std::max(e->max_T, j.dev.T);
     for (int t = 0; t < j.dev.T; ++t) {
       const Rect r = tile_rect(t, j.dev.ny, j.dev.nx, j.dev.ty, j.dev.tx);
       Sized z;
       z.px = (int64_t)(r.y1 - r.y0) * (r.x1 - r.x0);
-      tile_group(r.y1 - r.y0, r.x1 - r.x0, &z.G, &z.resident, &z.smem);
+      z.pipe = j.pipe ? 1 : 0;
+      z.w = r.x1 - r.x0;
+      if (z.pipe) {
+        pipe_tile_group(r.y1 - r.y0, z.w, &z.G, &z.resident, &z.rows);
+        z.smem = 0;
+      } else {
+        tile_group(r.y1 - r.y0, z.w, &z.G, &z.resident, &z.smem);
+        z.rows = (r.y1 - r.y0 + z.G - 1) / z.G;
+      }
       z.it = BatchItem{w, t};
       all.push_back(z);
     }
@@ -233,8 +282,9 @@ int engine_rebuild(clean_engine_s* e, cudaStream_t s) {
     imgs.push_back(im);
     (j.tma ? e->blocks_tma : e->blocks_plain) += im.nblocks;
   }
-  // groups of equal (G, resident), biggest tiles first within each
+  // groups of equal (kernel, G, resident), biggest tiles first within each
   std::stable_sort(all.begin(), all.end(), [](const Sized& a, const Sized& b) {
+    if (a.pipe != b.pipe) return a.pipe > b.pipe;
     if (a.G != b.G) return a.G > b.G;
     if (a.resident != b.resident) return a.resident < b.resident;
     return a.px > b.px;
@@ -242,25 +292,36 @@ int engine_rebuild(clean_engine_s* e, cudaStream_t s) {
   e->groups.clear();
   std::vector<BatchItem> items;
   for (size_t k = 0; k < all.size(); ++k) {
-    if (e->groups.empty() || e->groups.back().G != all[k].G ||
-        e->groups.back().resident != all[k].resident) {
+    if (e->groups.empty() || e->groups.back().pipe != all[k].pipe ||
+        e->groups.back().G != all[k].G || e->groups.back().resident != all[k].resident) {
       Group g;
       g.offset = (int)items.size();
+      g.pipe = all[k].pipe;
       g.G = all[k].G;
       g.resident = all[k].resident;
       e->groups.push_back(g);
     }
     Group& g = e->groups.back();
     g.smem = std::max(g.smem, all[k].smem);
+    g.max_rows = std::max(g.max_rows, all[k].rows);
+    g.max_w = std::max(g.max_w, all[k].w);
     ++g.count;
     items.push_back(all[k].it);
   }
-  // a cluster size the device cannot schedule falls back to smaller groups
-  for (Group& g : e->groups)
-    if (g.G > 1) {
+  for (Group& g : e->groups) {
+    if (g.pipe) {
+      // every tile fits alone, so the group's largest slab fits too
+      if (!minor_pipe_batch_geometry(g.cfg, g.G, g.resident, g.max_rows, g.max_w))
+        return CLEAN_ERR_UNSUPPORTED;
+      g.smem = g.cfg.smem;
+      if (g.G > 1 && minor_pipe_batch_cluster(g.G, g.resident, g.smem) != g.G)
+        return CLEAN_ERR_UNSUPPORTED;
+    } else if (g.G > 1) {
+      // a cluster size the device cannot schedule
       const int ok = minor_batch_cluster(g.G, g.resident, g.smem);
       if (ok != g.G) return CLEAN_ERR_UNSUPPORTED;
     }
+  }
   if ((int)items.size() > e->items_cap) {
     cudaFree(e->d_items);
     e->items_cap = std::max<int>((int)items.size(), 2 * e->items_cap);
@@ -273,6 +334,12 @@ int engine_rebuild(clean_engine_s* e, cudaStream_t s) {
                           cudaMemcpyHostToDevice, s);
     if (err == cudaSuccess)
       err = cudaMemcpyAsync(e->d_maps, maps.data(), sizeof(CUtensorMap) * maps.size(),
+                            cudaMemcpyHostToDevice, s);
+    if (err == cudaSuccess)
+      err = cudaMemcpyAsync(e->d_rmaps, rmaps.data(), sizeof(CUtensorMap) * rmaps.size(),
+                            cudaMemcpyHostToDevice, s);
+    if (err == cudaSuccess)
+      err = cudaMemcpyAsync(e->d_pmaps, pmaps.data(), sizeof(CUtensorMap) * pmaps.size(),
                             cudaMemcpyHostToDevice, s);
     if (err == cudaSuccess)
       err = cudaMemcpyAsync(e->d_imgs, imgs.data(), sizeof(BatchImage) * imgs.size(),
@@ -320,8 +387,10 @@ int engine_mark(clean_engine_s* e) {
 cudaError_t launch_round(clean_engine_s* e, int round, cudaStream_t s, int* n) {
   cudaError_t err = cudaSuccess;
   for (const Group& g : e->groups) {
-    err = launch_minor_batch(e->d_plans, e->d_items + g.offset, g.count, g.G, g.resident,
-                             g.smem, round, s);
+    err = g.pipe ? launch_minor_pipe_batch(e->d_plans, e->d_items + g.offset, g.count, g.cfg,
+                                           e->d_rmaps, e->d_pmaps, round, s)
+                 : launch_minor_batch(e->d_plans, e->d_items + g.offset, g.count, g.G,
+                                      g.resident, g.smem, round, s);
     ++*n;
     if (err != cudaSuccess) return err;
   }

@@ -191,6 +191,21 @@ cudaError_t launch_minor_batch(const PlanDev* plans, const BatchItem* items, int
                                int G, int resident, int smem, int round, cudaStream_t s);
 // Largest cluster size <= want that can be scheduled for the batched kernel.
 int minor_batch_cluster(int want, int resident, int smem);
+
+// Batched TMA pipeline: every image's residual and PSF box maps have boxes of
+// kBatchBoxW x kBatchBoxRows floats (chunks of 128 columns x 60 rows).
+constexpr int kBatchBoxW = 132;
+constexpr int kBatchBoxRows = 60;
+// Pipeline geometry for a batch group of G CTAs per tile whose CTAs hold at
+// most max_rows x max_w pixels (resident in shared memory or streamed);
+// false if the ring does not fit.
+bool minor_pipe_batch_geometry(MinorCfg& c, int G, int resident, int max_rows, int max_w);
+// Largest cluster size <= want (a power of two) the device can schedule for
+// the batched pipeline with `smem` bytes of dynamic shared memory (1 if none).
+int minor_pipe_batch_cluster(int want, int resident, int smem);
+cudaError_t launch_minor_pipe_batch(const PlanDev* plans, const BatchItem* items, int n_items,
+                                    const MinorCfg& c, const CUtensorMap* rmaps,
+                                    const CUtensorMap* pmaps, int round, cudaStream_t s);
 // Feedback for many images in one launch (plain loads, or TMA when maps is
 // non-NULL: one PSF tensor map per image in device memory, 64-byte aligned).
 cudaError_t launch_feedback_batch(const PlanDev* plans, const BatchImage* imgs, int n_images,

@@ -514,11 +514,12 @@ __device__ __forceinline__ void resolve_group(const PlanDev& d, const float* sRe
   best_v = k4 == 0 ? r.x : k4 == 1 ? r.y : k4 == 2 ? r.z : r.w;
 }
 
+// CTA `rank` of the group serving tile t; r_map and p_map describe the
+// residual and PSF boxes (r_map unused when the rows are resident).
 template <int SYNC, bool RES>
-__global__ void __launch_bounds__(kPipeThreads, 1)
-    minor_pipe_kernel(PlanDev d, MinorCfg c, int parity,
-                      const __grid_constant__ CUtensorMap r_map,
-                      const __grid_constant__ CUtensorMap p_map) {
+__device__ __forceinline__ void minor_pipe_body(const PlanDev& d, const MinorCfg& c, int parity,
+                                                const CUtensorMap* r_map,
+                                                const CUtensorMap* p_map, int t, int rank) {
   extern __shared__ __align__(128) float smem[];
   float* sRes = smem;                       // resident slab (RES), row stride WR
   float* sStage = smem + c.res_floats;      // ring of stages
@@ -531,8 +532,6 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
   __shared__ int s_dead;     // mbarrier timeout: stop working, keep exchanging
 
   const int G = c.G;
-  const int t = blockIdx.x / G;
-  const int rank = (SYNC == CLEAN_SYNC_CLUSTER) ? (int)cluster_rank() : (int)(blockIdx.x % G);
   const Rect rc = tile_rect(t, d.ny, d.nx, d.ty, d.tx);
   const int H = rc.y1 - rc.y0;
   const int ya = rc.y0 + (int)(((int64_t)rank * H) / G);
@@ -567,8 +566,8 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
     ptx::fence_barrier_init();
   }
   if (producer && lane == 0) {
-    if (!RES) ptx::prefetch_tensormap(&r_map);
-    ptx::prefetch_tensormap(&p_map);
+    if (!RES) ptx::prefetch_tensormap(r_map);
+    ptx::prefetch_tensormap(p_map);
   }
   if (RES) {
     const int n = (yb - ya) * W;
@@ -631,8 +630,8 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
           const int r0 = ya + rb * BH, c0 = x0 + cb * CW;
           float* stg = sStage + (size_t)p_st * stage_floats;
           ptx::mbar_arrive_expect_tx(&full_bar[p_st], stage_bytes);
-          if (!RES) ptx::tma_load_2d(stg, &r_map, c0 & ~3, r0, &full_bar[p_st]);
-          ptx::tma_load_2d(stg + (RES ? 0 : box_floats), &p_map, (c0 + dx) & ~3, r0 + dy,
+          if (!RES) ptx::tma_load_2d(stg, r_map, c0 & ~3, r0, &full_bar[p_st]);
+          ptx::tma_load_2d(stg + (RES ? 0 : box_floats), p_map, (c0 + dx) & ~3, r0 + dy,
                            &full_bar[p_st]);
           ++jnext;
           if (++p_st == S) {
@@ -749,6 +748,31 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
 }
 
 template <int SYNC, bool RES>
+__global__ void __launch_bounds__(kPipeThreads, 1)
+    minor_pipe_kernel(PlanDev d, MinorCfg c, int parity,
+                      const __grid_constant__ CUtensorMap r_map,
+                      const __grid_constant__ CUtensorMap p_map) {
+  const int t = blockIdx.x / c.G;
+  const int rank = (SYNC == CLEAN_SYNC_CLUSTER) ? (int)cluster_rank() : (int)(blockIdx.x % c.G);
+  minor_pipe_body<SYNC, RES>(d, c, parity, &r_map, &p_map, t, rank);
+}
+
+// Batched pipeline launch: one CTA (kSyncNone) or one cluster of G CTAs per
+// (image, tile) item, each image's plan state in `plans` and its residual and
+// PSF box maps in rmaps / pmaps (global memory, indexed like `plans`).
+template <int SYNC, bool RES>
+__global__ void __launch_bounds__(kPipeThreads, 1)
+    minor_pipe_batch_kernel(const PlanDev* __restrict__ plans,
+                            const BatchItem* __restrict__ items, const CUtensorMap* rmaps,
+                            const CUtensorMap* pmaps, MinorCfg c, int round) {
+  const BatchItem it = items[blockIdx.x / c.G];
+  const PlanDev d = plans[it.image];
+  const int rank = (SYNC == CLEAN_SYNC_CLUSTER) ? (int)cluster_rank() : 0;
+  minor_pipe_body<SYNC, RES>(d, c, (round - d.round0) & 1, rmaps + it.image, pmaps + it.image,
+                             it.tile, rank);
+}
+
+template <int SYNC, bool RES>
 void* kernel_ptr(bool pipe) {
   return pipe ? (void*)minor_pipe_kernel<SYNC, RES> : (void*)minor_kernel<SYNC, RES>;
 }
@@ -797,6 +821,92 @@ int minor_batch_cluster(int want, int resident, int smem) {
   }
   cudaGetLastError();
   return 1;
+}
+
+// ---- batched pipeline --------------------------------------------------------
+
+const void* pipe_batch_fn(int G, int resident) {
+  if (G > 1)
+    return resident ? (const void*)minor_pipe_batch_kernel<CLEAN_SYNC_CLUSTER, true>
+                    : (const void*)minor_pipe_batch_kernel<CLEAN_SYNC_CLUSTER, false>;
+  return resident ? (const void*)minor_pipe_batch_kernel<kSyncNone, true>
+                  : (const void*)minor_pipe_batch_kernel<kSyncNone, false>;
+}
+
+bool minor_pipe_batch_geometry(MinorCfg& c, int G, int resident, int max_rows, int max_w) {
+  c = MinorCfg{};
+  c.G = G;
+  c.sync = G > 1 ? CLEAN_SYNC_CLUSTER : kSyncNone;
+  c.resident = resident;
+  c.spin_limit_ns = 2000000000ll;
+  c.chunk_w = 128;
+  c.box_w = kBatchBoxW;
+  c.chunk_h = kBatchBoxRows;
+  const int64_t box = (int64_t)((c.box_w * c.chunk_h + 31) & ~31) * 4;
+  const int64_t stage = (resident ? 1 : 2) * box;
+  c.res_floats = resident ? ((max_rows * ((max_w + 3) & ~3) + 31) & ~31) : 0;
+  const int64_t budget = 200 * 1024 - (int64_t)c.res_floats * 4;
+  c.stages = (int)std::min<int64_t>(kPipeMaxStages, budget / stage);
+  if (c.stages < 2) return false;
+  c.smem = (int)((int64_t)c.res_floats * 4 + c.stages * stage);
+  c.threads = kPipeThreads;
+  c.pipe = 1;
+  return true;
+}
+
+int minor_pipe_batch_cluster(int want, int resident, int smem) {
+  for (int G = std::min(16, std::max(1, want)); G > 1; G /= 2) {
+    const void* fn = pipe_batch_fn(G, resident);
+    if (allow_max_smem(fn) != cudaSuccess) break;
+    if (G > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                     cudaSuccess)
+      continue;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(G, 1, 1);
+    cfg.blockDim = dim3(kPipeThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = G;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) == cudaSuccess && n >= 1) return G;
+  }
+  cudaGetLastError();
+  return 1;
+}
+
+cudaError_t launch_minor_pipe_batch(const PlanDev* plans, const BatchItem* items, int n_items,
+                                    const MinorCfg& c, const CUtensorMap* rmaps,
+                                    const CUtensorMap* pmaps, int round, cudaStream_t s) {
+  if (n_items <= 0) return cudaSuccess;
+  const void* fn = pipe_batch_fn(c.G, c.resident);
+  cudaError_t e = allow_max_smem(fn);
+  if (e != cudaSuccess) return e;
+  if (c.G > 8) {
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)(n_items * c.G), 1, 1);
+  cfg.blockDim = dim3(kPipeThreads, 1, 1);
+  cfg.dynamicSmemBytes = c.smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = c.G;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = c.G > 1 ? 1 : 0;
+  MinorCfg cc = c;
+  void* args[] = {const_cast<PlanDev**>(&plans), const_cast<BatchItem**>(&items),
+                  const_cast<CUtensorMap**>(&rmaps), const_cast<CUtensorMap**>(&pmaps), &cc,
+                  &round};
+  return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
 cudaError_t launch_minor_batch(const PlanDev* plans, const BatchItem* items, int n_items, int G,
