@@ -109,3 +109,26 @@ def test_batch_with_flux_trigger_equals_oracle():
             assert len(comps) == o.n
             assert np.array_equal(comps["flux"].view(np.uint32), o.comps["flux"].view(np.uint32))
             assert np.array_equal(res.cpu().numpy().view(np.uint32), o.residual.view(np.uint32))
+
+
+def test_batch_streamed_pipeline_groups_equal_solo_runs():
+    """Tiles too large for resident slabs run as 16 streaming CTAs of the
+    batched TMA pipeline (2048^2 in one tile, 1536^2 in 1 x 2 tiles);
+    every image still equals its solo run bit for bit."""
+    import torch
+    cases = [(2048, (1, 1), 0, 300), (1536, (1, 2), 25, 400), (256, (2, 2), 10, 300)]
+    data = [_job(n, 1.0 + 0.2 * i, 300 + i) for i, (n, tiles, K, niter) in enumerate(cases)]
+    jobs = [dict(psf=torch.from_numpy(p).cuda(), ny=n, nx=n, gain=0.1, niter=niter,
+                 threshold=0.0, tiles=tiles, feedback_interval=K)
+            for (p, _), (n, tiles, K, niter) in zip(data, cases)]
+    dirties = [torch.from_numpy(d).cuda() for _, d in data]
+    with cg.Batch(jobs) as b:
+        b.run(dirties)
+        for i, (n, tiles, K, niter) in enumerate(cases):
+            res, mod, comps = b.get(i)
+            solo = gpu_clean(data[i][1], data[i][0], 0.1, niter, 0.0, tiles, K)
+            assert len(comps) == solo["n"] == niter
+            assert np.array_equal(comps["flux"].view(np.uint32),
+                                  solo["comps"]["flux"].view(np.uint32)), i
+            assert np.array_equal(res.cpu().numpy().view(np.uint32),
+                                  solo["residual"].view(np.uint32)), i
