@@ -296,15 +296,27 @@ def serve_leg(cg, torch, n_jobs=60, load=0.7):
             b.record()
             torch.cuda.synchronize()
             service.append(a.elapsed_time(b) / 1e3)
-    rate = load / float(np.mean(service))
-    rng = np.random.default_rng(7)
-    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_jobs))
-    arrivals -= arrivals[0]
-    base = serve.fifo_latencies(arrivals, service)
-    jobs = [serve.Job(psf=dev[sp["n"]][0], dirty=dev[sp["n"]][1], niter=sp["niter"],
-                      tiles=sp["tiles"], feedback_interval=sp["K"], arrival=float(t))
-            for sp, t in zip(specs, arrivals)]
-    st = serve.serve(jobs, budget_bytes=150e9, rounds_per_step=2, keep_results=False)
+    gaps = np.random.default_rng(7).exponential(1.0, size=n_jobs)  # unit-rate Poisson
+
+    def stream(ld):
+        rate = ld / float(np.mean(service))
+        arrivals = np.cumsum(gaps / rate)
+        arrivals -= arrivals[0]
+        base = serve.fifo_latencies(arrivals, service)
+        jobs = [serve.Job(psf=dev[sp["n"]][0], dirty=dev[sp["n"]][1], niter=sp["niter"],
+                          tiles=sp["tiles"], feedback_interval=sp["K"], arrival=float(t))
+                for sp, t in zip(specs, arrivals)]
+        st = serve.serve(jobs, budget_bytes=150e9, rounds_per_step=2, keep_results=False)
+        return rate, base, jobs, st
+
+    stream(1.0)  # warm-up: kernels, tensor maps and graphs of every job shape
+    other = {}
+    for ld in (0.5, 0.9):
+        _, b2, _, s2 = stream(ld)
+        other[f"{ld:.1f}"] = {"p50_s": s2["p50_s"], "p99_s": s2["p99_s"],
+                              "one_at_a_time_plain_p50_s": float(np.percentile(b2, 50)),
+                              "one_at_a_time_plain_p99_s": float(np.percentile(b2, 99))}
+    rate, base, jobs, st = stream(load)
     # saturated throughput: every job waiting at t = 0
     for j in jobs:
         j.arrival, j.admitted, j.finished = 0.0, None, None
@@ -319,7 +331,8 @@ def serve_leg(cg, torch, n_jobs=60, load=0.7):
             "one_at_a_time_plain_p99_s": float(np.percentile(base, 99)),
             "saturated_jobs_per_s": sat["jobs_per_s"],
             "saturated_iters_per_s": total_iters / sat["makespan_s"],
-            "one_at_a_time_plain_jobs_per_s": n_jobs / float(np.sum(service))}
+            "one_at_a_time_plain_jobs_per_s": n_jobs / float(np.sum(service)),
+            "other_loads": other}
 
 
 def cpu_baseline(w, data):

@@ -207,10 +207,14 @@ void tile_group(int h, int w, int* G, int* resident, int* smem) {
 
 // CTAs per tile for the batched pipeline: the fewest power-of-two CTAs
 // (<= 16) whose row slabs fit in shared memory beside a ring of at least two
-// PSF boxes, else 16 CTAs streaming their rows.  The group's geometry is
-// checked once the group's largest slab is known.
-void pipe_tile_group(int h, int w, int* G, int* resident, int* rows) {
-  for (int g = 1; g <= 16; g *= 2) {
+// PSF boxes, and, when `fast`, at least one CTA per 8192 pixels (each
+// iteration's pass stays short, as in the single-plan choice); else 16 CTAs
+// streaming their rows.  The group's geometry is checked once the group's
+// largest slab is known.
+void pipe_tile_group(int h, int w, bool fast, int* G, int* resident, int* rows) {
+  int g0 = 1;
+  while (fast && g0 < 16 && (int64_t)g0 * 8192 < (int64_t)h * w) g0 *= 2;
+  for (int g = g0; g <= 16; g *= 2) {
     MinorCfg c;
     const int r = (h + g - 1) / g;
     if (minor_pipe_batch_geometry(c, g, 1, r, w)) {
@@ -245,6 +249,29 @@ int engine_rebuild(clean_engine_s* e, cudaStream_t s) {
   };
   std::vector<Sized> all;
   int block0 = 0;
+  // latency or throughput: when the tiles of every resident image fit on the
+  // SMs even with one CTA per 8192 pixels, use that many (short iterations);
+  // otherwise the fewest CTAs that hold each tile (the launches run in waves
+  // anyway, and fewer, larger CTAs lose less to exchanges)
+  bool fast = true;
+  {
+    int64_t ctas = 0;
+    for (int i : work) {
+      const Job& j = e->jobs[i];
+      for (int t = 0; t < j.dev.T; ++t) {
+        const Rect r = tile_rect(t, j.dev.ny, j.dev.nx, j.dev.ty, j.dev.tx);
+        int g = 1, res = 0, rows = 0, sm = 0;
+        if (j.pipe)
+          pipe_tile_group(r.y1 - r.y0, r.x1 - r.x0, true, &g, &res, &rows);
+        else
+          tile_group(r.y1 - r.y0, r.x1 - r.x0, &g, &res, &sm);
+        ctas += g;
+      }
+    }
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, e->device);
+    fast = ctas <= sms;
+  }
   e->blocks_tma = e->blocks_plain = 0;
   for (int w = 0; w < (int)work.size(); ++w) {
     const Job& j = e->jobs[work[w]];
@@ -261,7 +288,7 @@ int engine_rebuild(clean_engine_s* e, cudaStream_t s) {
       z.pipe = j.pipe ? 1 : 0;
       z.w = r.x1 - r.x0;
       if (z.pipe) {
-        pipe_tile_group(r.y1 - r.y0, z.w, &z.G, &z.resident, &z.rows);
+        pipe_tile_group(r.y1 - r.y0, z.w, fast, &z.G, &z.resident, &z.rows);
         z.smem = 0;
       } else {
         tile_group(r.y1 - r.y0, z.w, &z.G, &z.resident, &z.smem);
