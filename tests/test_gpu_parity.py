@@ -392,3 +392,32 @@ def test_checkpoint_resume_equals_uninterrupted_run(mode):
     for k in ("y", "x", "tile", "round"):
         assert np.array_equal(got[2][k], want[2][k])
     assert np.array_equal(got[2]["flux"].view(np.uint32), want[2]["flux"].view(np.uint32))
+
+
+DEGENERATE = [
+    # (ny, nx, psf, tiles, K, niter, threshold): one-pixel images and tiles,
+    # strips, a one-pixel PSF, budgets smaller than the tile count, a single
+    # iteration, a threshold above every pixel
+    (1, 1, (1, 1), (1, 1), 0, 5, 0.0),
+    (1, 40, (1, 80), (1, 4), 2, 30, 0.0),
+    (40, 1, (80, 1), (5, 1), 3, 30, 0.0),
+    (8, 8, (16, 16), (8, 8), 1, 100, 0.0),
+    (30, 30, (1, 1), (3, 3), 2, 200, 0.0),
+    (20, 20, (40, 40), (4, 4), 2, 7, 0.0),
+    (20, 20, (40, 40), (2, 2), 2, 50, 100.0),
+    (16, 16, (32, 32), (2, 2), 1, 1, 0.0),
+]
+
+
+@pytest.mark.parametrize("case", DEGENERATE, ids=[f"{c[0]}x{c[1]}-psf{c[2][0]}x{c[2][1]}-t{c[3][0]}x{c[3][1]}-n{c[5]}"
+                                                  for c in DEGENERATE])
+def test_degenerate_bit_exact(case):
+    ny, nx, ps, tiles, K, niter, thr = case
+    rng = np.random.default_rng(ny * 131 + nx)
+    psf = synth.random_psf(*ps, rng) if ps[0] * ps[1] > 1 else np.ones((1, 1), np.float32)
+    dirty = synth.random_image(ny, nx, rng)
+    o = oracle.clean_f32(dirty, psf, 0.3, niter, thr, tiles, K)
+    g = gpu_clean(dirty, psf, 0.3, niter, thr, tiles, K)
+    assert_bit_exact(g, o, str(case))
+    if thr >= 100.0:
+        assert g["n"] == 0 and np.array_equal(g["residual"], dirty)
