@@ -277,8 +277,10 @@ CLEAN_API int clean_hogbom_noalloc(const float* d_dirty, const float* d_psf, int
  * one CTA per (image, tile), largest tiles first, and one feedback launch over
  * every image's blocks.  The paper treats one image; batching changes only
  * which CTA serves which tile, so each image's results are bit for bit those
- * of its own clean_plan + clean_run (exact gather feedback; FFT feedback and
- * the untiled mode are not accepted). */
+ * of its own clean_plan + clean_run.  Images with FFT feedback (feedback_mode
+ * FFT, or AUTO when the plan picks it) share the minor-loop launches and run
+ * their own transforms and kernels for the feedback.  The untiled mode
+ * (CLEAN_UNTILED_GRID) is not accepted: a one-tile grid serves instead. */
 typedef struct clean_batch_s* clean_batch_t;
 
 /* Creates a batch of n images: params[i] as for clean_plan (checked before
@@ -329,7 +331,7 @@ typedef struct clean_server_s* clean_server_t;
 /* A server with room for max_jobs resident jobs. */
 CLEAN_API int clean_server_create(clean_server_t* out, int32_t max_jobs, void* stream);
 
-/* Adds a job: params as for clean_plan (tiled, gather feedback), d_psf
+/* Adds a job: params as for clean_plan (CLEAN_TILED), d_psf
  * BORROWED until clean_server_remove, d_dirty read by this call's set-up
  * (stream-ordered) only.  Allocates the job's state and synchronises (PSF
  * check).  *job_id identifies it from then on. */

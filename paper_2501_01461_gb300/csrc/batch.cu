@@ -40,6 +40,7 @@ struct Job {
   // residual and PSF box maps of the batched minor-loop pipeline
   CUtensorMap rmap{}, pmap{};
   bool pipe = false;
+  bool fft = false;  // feedback by FFT convolution (the job's own launches)
   int64_t id = 0;
   int slot = 0;
   bool finished = false;
@@ -71,7 +72,9 @@ struct clean_engine_s {
   CUtensorMap* d_rmaps = nullptr;       // [cap] minor-loop residual boxes
   CUtensorMap* d_pmaps = nullptr;       // [cap] minor-loop PSF boxes
   std::vector<Group> groups;
-  int n_work = 0, n_tma = 0, blocks_tma = 0, blocks_plain = 0, max_T = 1;
+  int n_work = 0, n_tma = 0, n_gather = 0, blocks_tma = 0, blocks_plain = 0, max_T = 1;
+  std::vector<int> fft_work;            // work positions of FFT-feedback jobs
+  std::vector<int> work_jobs;           // job index of each work position
   bool dirty = true;                    // work lists need a rebuild
   int round = 0;                        // rounds launched so far (global)
   int64_t next_id = 1;
@@ -151,6 +154,7 @@ int engine_start(clean_engine_s* e, Job& j, const float* d_dirty, cudaStream_t s
   if (err == cudaSuccess) err = launch_init(j.dev, d_dirty, plan_niter(j.plan), s);
   ++e->kernel_launches;
   if (err == cudaSuccess) err = launch_first_level(j.dev, s);
+  if (err == cudaSuccess && j.fft) err = plan_fft_start(j.plan, j.dev, s);
   if (err != cudaSuccess) return eng_fail(e, CLEAN_ERR_CUDA);
   std::memset(&e->h_states[j.slot], 0, sizeof(DevState));
   e->h_states[j.slot].active = 1;  // refreshed at the next status read
@@ -164,13 +168,11 @@ int engine_register(clean_engine_s* e, const clean_params* p, const float* d_psf
   if (e->free_slots.empty()) return CLEAN_ERR_OOM;
   int rc = clean_params_check(p);
   if (rc != CLEAN_OK) return rc;
-  if (!d_psf || p->mode != CLEAN_TILED || p->feedback_mode == CLEAN_FB_FFT)
-    return CLEAN_ERR_INVALID_ARG;
-  clean_params q = *p;
-  q.feedback_mode = CLEAN_FB_GATHER;
+  if (!d_psf || p->mode != CLEAN_TILED) return CLEAN_ERR_INVALID_ARG;
   Job j;
-  rc = clean_plan(&j.plan, &q, d_psf, s);
+  rc = clean_plan(&j.plan, p, d_psf, s);
   if (rc != CLEAN_OK) return rc;
+  j.fft = plan_uses_fft(j.plan);
   j.slot = e->free_slots.back();
   e->free_slots.pop_back();
   j.dev = plan_device_state(j.plan);
@@ -234,10 +236,16 @@ int engine_rebuild(clean_engine_s* e, cudaStream_t s) {
   std::vector<int> work;
   for (int i = 0; i < (int)e->jobs.size(); ++i)
     if (!e->jobs[i].finished) work.push_back(i);
-  // TMA-fed images first, so each feedback launch covers a contiguous range
-  std::stable_partition(work.begin(), work.end(), [&](int i) { return e->jobs[i].tma; });
+  // gather images fed by TMA first, then gather images with plain loads (each
+  // feedback launch covers a contiguous range), FFT-feedback images last
+  std::stable_partition(work.begin(), work.end(), [&](int i) { return !e->jobs[i].fft; });
+  std::stable_partition(work.begin(), work.end(),
+                        [&](int i) { return !e->jobs[i].fft && e->jobs[i].tma; });
   e->n_work = (int)work.size();
   e->n_tma = 0;
+  e->n_gather = 0;
+  e->fft_work.clear();
+  e->work_jobs = work;
   e->max_T = 1;
   std::vector<PlanDev> plans;
   std::vector<CUtensorMap> maps, rmaps, pmaps;
@@ -279,7 +287,11 @@ int engine_rebuild(clean_engine_s* e, cudaStream_t s) {
     maps.push_back(j.map);
     rmaps.push_back(j.rmap);
     pmaps.push_back(j.pmap);
-    if (j.tma) ++e->n_tma;
+    if (j.fft)
+      e->fft_work.push_back(w);
+    else
+      ++e->n_gather;
+    if (j.tma && !j.fft) ++e->n_tma;
     e->max_T = std::max(e->max_T, j.dev.T);
     for (int t = 0; t < j.dev.T; ++t) {
       const Rect r = tile_rect(t, j.dev.ny, j.dev.nx, j.dev.ty, j.dev.tx);
@@ -305,9 +317,11 @@ int engine_rebuild(clean_engine_s* e, cudaStream_t s) {
     im.bx = bx;
     im.by = by;
     im.nblocks = bx * by * j.dev.T;
-    block0 += im.nblocks;
+    if (!j.fft) {
+      block0 += im.nblocks;
+      (j.tma ? e->blocks_tma : e->blocks_plain) += im.nblocks;
+    }
     imgs.push_back(im);
-    (j.tma ? e->blocks_tma : e->blocks_plain) += im.nblocks;
   }
   // groups of equal (kernel, G, resident), biggest tiles first within each
   std::stable_sort(all.begin(), all.end(), [](const Sized& a, const Sized& b) {
@@ -429,9 +443,17 @@ cudaError_t launch_round(clean_engine_s* e, int round, cudaStream_t s, int* n) {
   }
   if (e->blocks_plain > 0) {
     err = launch_feedback_batch(e->d_plans + e->n_tma, e->d_imgs + e->n_tma,
-                                e->n_work - e->n_tma, e->blocks_plain, e->max_T, nullptr,
+                                e->n_gather - e->n_tma, e->blocks_plain, e->max_T, nullptr,
                                 round, 1, 2000000000ull, s);
     ++*n;
+    if (err != cudaSuccess) return err;
+  }
+  // FFT-feedback images: each its own transforms and kernels
+  for (int w : e->fft_work) {
+    const Job& j = e->jobs[e->work_jobs[w]];
+    err = plan_fft_round(j.plan, j.dev, (round - j.dev.round0) & 1, s);
+    *n += 5;
+    if (err != cudaSuccess) return err;
   }
   return err;
 }
@@ -549,8 +571,7 @@ int clean_batch_create(clean_batch_t* out, int32_t n, const clean_params* params
   for (int i = 0; i < n; ++i) {
     const int rc = clean_params_check(&params[i]);
     if (rc != CLEAN_OK) return rc;
-    if (!d_psfs[i] || params[i].mode != CLEAN_TILED || params[i].feedback_mode == CLEAN_FB_FFT)
-      return CLEAN_ERR_INVALID_ARG;
+    if (!d_psfs[i] || params[i].mode != CLEAN_TILED) return CLEAN_ERR_INVALID_ARG;
   }
   clean_batch_s* b = new (std::nothrow) clean_batch_s();
   if (!b) return CLEAN_ERR_OOM;

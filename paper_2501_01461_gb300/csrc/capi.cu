@@ -251,22 +251,8 @@ int check_psf(clean_plan_s* pl, cudaStream_t s) {
 // One FFT feedback: scatter the round's components, convolve with the PSF
 // through the cached spectrum, R <- R0 - S everywhere, next peaks, close.
 cudaError_t launch_fft_feedback(clean_plan_s* pl, cudaStream_t s) {
-  const int64_t pitch = pl->Lx;
-  const int64_t nspec = (int64_t)pl->Ly * (pl->Lx / 2 + 1);
-  cudaError_t e = fft_launch_scatter(pl->d, pl->fft_A, pitch, s);
-  if (e != cudaSuccess) return e;
-  if (cufftSetStream(pl->fft_r2c, s) != CUFFT_SUCCESS ||
-      cufftSetStream(pl->fft_c2r, s) != CUFFT_SUCCESS ||
-      cufftExecR2C(pl->fft_r2c, pl->fft_A, reinterpret_cast<cufftComplex*>(pl->fft_X)) !=
-          CUFFT_SUCCESS)
-    return cudaErrorUnknown;
-  e = fft_launch_multiply(pl->fft_X, pl->fft_Kh, nspec, 1.0f / ((float)pl->Ly * (float)pl->Lx), s);
-  if (e != cudaSuccess) return e;
-  if (cufftExecC2R(pl->fft_c2r, reinterpret_cast<cufftComplex*>(pl->fft_X), pl->fft_S) !=
-      CUFFT_SUCCESS)
-    return cudaErrorUnknown;
-  pl->kernel_launches += 2;
-  return fft_launch_subtract(pl->d, pl->R0, pl->fft_S, pitch, pl->fft_A, pl->parity, s);
+  pl->kernel_launches += 2;  // the two transforms
+  return plan_fft_round(pl, pl->d, pl->parity, s);
 }
 
 int launch_round_feedback(clean_plan_s* pl, cudaStream_t s) {
@@ -501,6 +487,31 @@ bool plan_psf_tensor_map(const clean_plan_s* pl, CUtensorMap* out) {
 }
 
 int64_t plan_niter(const clean_plan_s* pl) { return pl->p.niter; }
+
+bool plan_uses_fft(const clean_plan_s* pl) { return pl->fft; }
+
+cudaError_t plan_fft_start(clean_plan_s* pl, const PlanDev& d, cudaStream_t s) {
+  return cudaMemcpyAsync(pl->R0, d.R, sizeof(float) * (size_t)d.ny * d.nx,
+                         cudaMemcpyDeviceToDevice, s);
+}
+
+cudaError_t plan_fft_round(clean_plan_s* pl, const PlanDev& d, int parity, cudaStream_t s) {
+  const int64_t pitch = pl->Lx;
+  const int64_t nspec = (int64_t)pl->Ly * (pl->Lx / 2 + 1);
+  cudaError_t e = fft_launch_scatter(d, pl->fft_A, pitch, s);
+  if (e != cudaSuccess) return e;
+  if (cufftSetStream(pl->fft_r2c, s) != CUFFT_SUCCESS ||
+      cufftSetStream(pl->fft_c2r, s) != CUFFT_SUCCESS ||
+      cufftExecR2C(pl->fft_r2c, pl->fft_A, reinterpret_cast<cufftComplex*>(pl->fft_X)) !=
+          CUFFT_SUCCESS)
+    return cudaErrorUnknown;
+  e = fft_launch_multiply(pl->fft_X, pl->fft_Kh, nspec, 1.0f / ((float)pl->Ly * (float)pl->Lx), s);
+  if (e != cudaSuccess) return e;
+  if (cufftExecC2R(pl->fft_c2r, reinterpret_cast<cufftComplex*>(pl->fft_X), pl->fft_S) !=
+      CUFFT_SUCCESS)
+    return cudaErrorUnknown;
+  return fft_launch_subtract(d, pl->R0, pl->fft_S, pitch, pl->fft_A, parity, s);
+}
 
 }  // namespace cleangb
 

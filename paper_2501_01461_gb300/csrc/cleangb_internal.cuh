@@ -240,5 +240,10 @@ int minor_threads();
 PlanDev plan_device_state(const clean_plan_s* pl);
 bool plan_psf_tensor_map(const clean_plan_s* pl, CUtensorMap* out);
 int64_t plan_niter(const clean_plan_s* pl);
+// FFT feedback of a plan on the state `d` (a batch job's copy of the plan's
+// device state, with its own control block and round phase).
+bool plan_uses_fft(const clean_plan_s* pl);
+cudaError_t plan_fft_start(clean_plan_s* pl, const PlanDev& d, cudaStream_t s);
+cudaError_t plan_fft_round(clean_plan_s* pl, const PlanDev& d, int parity, cudaStream_t s);
 
 }  // namespace cleangb

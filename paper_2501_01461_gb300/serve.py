@@ -20,18 +20,37 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import (COMPONENT_DTYPE, CleanError, _check, _dptr, _stream_ptr, lib, make_params)
+from . import (COMPONENT_DTYPE, FB_FFT, FB_GATHER, CleanError, _check, _dptr, _stream_ptr,
+               lib, make_params)
 
 
-def footprint_bytes(n: int, psf_shape, niter: int, tiles=(1, 1), K: int = 0) -> int:
+def _fft_size(m: int) -> int:
+    n = max(m, 1)
+    while True:
+        r = n
+        for f in (2, 3, 5, 7):
+            while r % f == 0:
+                r //= f
+        if r == 1:
+            return n
+        n += 1
+
+
+def footprint_bytes(n: int, psf_shape, niter: int, tiles=(1, 1), K: int = 0,
+                    feedback_mode: int = FB_GATHER) -> int:
     """Device bytes a job holds while resident: residual and model images,
     its PSF (held by the caller but pinned for the job's lifetime), the
-    component list and the round buffer."""
+    component list and the round buffer, and with FFT feedback the
+    convolution grids, spectra and round-start residual."""
     T = tiles[0] * tiles[1]
     per_tile = niter // T + (1 if niter % T else 0)
     cap = min(K, per_tile) if K > 0 else per_tile
-    return int(8 * n * n + 4 * psf_shape[0] * psf_shape[1] + 16 * niter + 16 * T * max(cap, 1)
-               + 8 * niter + 4096)
+    b = (8 * n * n + 4 * psf_shape[0] * psf_shape[1] + 16 * niter + 16 * T * max(cap, 1)
+         + 8 * niter + 4096)
+    if feedback_mode == FB_FFT and T > 1:
+        L = _fft_size(2 * n - 1)
+        b += 2 * 4 * L * L + 2 * 8 * L * (L // 2 + 1) + 4 * n * n
+    return int(b)
 
 
 @dataclass
@@ -44,6 +63,7 @@ class Job:
     threshold: float = 0.0
     tiles: tuple = (1, 1)
     feedback_interval: int = 50
+    feedback_mode: int = FB_GATHER  # FB_FFT: feedback by FFT convolution (within tolerance)
     arrival: float = 0.0           # seconds after the start of serve()
     tag: object = None
     # filled by the server
@@ -61,7 +81,7 @@ class Job:
 
     def footprint(self):
         return footprint_bytes(self.n, tuple(self.psf.shape), self.niter, self.tiles,
-                               self.feedback_interval)
+                               self.feedback_interval, self.feedback_mode)
 
 
 class Server:
@@ -88,7 +108,8 @@ class Server:
         ny, nx = job.dirty.shape
         p = make_params(ny, nx, tuple(job.psf.shape), gain=job.gain, niter=job.niter,
                         threshold=job.threshold, tiles=job.tiles,
-                        feedback_interval=job.feedback_interval)
+                        feedback_interval=job.feedback_interval,
+                        feedback_mode=job.feedback_mode)
         jid = ctypes.c_int64(0)
         _check(lib().clean_server_add(self._h, ctypes.byref(p), _dptr(job.psf, what="psf"),
                                       _dptr(job.dirty, what="dirty"), ctypes.byref(jid),

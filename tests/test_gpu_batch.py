@@ -86,13 +86,40 @@ def test_batch_small_images_equal_oracle_and_resume():
             assert np.array_equal(mod.cpu().numpy().view(np.uint32), o.model.view(np.uint32))
 
 
-def test_batch_rejects_fft_and_untiled():
+def test_batch_rejects_untiled_mode():
     import torch
     psf = torch.from_numpy(synth.make_psf(128, 128)).cuda()
     with pytest.raises(cg.CleanError):
-        cg.Batch([dict(psf=psf, ny=64, nx=64, niter=10, feedback_mode=cg.FB_FFT)])
-    with pytest.raises(cg.CleanError):
         cg.Batch([dict(psf=psf, ny=64, nx=64, niter=10, mode=cg.UNTILED_GRID)])
+
+
+def test_batch_with_fft_feedback_equals_solo_runs():
+    """FFT-feedback images share the minor-loop launches with gather images
+    and run their own transforms; each equals its solo run bit for bit
+    (same kernels, same cuFFT plans), with graphs on and off."""
+    import torch
+    cases = [(256, (2, 2), 10, 600, cg.FB_FFT), (300, (3, 3), 7, 900, cg.FB_GATHER),
+             (512, (4, 4), 20, 1600, cg.FB_FFT), (128, (2, 2), 5, 300, cg.FB_AUTO)]
+    data = [_job(n, 1.0 + 0.1 * i, 400 + i) for i, (n, *_r) in enumerate(cases)]
+    jobs = [dict(psf=torch.from_numpy(p).cuda(), ny=n, nx=n, gain=0.1, niter=niter,
+                 threshold=0.0, tiles=tiles, feedback_interval=K, feedback_mode=mode)
+            for (p, _), (n, tiles, K, niter, mode) in zip(data, cases)]
+    dirties = [torch.from_numpy(d).cuda() for _, d in data]
+    with cg.Batch(jobs) as b:
+        for graphs in (True, False):
+            b.graphs(graphs)
+            b.run(dirties)
+            for i, (n, tiles, K, niter, mode) in enumerate(cases):
+                res, mod, comps = b.get(i)
+                solo = gpu_clean(data[i][1], data[i][0], 0.1, niter, 0.0, tiles, K,
+                                 feedback_mode=mode)
+                assert len(comps) == solo["n"], (i, graphs)
+                assert np.array_equal(comps["flux"].view(np.uint32),
+                                      solo["comps"]["flux"].view(np.uint32)), (i, graphs)
+                assert np.array_equal(res.cpu().numpy().view(np.uint32),
+                                      solo["residual"].view(np.uint32)), (i, graphs)
+                assert np.array_equal(mod.cpu().numpy().view(np.uint32),
+                                      solo["model"].view(np.uint32)), (i, graphs)
 
 
 def test_batch_with_flux_trigger_equals_oracle():

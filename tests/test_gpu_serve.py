@@ -104,3 +104,28 @@ def test_remove_running_job_and_memory_budget_admission():
     serve.serve(jobs, budget_bytes=jobs[0].footprint() * 1.5, keep_results=False)
     order = sorted(jobs, key=lambda j: j.admitted)
     assert order[1].admitted >= order[0].finished - 1e-9
+
+
+def test_served_fft_job_equals_solo_fft_run():
+    """A job asking for FFT feedback, served beside gather jobs, equals its
+    solo FFT run bit for bit."""
+    import torch
+    rng = np.random.default_rng(17)
+    specs = [(256, (2, 2), 800, cg.FB_FFT, 0.0), (192, (2, 2), 500, cg.FB_GATHER, 0.002)]
+    jobs = []
+    for n, tiles, niter, mode, arrival in specs:
+        psf = synth.make_psf(2 * n, 2 * n)
+        ys, xs, fl = synth.make_sky(n, 10, 0.05, 2.1, rng)
+        dirty = synth.make_dirty(psf, n, ys, xs, fl, 1e-3, rng)
+        jobs.append(serve.Job(psf=torch.from_numpy(psf).cuda(), dirty=torch.from_numpy(dirty).cuda(),
+                              niter=niter, tiles=tiles, feedback_interval=10, feedback_mode=mode,
+                              arrival=arrival))
+    serve.serve(jobs, budget_bytes=4e9)
+    for j, (n, tiles, niter, mode, _) in zip(jobs, specs):
+        res, mod, comps = j.result
+        solo = gpu_clean(j.dirty.cpu().numpy(), j.psf.cpu().numpy(), 0.1, niter, 0.0, tiles, 10,
+                         feedback_mode=mode)
+        assert len(comps) == solo["n"]
+        assert np.array_equal(res.cpu().numpy().view(np.uint32), solo["residual"].view(np.uint32))
+        assert np.array_equal(comps["flux"].view(np.uint32), solo["comps"]["flux"].view(np.uint32))
+
