@@ -267,7 +267,7 @@ def test_restore_matches_oracle():
 FB_CASES = [
     # (ny, nx, psf, tiles, K, niter)
     (250, 250, (500, 500), (4, 4), 10, 800),    # ragged tiles, full PSF
-    (130, 200, (100, 120), (3, 2), 6, 400),     # PSF smaller than the image: clipped windows
+    (200, 300, (150, 180), (3, 2), 6, 400),     # PSF smaller than the image: clipped windows
     (256, 256, (512, 512), (2, 2), 300, 1200),  # more components than one staged chunk
     (300, 260, (600, 520), (5, 3), 40, 3000),
     (256, 256, (512, 512), (3, 3), 200, 3600),  # more than 1024 components a round
@@ -288,6 +288,20 @@ def test_feedback_paths_bit_exact(case):
         g = gpu_clean(dirty, psf, 0.1, niter, 0.0, tiles, K, feedback_path=path)
         assert g["stats"]["feedback_tma"] == (1 if path == 2 else 0)
         assert_bit_exact(g, o, f"{case} path={path}")
+
+
+def test_psf_narrower_than_tma_box_uses_plain_loads():
+    """A PSF narrower than the TMA window box (132 floats) cannot be tiled by
+    the tensor map: the plan falls back to plain loads, with the oracle's
+    bits, even when the TMA kernel is requested."""
+    rng = np.random.default_rng(330)
+    psf = synth.random_psf(100, 120, rng)
+    dirty = synth.random_image(130, 200, rng)
+    o = oracle.clean_f32(dirty, psf, 0.1, 400, 0.0, (3, 2), 6)
+    for path in (0, 2):
+        g = gpu_clean(dirty, psf, 0.1, 400, 0.0, (3, 2), 6, feedback_path=path)
+        assert g["stats"]["feedback_tma"] == 0
+        assert_bit_exact(g, o, f"narrow PSF path={path}")
 
 
 def test_plans_with_different_shared_memory_coexist():
