@@ -129,7 +129,8 @@ typedef struct {
   int32_t sm_count;       /* SMs of the device */
   int32_t feedback_tma;   /* 1 if feedback stages PSF windows with TMA */
   int32_t minor_pipe;     /* 1 if the minor loop streams rows with bulk copies */
-  int32_t reserved;
+  int32_t minor_tmem;     /* 1 if the pipeline keeps each CTA's leading chunks in
+                             tensor memory (CLEAN_DEBUG_MINOR_TMEM) */
   int64_t kernel_launches;   /* kernels this plan has launched in total */
   int64_t minor_launches;    /* minor-loop launches timed (CLEAN_DEBUG_TIMING) */
   int64_t feedback_launches; /* feedback launches timed (CLEAN_DEBUG_TIMING) */
@@ -393,6 +394,12 @@ CLEAN_API const char* clean_strerror(int status);
  *   CLEAN_DEBUG_PIPE_STAGES    pipeline tuning: at most this many buffers in
  *                              the ring (0: 8); both fail with
  *                              CLEAN_ERR_INVALID_ARG if the ring no longer fits
+ *   CLEAN_DEBUG_MINOR_TMEM     1 (default): the pipeline keeps each CTA's
+ *                              leading full 128 x 60 chunks (up to 8) in
+ *                              tensor memory for the launch when the
+ *                              configuration allows it (clean_stats_t.
+ *                              minor_tmem); 0: stream every chunk.  Same
+ *                              results, bit for bit.
  *   CLEAN_DEBUG_TIMING         1: bracket every minor-loop and feedback launch
  *                              with CUDA events on its stream and sum their
  *                              durations into clean_stats (0: off, resets)
@@ -407,7 +414,8 @@ enum {
   CLEAN_DEBUG_MINOR_PATH = 5,
   CLEAN_DEBUG_PIPE_CHUNK_PX = 6,
   CLEAN_DEBUG_PIPE_STAGES = 7,
-  CLEAN_DEBUG_GRAPHS = 8
+  CLEAN_DEBUG_GRAPHS = 8,
+  CLEAN_DEBUG_MINOR_TMEM = 9
 };
 CLEAN_API int clean_debug_set(clean_plan_t plan, int32_t what, int64_t value);
 CLEAN_API void clean_debug_alloc_limit(int64_t bytes);

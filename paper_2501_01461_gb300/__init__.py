@@ -32,7 +32,7 @@ TILED, UNTILED_GRID = 0, 1
 SYNC_AUTO, SYNC_CLUSTER, SYNC_GRID = 0, 1, 2
 DEBUG_SPIN_LIMIT_NS, DEBUG_FORCE_TIMEOUT, DEBUG_TIMING = 1, 2, 3
 DEBUG_FEEDBACK_PATH, DEBUG_MINOR_PATH, DEBUG_PIPE_CHUNK_PX, DEBUG_PIPE_STAGES = 4, 5, 6, 7
-DEBUG_GRAPHS = 8
+DEBUG_GRAPHS, DEBUG_MINOR_TMEM = 8, 9
 STATUS = {0: "CLEAN_OK", 1: "CLEAN_ERR_INVALID_ARG", 2: "CLEAN_ERR_NONFINITE",
           3: "CLEAN_ERR_OOM", 4: "CLEAN_ERR_CUDA", 5: "CLEAN_ERR_TIMEOUT",
           6: "CLEAN_ERR_UNSUPPORTED"}
@@ -64,7 +64,7 @@ class Stats(ctypes.Structure):
                 ("group_sync", ctypes.c_int32), ("resident", ctypes.c_int32),
                 ("feedback_mode", ctypes.c_int32), ("sm_count", ctypes.c_int32),
                 ("feedback_tma", ctypes.c_int32), ("minor_pipe", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("kernel_launches", ctypes.c_int64),
+                ("minor_tmem", ctypes.c_int32), ("kernel_launches", ctypes.c_int64),
                 ("minor_launches", ctypes.c_int64), ("feedback_launches", ctypes.c_int64),
                 ("minor_ms", ctypes.c_double), ("feedback_ms", ctypes.c_double),
                 ("graph_launches", ctypes.c_int64)]

@@ -38,6 +38,7 @@ struct clean_plan_s {
   int minor_path = 0;        // 0 auto, 1 plain loads, 2 pipeline
   int pipe_chunk_px = 0;     // pipeline tuning (0: defaults)
   int pipe_stages = 0;
+  bool tmem_allowed = true;  // CLEAN_DEBUG_MINOR_TMEM
   int max_rows = 0, max_w = 0;  // largest CTA slab of the minor loop
   float* psf_own = nullptr;
   bool psf_set = false;
@@ -427,8 +428,26 @@ bool configure_pipe(clean_plan_s* pl) {
     q.resident = 0;
     ok = minor_pipe_geometry(q, pl->max_rows, pl->max_w, pl->pipe_chunk_px, pl->pipe_stages);
   }
-  if (ok) pl->mc_pipe = q;
+  if (ok) {
+    if (!pl->tmem_allowed) q.tmem = 0;
+    pl->mc_pipe = q;
+  }
   return ok;
+}
+
+// Whether every CTA of a tensor-memory configuration keeps its leading
+// chunks in TMEM: the PSF array holds every window of every tile pixel.
+bool tmem_in_use(const clean_plan_s* pl) {
+  if (!pl->mc_pipe.tmem) return false;
+  int maxH = 0, maxW = 0;
+  for (int i = 0; i < pl->d.ty; ++i)
+    maxH = std::max(maxH, (int)(((int64_t)(i + 1) * pl->d.ny) / pl->d.ty -
+                                ((int64_t)i * pl->d.ny) / pl->d.ty));
+  for (int j = 0; j < pl->d.tx; ++j)
+    maxW = std::max(maxW, (int)(((int64_t)(j + 1) * pl->d.nx) / pl->d.tx -
+                                ((int64_t)j * pl->d.nx) / pl->d.tx));
+  return pl->d.cy >= maxH - 1 && pl->d.pny - pl->d.cy >= maxH && pl->d.cx >= maxW - 1 &&
+         pl->d.pnx - pl->d.cx >= maxW;
 }
 
 int common_checks(clean_plan_s* pl) {
@@ -1116,6 +1135,7 @@ int clean_stats(clean_plan_t pl, clean_stats_t* out, void* stream) {
   out->group_sync = pl->mc.sync;
   out->resident = pipe ? pl->mc_pipe.resident : pl->mc.resident;
   out->minor_pipe = pipe ? 1 : 0;
+  out->minor_tmem = (pipe && tmem_in_use(pl)) ? 1 : 0;
   out->feedback_mode = pl->fft ? CLEAN_FB_FFT : CLEAN_FB_GATHER;
   out->feedback_tma =
       (pl->psf_map_ok && pl->feedback_path != 1 && pl->feedback_path != 3) ? 1 : 0;
@@ -1171,6 +1191,22 @@ int clean_debug_set(clean_plan_t pl, int32_t what, int64_t value) {
         cudaGetLastError();
         pl->pipe_chunk_px = old_chunk;
         pl->pipe_stages = old_stages;
+        pl->mc_pipe = old_cfg;
+        return CLEAN_ERR_INVALID_ARG;
+      }
+      return CLEAN_OK;
+    }
+    case CLEAN_DEBUG_MINOR_TMEM: {
+      if (value < 0 || value > 1) return CLEAN_ERR_INVALID_ARG;
+      const bool old_allowed = pl->tmem_allowed;
+      pl->tmem_allowed = value != 0;
+      if (!pl->pipe_ok) return CLEAN_OK;
+      const MinorCfg old_cfg = pl->mc_pipe;
+      DeviceGuard g(pl->device);
+      const bool ok = configure_pipe(pl) && minor_prepare(pl->mc_pipe) == cudaSuccess;
+      if (!ok) {
+        cudaGetLastError();
+        pl->tmem_allowed = old_allowed;
         pl->mc_pipe = old_cfg;
         return CLEAN_ERR_INVALID_ARG;
       }

@@ -135,6 +135,8 @@ struct MinorCfg {
   int32_t box_w;      // TMA box width in floats (chunk_w + 4)
   int32_t stages;
   int32_t res_floats; // resident slab floats (0 when streamed)
+  int32_t tmem;       // 1: each CTA's leading full chunks keep their residual
+                      // in tensor memory for the launch (streamed pipeline)
 };
 
 // Pipeline geometry and shared-memory size for a minor-loop configuration

@@ -425,7 +425,8 @@ template <bool RES, int OFF, int U>
 __device__ __forceinline__ void slab_step(const PlanDev& d, float* sRes, int WR, int ya,
                                           const float* stgR, const float* stgP, int BW, int r0,
                                           int r1, int x, int x0, int g, int rps, int sub, int s,
-                                          float f, float& best_a, int& best_base) {
+                                          float f, float& best_a, int& best_base,
+                                          float4& best_r) {
   constexpr int kWarps = kPipeConsumers / 32;
   float4 rv[U], pa[U], pb[U];
 #pragma unroll
@@ -466,6 +467,7 @@ __device__ __forceinline__ void slab_step(const PlanDev& d, float* sRes, int WR,
     const bool better = m > best_a || (m == best_a && base < best_base);
     best_a = better ? m : best_a;
     best_base = better ? base : best_base;
+    best_r = better ? r : best_r;
   }
 }
 
@@ -474,7 +476,7 @@ __device__ __forceinline__ void chunk_slabs(const PlanDev& d, float* sRes, int W
                                             const float* stgR, const float* stgP, int BW,
                                             int r0, int r1, int c0, int c1, int x0, float f,
                                             int lpr_log2, int s_first, float& best_a,
-                                            int& best_base) {
+                                            int& best_base, float4& best_r) {
   constexpr int kWarps = kPipeConsumers / 32;
   const int lane = threadIdx.x & 31;
   const int g = lane & ((1 << lpr_log2) - 1);
@@ -489,34 +491,96 @@ __device__ __forceinline__ void chunk_slabs(const PlanDev& d, float* sRes, int W
   int s = s_first;
   for (; s + (kSlabUnroll - 1) * kWarps < nslabs; s += kSlabUnroll * kWarps)
     slab_step<RES, OFF, kSlabUnroll>(d, sRes, WR, ya, stgR, stgP, BW, r0, r1, x, x0, g, rps,
-                                     sub, s, f, best_a, best_base);
+                                     sub, s, f, best_a, best_base, best_r);
   if (s + kWarps < nslabs) {
     slab_step<RES, OFF, 2>(d, sRes, WR, ya, stgR, stgP, BW, r0, r1, x, x0, g, rps, sub, s, f,
-                           best_a, best_base);
+                           best_a, best_base, best_r);
     s += 2 * kWarps;
   }
   if (s < nslabs)
     slab_step<RES, OFF, 1>(d, sRes, WR, ya, stgR, stgP, BW, r0, r1, x, x0, g, rps, sub, s, f,
-                           best_a, best_base);
+                           best_a, best_base, best_r);
 }
 
 // The pixel of the best 4-pixel group that holds |R| = best_a first (lowest
-// index), and its signed value, read back from where this thread stored it.
-template <bool RES>
-__device__ __forceinline__ void resolve_group(const PlanDev& d, const float* sRes, int WR,
-                                              int ya, int x0, float best_a, int base,
+// index), and its signed value, from the group's values kept in registers.
+__device__ __forceinline__ void resolve_group(float best_a, int base, const float4& r,
                                               int& best_i, float& best_v) {
-  const int y = base / d.nx, x = base - y * d.nx;
-  const float4 r = RES ? *reinterpret_cast<const float4*>(sRes + (y - ya) * WR + (x - x0))
-                       : *reinterpret_cast<const float4*>(d.R + (int64_t)y * d.nx + x);
   const int k4 = fabsf(r.x) == best_a ? 0 : fabsf(r.y) == best_a ? 1 : fabsf(r.z) == best_a ? 2 : 3;
   best_i = base + k4;
   best_v = k4 == 0 ? r.x : k4 == 1 ? r.y : k4 == 2 ? r.z : r.w;
 }
 
+// One chunk whose residual lives in tensor memory (a full CW = 128, 60-row
+// chunk: warp w owns rows w, w + 15, w + 30, w + 45, lane l the pixels
+// 4l..4l+3 of each, 16 TMEM columns from taddr).  On a launch's first
+// iteration the residual comes from the staged box instead.  Same arithmetic
+// and peak tracking as slab_step.
+template <int OFF>
+__device__ __forceinline__ void tmem_chunk(const PlanDev& d, uint32_t taddr, bool from_box,
+                                           const float* stgR, const float* stgP, int BW,
+                                           int r0, int c0, float f, float& best_a,
+                                           int& best_base, float4& best_r) {
+  constexpr int kWarps = kPipeConsumers / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float4 rv[kSlabUnroll], pa[kSlabUnroll], pb[kSlabUnroll];
+#pragma unroll
+  for (int u = 0; u < kSlabUnroll; ++u) {
+    const float4* rowP4 = reinterpret_cast<const float4*>(stgP + (warp + u * kWarps) * BW);
+    pa[u] = rowP4[lane];
+    if (OFF != 0) pb[u] = rowP4[lane + 1];
+  }
+  if (from_box) {
+#pragma unroll
+    for (int u = 0; u < kSlabUnroll; ++u)
+      rv[u] = reinterpret_cast<const float4*>(stgR + (warp + u * kWarps) * BW)[lane];
+  } else {
+    __syncwarp();
+    ptx::tmem_ld16(taddr, rv);
+  }
+#pragma unroll
+  for (int u = 0; u < kSlabUnroll; ++u) {
+    const float4 a = pa[u];
+    float4 p;
+    if (OFF == 0) {
+      p = a;
+    } else {
+      const float4 b = pb[u];
+      p = OFF == 1 ? make_float4(a.y, a.z, a.w, b.x)
+                   : OFF == 2 ? make_float4(a.z, a.w, b.x, b.y) : make_float4(a.w, b.x, b.y, b.z);
+    }
+    float4 r = rv[u];
+    fms2(r.x, r.y, p.x, p.y, f);
+    fms2(r.z, r.w, p.z, p.w, f);
+    rv[u] = r;
+    const float m = fmaxf(fmaxf(fabsf(r.x), fabsf(r.y)), fmaxf(fabsf(r.z), fabsf(r.w)));
+    const int base = (r0 + warp + u * kWarps) * d.nx + c0 + 4 * lane;
+    const bool better = m > best_a || (m == best_a && base < best_base);
+    best_a = better ? m : best_a;
+    best_base = better ? base : best_base;
+    best_r = better ? r : best_r;
+  }
+  __syncwarp();
+  ptx::tmem_st16(taddr, rv);
+}
+
 // CTA `rank` of the group serving tile t; r_map and p_map describe the
 // residual and PSF boxes (r_map unused when the rows are resident).
-template <int SYNC, bool RES>
+//
+// TM: the CTA's first (up to 8) full chunks keep their residual in tensor
+// memory for the whole launch (16 columns per chunk and consumer warp; warps
+// w, w + 4, w + 8, w + 12 share lane quarter w mod 4 and take columns
+// 128 (w / 4) ..), so those chunks stream only their PSF box: a third fewer
+// bytes per iteration at 4096^2.  Used when every window of the CTA's rows is
+// inside the PSF array (the vector path applies to every iteration) and the
+// CTA owns its SM (shared memory above half of it), so the 512-column
+// allocation never waits.  The residual is read from the staged box in the
+// launch's first iteration and written back to global memory at the end.
+constexpr int kTmemCols = 512;
+constexpr int kTmemChunks = 8;       // 4 warps per lane quarter x 8 chunks x 16 columns
+constexpr int kTmemChunkRows = 60;   // 15 warps x 4 slabs of one row
+
+template <int SYNC, bool RES, bool TM = false>
 __device__ __forceinline__ void minor_pipe_body(const PlanDev& d, const MinorCfg& c, int parity,
                                                 const CUtensorMap* r_map,
                                                 const CUtensorMap* p_map, int t, int rank) {
@@ -530,6 +594,7 @@ __device__ __forceinline__ void minor_pipe_body(const PlanDev& d, const MinorCfg
   __shared__ uint64_t s_best;
   __shared__ int s_abort;    // grid-barrier timeout: leave the loop
   __shared__ int s_dead;     // mbarrier timeout: stop working, keep exchanging
+  __shared__ uint32_t s_tmem;  // TMEM base address (TM)
 
   const int G = c.G;
   const Rect rc = tile_rect(t, d.ny, d.nx, d.ty, d.tx);
@@ -543,12 +608,36 @@ __device__ __forceinline__ void minor_pipe_body(const PlanDev& d, const MinorCfg
   const int box_floats = (BW * BH + 31) & ~31;  // each box starts 128-byte aligned
   const int stage_floats = (RES ? 1 : 2) * box_floats;
   const uint32_t stage_bytes = (uint32_t)((RES ? 1 : 2) * BW * BH) * 4u;  // bytes the boxes land
+  const uint32_t p_box_bytes = (uint32_t)(BW * BH) * 4u;
   const int nrb = (yb - ya + BH - 1) / BH, ncb = (W + CW - 1) / CW;
   const int nch = nrb * ncb;                // chunks per iteration
   const uint64_t limit = (uint64_t)c.spin_limit_ns;
   const int WR = (W + 3) & ~3;              // resident slab row stride
 
   if (*(volatile int32_t*)&d.st->status != 0) return;  // uniform, see minor_kernel
+
+  // consumer geometry within a chunk: row slabs of 4-pixel groups (vector
+  // path, CW = 32, 64 or 128) or single pixels, threads per row a power of two
+  const bool vec_cols = (x0 % 4) == 0 && (W % 4) == 0 && (CW == 32 || CW == 64 || CW == 128);
+
+  // tensor-memory chunks: the leading full chunks, when every peak of the
+  // tile puts this CTA's whole window inside the PSF array
+  int n_tm = 0;
+  if (TM && c.tmem && vec_cols && CW == 128 && BH == kTmemChunkRows &&
+      ya + d.cy - (rc.y1 - 1) >= 0 && yb - 1 + d.cy - rc.y0 < d.pny &&
+      x0 + d.cx - (x1 - 1) >= 0 && x1 - 1 + d.cx - x0 < d.pnx) {
+    while (n_tm < kTmemChunks && n_tm < nch) {
+      const int rb = n_tm / ncb, cb = n_tm - rb * ncb;
+      if (ya + (rb + 1) * BH > yb || x0 + (cb + 1) * CW > x1) break;
+      ++n_tm;
+    }
+  }
+  const bool tm_on = TM && n_tm > 0;
+  if (tm_on && warp == 0) {
+    ptx::tmem_alloc(&s_tmem, kTmemCols);
+    ptx::tmem_relinquish();
+    ptx::tmem_fence_before_sync();
+  }
 
   uint64_t key = d.peak[parity * d.T + t];
   const int64_t budget = d.budget[t];
@@ -577,10 +666,12 @@ __device__ __forceinline__ void minor_pipe_body(const PlanDev& d, const MinorCfg
     }
   }
   __syncthreads();
+  if (tm_on) ptx::tmem_fence_after_sync();
+  // this warp's lane quarter and first column (the producer warp's is unused)
+  const uint32_t tm_base =
+      tm_on ? s_tmem + (((uint32_t)(warp & 3) * 32u) << 16) + (uint32_t)(warp >> 2) * 128u : 0u;
+  bool tm_filled = false;  // tensor memory holds this launch's residual
 
-  // consumer geometry within a chunk: row slabs of 4-pixel groups (vector
-  // path, CW = 32, 64 or 128) or single pixels, threads per row a power of two
-  const bool vec_cols = (x0 % 4) == 0 && (W % 4) == 0 && (CW == 32 || CW == 64 || CW == 128);
   const int lpr_log2 = CW == 128 ? 5 : CW == 64 ? 4 : 3;
   const int slabs = (BH + (32 >> lpr_log2) - 1) / (32 >> lpr_log2);  // per full chunk
   int tpr = 1;
@@ -629,8 +720,10 @@ __device__ __forceinline__ void minor_pipe_body(const PlanDev& d, const MinorCfg
             break;
           const int r0 = ya + rb * BH, c0 = x0 + cb * CW;
           float* stg = sStage + (size_t)p_st * stage_floats;
-          ptx::mbar_arrive_expect_tx(&full_bar[p_st], stage_bytes);
-          if (!RES) ptx::tma_load_2d(stg, r_map, c0 & ~3, r0, &full_bar[p_st]);
+          // a tensor-memory chunk needs its residual box only in iteration 0
+          const bool r_box = !RES && !(TM && ch < n_tm && k > 0);
+          ptx::mbar_arrive_expect_tx(&full_bar[p_st], r_box ? stage_bytes : p_box_bytes);
+          if (r_box) ptx::tma_load_2d(stg, r_map, c0 & ~3, r0, &full_bar[p_st]);
           ptx::tma_load_2d(stg + (RES ? 0 : box_floats), p_map, (c0 + dx) & ~3, r0 + dy,
                            &full_bar[p_st]);
           ++jnext;
@@ -646,12 +739,21 @@ __device__ __forceinline__ void minor_pipe_body(const PlanDev& d, const MinorCfg
       }
     } else {
       int best_base = 0x7fffffff;
+      float4 best_r = make_float4(0.f, 0.f, 0.f, 0.f);
       int rb = 0, cb = 0;
+      // the previous iteration's tensor-memory stores land before this
+      // iteration reads them back
+      if (tm_on && k > 0) {
+        __syncwarp();
+        ptx::tmem_wait_st();
+      }
       for (int ch = 0; ch < nch; ++ch) {
         const int st = c_st;
-        if (*(volatile int*)&s_dead ||
-            !pipe_wait(&full_bar[st], c_ph, limit, &s_dead, &d.st->status))
-          break;
+        bool ok = !*(volatile int*)&s_dead &&
+                  pipe_wait(&full_bar[st], c_ph, limit, &s_dead, &d.st->status);
+        // tensor-memory accesses are warp-wide: the whole warp stops or none
+        if (TM) ok = __all_sync(0xffffffffu, ok);
+        if (!ok) break;
         if (++c_st == S) {
           c_st = 0;
           c_ph ^= 1u;
@@ -666,25 +768,47 @@ __device__ __forceinline__ void minor_pipe_body(const PlanDev& d, const MinorCfg
         const float* stgR = stg;                            // streamed residual box
         const float* stgP = stg + (RES ? 0 : box_floats);   // PSF box
         const int offR = c0 - (c0 & ~3), offP = (c0 + dx) - ((c0 + dx) & ~3);
-        if (fast) {
+        if (TM && fast && ch < n_tm) {
+          // full chunk, rot == 0 (60 slabs a chunk): warp w owns slabs w + 15u
+          const uint32_t ta = tm_base + (uint32_t)ch * 16u;
+          const bool from_box = k == 0;
+          switch (offP) {
+            case 0:
+              tmem_chunk<0>(d, ta, from_box, stgR, stgP, BW, r0, c0, f, best_a, best_base,
+                            best_r);
+              break;
+            case 1:
+              tmem_chunk<1>(d, ta, from_box, stgR, stgP, BW, r0, c0, f, best_a, best_base,
+                            best_r);
+              break;
+            case 2:
+              tmem_chunk<2>(d, ta, from_box, stgR, stgP, BW, r0, c0, f, best_a, best_base,
+                            best_r);
+              break;
+            default:
+              tmem_chunk<3>(d, ta, from_box, stgR, stgP, BW, r0, c0, f, best_a, best_base,
+                            best_r);
+              break;
+          }
+        } else if (fast) {
           // continue the slab round-robin where the previous chunk ended
           const int s_first = warp >= rot ? warp - rot : warp + kW - rot;
           switch (offP) {
             case 0:
               chunk_slabs<RES, 0>(d, sRes, WR, ya, stgR, stgP, BW, r0, r1, c0, c1, x0, f,
-                                  lpr_log2, s_first, best_a, best_base);
+                                  lpr_log2, s_first, best_a, best_base, best_r);
               break;
             case 1:
               chunk_slabs<RES, 1>(d, sRes, WR, ya, stgR, stgP, BW, r0, r1, c0, c1, x0, f,
-                                  lpr_log2, s_first, best_a, best_base);
+                                  lpr_log2, s_first, best_a, best_base, best_r);
               break;
             case 2:
               chunk_slabs<RES, 2>(d, sRes, WR, ya, stgR, stgP, BW, r0, r1, c0, c1, x0, f,
-                                  lpr_log2, s_first, best_a, best_base);
+                                  lpr_log2, s_first, best_a, best_base, best_r);
               break;
             default:
               chunk_slabs<RES, 3>(d, sRes, WR, ya, stgR, stgP, BW, r0, r1, c0, c1, x0, f,
-                                  lpr_log2, s_first, best_a, best_base);
+                                  lpr_log2, s_first, best_a, best_base, best_r);
               break;
           }
         } else {
@@ -710,8 +834,8 @@ __device__ __forceinline__ void minor_pipe_body(const PlanDev& d, const MinorCfg
         __syncwarp();
         if (lane == 0) ptx::mbar_arrive(&empty_bar[st]);
       }
-      if (fast && best_a >= 0.f)
-        resolve_group<RES>(d, sRes, WR, ya, x0, best_a, best_base, best_i, best_v);
+      if (fast && best_a >= 0.f) resolve_group(best_a, best_base, best_r, best_i, best_v);
+      tm_filled = tm_on && !*(volatile int*)&s_dead;
       // residual rows written through the generic proxy are read back by TMA
       // (async proxy) in the next iteration
       if (!RES) asm volatile("fence.proxy.async.global;" ::: "memory");
@@ -723,6 +847,34 @@ __device__ __forceinline__ void minor_pipe_body(const PlanDev& d, const MinorCfg
     ++k;
   }
 
+  if (tm_on) {
+    // tensor-memory chunks back to global memory, then free the columns
+    if (!producer) {
+      __syncwarp();
+      ptx::tmem_wait_st();
+      const bool wb = __shfl_sync(0xffffffffu, (int)(tm_filled && !*(volatile int*)&s_dead), 0);
+      if (wb) {
+        for (int ch = 0; ch < n_tm; ++ch) {
+          const int rb = ch / ncb, cb = ch - rb * ncb;
+          const int r0 = ya + rb * BH, c0 = x0 + cb * CW;
+          float4 v[kSlabUnroll];
+          __syncwarp();
+          ptx::tmem_ld16(tm_base + (uint32_t)ch * 16u, v);
+#pragma unroll
+          for (int u = 0; u < kSlabUnroll; ++u)
+            *reinterpret_cast<float4*>(d.R + (int64_t)(r0 + warp + u * (kW)) * d.nx + c0 +
+                                       4 * lane) = v[u];
+        }
+      }
+    }
+    ptx::tmem_fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+      ptx::tmem_fence_after_sync();
+      __syncwarp();
+      ptx::tmem_dealloc(s_tmem, kTmemCols);
+    }
+  }
   if (SYNC == CLEAN_SYNC_CLUSTER) cluster_sync_all();
   if (producer && lane == 0 && s_dead) {
     // after an expired wait: let this CTA's own copies in flight land
@@ -747,14 +899,14 @@ __device__ __forceinline__ void minor_pipe_body(const PlanDev& d, const MinorCfg
   }
 }
 
-template <int SYNC, bool RES>
+template <int SYNC, bool RES, bool TM>
 __global__ void __launch_bounds__(kPipeThreads, 1)
     minor_pipe_kernel(PlanDev d, MinorCfg c, int parity,
                       const __grid_constant__ CUtensorMap r_map,
                       const __grid_constant__ CUtensorMap p_map) {
   const int t = blockIdx.x / c.G;
   const int rank = (SYNC == CLEAN_SYNC_CLUSTER) ? (int)cluster_rank() : (int)(blockIdx.x % c.G);
-  minor_pipe_body<SYNC, RES>(d, c, parity, &r_map, &p_map, t, rank);
+  minor_pipe_body<SYNC, RES, TM>(d, c, parity, &r_map, &p_map, t, rank);
 }
 
 // Batched pipeline launch: one CTA (kSyncNone) or one cluster of G CTAs per
@@ -773,17 +925,19 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
 }
 
 template <int SYNC, bool RES>
-void* kernel_ptr(bool pipe) {
-  return pipe ? (void*)minor_pipe_kernel<SYNC, RES> : (void*)minor_kernel<SYNC, RES>;
+void* kernel_ptr(bool pipe, bool tmem) {
+  if (!pipe) return (void*)minor_kernel<SYNC, RES>;
+  if (!RES && tmem) return (void*)minor_pipe_kernel<SYNC, false, true>;
+  return (void*)minor_pipe_kernel<SYNC, RES, false>;
 }
 
 void* pick(const MinorCfg& c) {
-  const bool p = c.pipe != 0;
+  const bool p = c.pipe != 0, tm = c.tmem != 0;
   if (c.sync == CLEAN_SYNC_CLUSTER)
-    return c.resident ? kernel_ptr<CLEAN_SYNC_CLUSTER, true>(p)
-                      : kernel_ptr<CLEAN_SYNC_CLUSTER, false>(p);
-  return c.resident ? kernel_ptr<CLEAN_SYNC_GRID, true>(p)
-                    : kernel_ptr<CLEAN_SYNC_GRID, false>(p);
+    return c.resident ? kernel_ptr<CLEAN_SYNC_CLUSTER, true>(p, tm)
+                      : kernel_ptr<CLEAN_SYNC_CLUSTER, false>(p, tm);
+  return c.resident ? kernel_ptr<CLEAN_SYNC_GRID, true>(p, tm)
+                    : kernel_ptr<CLEAN_SYNC_GRID, false>(p, tm);
 }
 
 }  // namespace
@@ -987,6 +1141,11 @@ bool minor_pipe_geometry(MinorCfg& c, int max_rows, int max_w, int chunk_px, int
   c.smem = (int)total;
   c.threads = kPipeThreads;
   c.pipe = 1;
+  // tensor-memory chunks: streamed 128 x 60 chunks, and shared memory above
+  // half of an SM's 228 KB so that no second CTA of this kernel shares the SM
+  // (the 512-column allocation then never waits)
+  c.tmem = (!c.resident && c.chunk_w == 128 && c.chunk_h == kTmemChunkRows &&
+            c.smem > 114 * 1024) ? 1 : 0;
   return true;
 }
 

@@ -1,5 +1,6 @@
 // Inline-PTX helpers for sm_103a: mbarriers, 2-D TMA tile loads, cluster
-// barriers and the global timer.  Every wait here is bounded by the caller.
+// barriers, the global timer and tensor-memory (TMEM) storage.  Every wait
+// here is bounded by the caller.
 #pragma once
 
 #include <cstdint>
@@ -102,6 +103,80 @@ __device__ __forceinline__ void tma_load_2d(void* smem_dst, const CUtensorMap* m
 
 __device__ __forceinline__ void prefetch_tensormap(const CUtensorMap* map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Tensor memory (TMEM): 128 lanes x 512 columns of 32-bit cells per SM.  A
+// warp reaches only the 32 lanes of its quarter (warp index mod 4); thread i
+// of the warp reads and writes lane 32 * (warp mod 4) + i.  Allocation and
+// deallocation are warp-wide; the CTA must free what it took before it exits.
+// ---------------------------------------------------------------------------
+
+// Allocates `ncols` columns (a power of two, 32..512) and writes the base
+// address to *dst (shared memory).  Warp-wide.
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_u32(dst)),
+               "r"(ncols)
+               : "memory");
+}
+
+// This CTA will allocate no more TMEM (lets other CTAs on the SM allocate).
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+// Frees `ncols` columns at `taddr`.  Warp-wide.
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+
+// Orders this thread's TMEM operations before / after a thread barrier.
+__device__ __forceinline__ void tmem_fence_before_sync() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_fence_after_sync() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Reads 16 consecutive columns of this thread's lane starting at `taddr`
+// (lane in bits 31..16, column in bits 15..0) and waits for the values, so
+// the outputs are complete when the statement ends.  Warp-wide.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float4 (&v)[4]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+    v[u] = make_float4(__uint_as_float(r[4 * u]), __uint_as_float(r[4 * u + 1]),
+                       __uint_as_float(r[4 * u + 2]), __uint_as_float(r[4 * u + 3]));
+}
+
+// Writes 16 consecutive columns of this thread's lane (asynchronous: call
+// tmem_wait_st before the cells are read again or freed).  Warp-wide.
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float4 (&v)[4]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+      "r"(__float_as_uint(v[0].x)), "r"(__float_as_uint(v[0].y)), "r"(__float_as_uint(v[0].z)),
+      "r"(__float_as_uint(v[0].w)), "r"(__float_as_uint(v[1].x)), "r"(__float_as_uint(v[1].y)),
+      "r"(__float_as_uint(v[1].z)), "r"(__float_as_uint(v[1].w)), "r"(__float_as_uint(v[2].x)),
+      "r"(__float_as_uint(v[2].y)), "r"(__float_as_uint(v[2].z)), "r"(__float_as_uint(v[2].w)),
+      "r"(__float_as_uint(v[3].x)), "r"(__float_as_uint(v[3].y)), "r"(__float_as_uint(v[3].z)),
+      "r"(__float_as_uint(v[3].w))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
 }  // namespace ptx

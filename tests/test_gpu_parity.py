@@ -136,6 +136,47 @@ def test_minor_paths_bit_exact(case):
         assert_bit_exact(g, o, f"{case} path={path}")
 
 
+TMEM_CASES = [
+    # (ny, nx, psf, tiles, K, niter, G, threshold, expect_flag): streamed
+    # pipeline slabs whose leading full 128 x 60 chunks live in tensor memory
+    (512, 512, (1024, 1024), (1, 1), 0, 400, 2, 0.0, 1),     # 8 TMEM chunks a CTA
+    (512, 512, (900, 1024), (1, 1), 0, 400, 4, 0.0, 0),      # only the middle CTAs qualify
+    (512, 600, (1024, 1200), (1, 1), 0, 300, 2, 0.0, 1),     # ragged 88-column chunk ends the run
+    (1024, 1024, (2048, 2048), (2, 2), 20, 600, 2, 0.0, 1),  # feedback between launches
+    (512, 512, (1024, 1024), (1, 2), 1, 120, 1, 0.0, 1),     # one iteration a launch
+    (512, 512, (1024, 1024), (1, 1), 0, 4000, 2, 0.05, 1),   # threshold stops mid-launch
+]
+
+
+@pytest.mark.parametrize("case", TMEM_CASES, ids=[f"{c[0]}x{c[1]}-psf{c[2][0]}x{c[2][1]}-t{c[3][0]}x{c[3][1]}-K{c[4]}-G{c[6]}"
+                                                  for c in TMEM_CASES])
+def test_minor_tmem_bit_exact(case):
+    """The pipeline with each CTA's leading chunks in tensor memory gives the
+    oracle's bits, as does the same pipeline streaming every chunk; CTAs whose
+    windows can leave the PSF array stream all their chunks."""
+    ny, nx, ps, tiles, K, niter, G, thr, flag = case
+    rng = np.random.default_rng(ny * 7 + nx + G)
+    if ps[0] >= 2 * ny and ps[1] >= 2 * nx:
+        psf = synth.make_psf(*ps)
+        ys, xs, fl = synth.make_sky(min(ny, nx), 12, 0.05, 2.1, rng)
+        d = synth.make_dirty(psf, min(ny, nx), ys, xs, fl, 1e-3, rng)
+        dirty = synth.random_image(ny, nx, rng, 1e-3)
+        dirty[:d.shape[0], :d.shape[1]] += d
+    else:
+        psf = synth.random_psf(*ps, rng)
+        dirty = synth.random_image(ny, nx, rng)
+    o = oracle.clean_f32(dirty, psf, 0.1, niter, thr, tiles, K)
+    for tm in (1, 0):
+        g = gpu_clean(dirty, psf, 0.1, niter, thr, tiles, K, group_ctas=G,
+                      group_sync=cg.SYNC_GRID, minor_path=2, minor_tmem=tm)
+        st = g["stats"]
+        assert st["minor_pipe"] == 1 and st["resident"] == 0
+        assert st["minor_tmem"] == (flag if tm else 0), st
+        assert_bit_exact(g, o, f"{case} tmem={tm}")
+    if thr > 0:
+        assert o.n < niter  # the threshold, not the budget, ended the run
+
+
 def test_untiled_grid_256():
     """Plain Hogbom CLEAN on the whole GPU: 256^2 image, 512^2 PSF, 20
     sources, gain 0.1, 2000 iterations, threshold 5 mJy."""
