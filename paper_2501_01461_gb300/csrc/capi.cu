@@ -728,7 +728,7 @@ int clean_plan(clean_plan_t* out, const clean_params* p, const float* d_psf, voi
   };
   // FFT feedback: a grid of at least (2 ny - 1) x (2 nx - 1) so the circular
   // convolution never wraps onto an image pixel.  AUTO takes it when a round's
-  // gather (about 0.23 ns per pixel-component update on GB300) would cost more
+  // gather (about 0.21 ns per pixel-component update on GB300) would cost more
   // than the transforms (estimated 16 ps per grid cell plus 60 us of launches).
   const bool fb_on = (p->feedback_interval > 0 || p->feedback_trigger > 0.f) && T > 1;
   const int fb_mode = forced_feedback_mode(p->feedback_mode);
@@ -739,7 +739,7 @@ int clean_plan(clean_plan_t* out, const clean_params* p, const float* d_psf, voi
     const double comps =
         (double)(p->feedback_interval > 0 ? std::min<int64_t>(p->feedback_interval, per_tile_max)
                                           : per_tile_max) * T;
-    const double gather_s = comps * ((double)npix - (double)npix / T) * 0.23e-9;
+    const double gather_s = comps * ((double)npix - (double)npix / T) * 0.21e-9;
     const double fft_s = (double)pl->Ly * pl->Lx * 16e-12 + 60e-6;
     pl->fft = fft_s < gather_s;
   }
