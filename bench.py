@@ -57,6 +57,10 @@ def parse():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
     ap.add_argument("--untiled-iters", type=int, default=2000,
                     help="iterations of the untiled whole-GPU comparison run (0: skip)")
+    ap.add_argument("--sweep", action="store_true",
+                    help="the measurement plan's other configurations: 256^2 untiled and "
+                         "1024^2 tiled in full (GPU and CPU oracle), 4096^2 at K = 10..200 "
+                         "(exact and FFT feedback); one JSON line, no headline")
     ap.add_argument("--profile", type=int, default=0, metavar="R",
                     help="profiling target: one run of the workload truncated to R rounds "
                          "(no warm-up, no timing, no JSON line)")
@@ -395,6 +399,87 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_sweep(args):
+    """The measurement plan's configurations besides the headline: the 256^2
+    untiled workload and the 1024^2 tiled one run in full on the GPU and on
+    the CPU oracle (one thread, and the oracle's arithmetic on all host
+    cores), and the 4096^2 workload at feedback intervals 10, 20, 50, 100 and
+    200 with exact (gather) and FFT feedback.  GPU figures are the median of
+    three CUDA-event-timed runs after one warm-up, with a 512 MiB write
+    between runs; each run deconvolves the whole image."""
+    import torch
+
+    import oracle
+    import paper_2501_01461_gb300 as cg
+    cg.lib()
+    oracle.build()
+    oracle.build_parallel()
+    cores = oracle.parallel_threads(os.cpu_count() or 1)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def gpu(w, data, thr, K, mode=cg.TILED, fb=cg.FB_GATHER, reps=3):
+        P = torch.from_numpy(data["psf"]).cuda()
+        D = torch.from_numpy(data["dirty"]).cuda()
+        with cg.Plan(P, w.n, w.n, gain=w.gain, niter=w.niter, threshold=thr, tiles=w.tiles,
+                     feedback_interval=K, mode=mode, feedback_mode=fb) as p:
+            p.run(D)
+            torch.cuda.synchronize()
+            ms = []
+            for i in range(reps):
+                flush.fill_(float(i))
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                p.run(D)
+                b.record(stream)
+                torch.cuda.synchronize()
+                ms.append(a.elapsed_time(b))
+            n = p.n_components()
+        med = sorted(ms)[len(ms) // 2]
+        return {"iters": n, "ms": med, "iters_per_s": n / (med / 1e3)}
+
+    def cpu(w, data, thr, K, parallel):
+        t0 = time.perf_counter()
+        if parallel:
+            r = oracle.parallel_clean_f32(data["dirty"], data["psf"], w.gain, w.niter, thr,
+                                          w.tiles, K)
+        else:
+            r = oracle.clean_f32(data["dirty"], data["psf"], w.gain, w.niter, thr, w.tiles, K)
+        dt = time.perf_counter() - t0
+        return {"iters": r.n, "s": dt, "iters_per_s": r.n / dt}
+
+    def cfgd(w, thr):
+        c = config_dict(w)
+        c.pop("l2", None)
+        c["threshold"] = thr
+        return c
+
+    out = {"sweep": True, "unit": UNIT, "cpu_cores": cores}
+    w0 = synth.workload("untiled-256")
+    d0 = w0.build()
+    out["untiled-256"] = {
+        "config": cfgd(w0, w0.threshold),
+        "gpu_untiled_grid": gpu(w0, d0, w0.threshold, 0, mode=cg.UNTILED_GRID),
+        "cpu_oracle_1_thread": cpu(w0, d0, w0.threshold, 0, False),
+        "cpu_oracle_all_cores": cpu(w0, d0, w0.threshold, 0, True)}
+    w1 = synth.workload("tiled-1024")
+    d1 = w1.build(threshold=0.0)
+    out["tiled-1024"] = {
+        "config": cfgd(w1, 0.0),
+        "gpu_gather": gpu(w1, d1, 0.0, w1.feedback_interval),
+        "gpu_fft": gpu(w1, d1, 0.0, w1.feedback_interval, fb=cg.FB_FFT),
+        "cpu_oracle_1_thread": cpu(w1, d1, 0.0, w1.feedback_interval, False),
+        "cpu_oracle_all_cores": cpu(w1, d1, 0.0, w1.feedback_interval, True)}
+    w2 = synth.workload("tiled-4096")
+    d2 = w2.build(threshold=0.0)
+    ks = {}
+    for K in (10, 20, 50, 100, 200):
+        ks[str(K)] = {"gpu_gather": gpu(w2, d2, 0.0, K, reps=2),
+                      "gpu_fft": gpu(w2, d2, 0.0, K, fb=cg.FB_FFT, reps=2)}
+    out["tiled-4096-K"] = {"config": cfgd(w2, 0.0), "by_K": ks}
+    print(json.dumps(out))
+
+
 def config_dict(w):
     return {"workload": w.name, "image": f"{w.n}x{w.n}", "psf": f"{w.psf_n}x{w.psf_n}",
             "tiles": f"{w.tiles[0]}x{w.tiles[1]}", "feedback_interval": w.feedback_interval,
@@ -409,6 +494,9 @@ def main():
         return
     if args.profile > 0:
         run_profile(args)
+        return
+    if args.sweep:
+        run_sweep(args)
         return
     import torch
 
