@@ -312,6 +312,8 @@ FB_CASES = [
     (256, 256, (512, 512), (2, 2), 300, 1200),  # more components than one staged chunk
     (300, 260, (600, 520), (5, 3), 40, 3000),
     (256, 256, (512, 512), (3, 3), 200, 3600),  # more than 1024 components a round
+    (512, 1000, (1024, 2000), (2, 2), 25, 1200),  # ragged 500-wide tiles: 4 blocks, the last 116
+    (512, 512, (600, 700), (2, 2), 10, 600),      # 256-wide tiles, clipped windows
 ]
 
 
