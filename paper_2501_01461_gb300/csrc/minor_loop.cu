@@ -912,7 +912,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
 // Batched pipeline launch: one CTA (kSyncNone) or one cluster of G CTAs per
 // (image, tile) item, each image's plan state in `plans` and its residual and
 // PSF box maps in rmaps / pmaps (global memory, indexed like `plans`).
-template <int SYNC, bool RES>
+template <int SYNC, bool RES, bool TM>
 __global__ void __launch_bounds__(kPipeThreads, 1)
     minor_pipe_batch_kernel(const PlanDev* __restrict__ plans,
                             const BatchItem* __restrict__ items, const CUtensorMap* rmaps,
@@ -920,8 +920,8 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
   const BatchItem it = items[blockIdx.x / c.G];
   const PlanDev d = plans[it.image];
   const int rank = (SYNC == CLEAN_SYNC_CLUSTER) ? (int)cluster_rank() : 0;
-  minor_pipe_body<SYNC, RES>(d, c, (round - d.round0) & 1, rmaps + it.image, pmaps + it.image,
-                             it.tile, rank);
+  minor_pipe_body<SYNC, RES, TM>(d, c, (round - d.round0) & 1, rmaps + it.image,
+                                 pmaps + it.image, it.tile, rank);
 }
 
 template <int SYNC, bool RES>
@@ -979,12 +979,18 @@ int minor_batch_cluster(int want, int resident, int smem) {
 
 // ---- batched pipeline --------------------------------------------------------
 
-const void* pipe_batch_fn(int G, int resident) {
+// tmem: the streamed variant that keeps each CTA's leading chunks in tensor
+// memory (every CTA owns its SM: the ring takes more than half of its
+// shared memory, so a later CTA starts there only after this one freed its
+// columns)
+const void* pipe_batch_fn(int G, int resident, int tmem) {
   if (G > 1)
-    return resident ? (const void*)minor_pipe_batch_kernel<CLEAN_SYNC_CLUSTER, true>
-                    : (const void*)minor_pipe_batch_kernel<CLEAN_SYNC_CLUSTER, false>;
-  return resident ? (const void*)minor_pipe_batch_kernel<kSyncNone, true>
-                  : (const void*)minor_pipe_batch_kernel<kSyncNone, false>;
+    return resident ? (const void*)minor_pipe_batch_kernel<CLEAN_SYNC_CLUSTER, true, false>
+           : tmem   ? (const void*)minor_pipe_batch_kernel<CLEAN_SYNC_CLUSTER, false, true>
+                    : (const void*)minor_pipe_batch_kernel<CLEAN_SYNC_CLUSTER, false, false>;
+  return resident ? (const void*)minor_pipe_batch_kernel<kSyncNone, true, false>
+         : tmem   ? (const void*)minor_pipe_batch_kernel<kSyncNone, false, true>
+                  : (const void*)minor_pipe_batch_kernel<kSyncNone, false, false>;
 }
 
 bool minor_pipe_batch_geometry(MinorCfg& c, int G, int resident, int max_rows, int max_w) {
@@ -1005,12 +1011,13 @@ bool minor_pipe_batch_geometry(MinorCfg& c, int G, int resident, int max_rows, i
   c.smem = (int)((int64_t)c.res_floats * 4 + c.stages * stage);
   c.threads = kPipeThreads;
   c.pipe = 1;
+  c.tmem = (!resident && c.smem > 114 * 1024) ? 1 : 0;
   return true;
 }
 
 int minor_pipe_batch_cluster(int want, int resident, int smem) {
   for (int G = std::min(16, std::max(1, want)); G > 1; G /= 2) {
-    const void* fn = pipe_batch_fn(G, resident);
+    const void* fn = pipe_batch_fn(G, resident, 0);
     if (allow_max_smem(fn) != cudaSuccess) break;
     if (G > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
                      cudaSuccess)
@@ -1037,7 +1044,7 @@ cudaError_t launch_minor_pipe_batch(const PlanDev* plans, const BatchItem* items
                                     const MinorCfg& c, const CUtensorMap* rmaps,
                                     const CUtensorMap* pmaps, int round, cudaStream_t s) {
   if (n_items <= 0) return cudaSuccess;
-  const void* fn = pipe_batch_fn(c.G, c.resident);
+  const void* fn = pipe_batch_fn(c.G, c.resident, c.tmem);
   cudaError_t e = allow_max_smem(fn);
   if (e != cudaSuccess) return e;
   if (c.G > 8) {
