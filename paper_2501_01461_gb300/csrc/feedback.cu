@@ -751,16 +751,38 @@ __global__ void fft_kernel_image(const float* __restrict__ P, int pny, int pnx, 
   }
 }
 
-// The round's components onto the (zeroed) grid: one thread per tile, its
-// components in iteration order, so the sums are deterministic.
+// The round's components onto the (zeroed) grid: one warp per tile (a
+// tile's components lie inside it, so tiles never share a cell).  Lane l
+// takes components l, l + 32, ...; the first component at a cell sums every
+// component of the tile at that cell in iteration order and writes the cell
+// once, so each cell gets ((0 + f1) + f2) + ... exactly as one thread adding
+// them in order would.  Above kScatterQuadMax components the quadratic
+// search gives way to one thread in order.
+constexpr int kScatterQuadMax = 4096;
 __global__ void fft_scatter(PlanDev d, float* __restrict__ A, int64_t pitch) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
   if (t >= d.T) return;
   const int n = d.rcount[t];
-  for (int k = 0; k < n; ++k) {
-    const clean_component cc = d.rcomps[(int64_t)t * d.cap_round + k];
-    float* a = &A[(int64_t)cc.y * pitch + cc.x];
-    *a = *a + cc.flux;
+  const clean_component* c = d.rcomps + (int64_t)t * d.cap_round;
+  if (n > kScatterQuadMax) {
+    if (lane == 0)
+      for (int k = 0; k < n; ++k) {
+        float* a = &A[(int64_t)c[k].y * pitch + c[k].x];
+        *a = *a + c[k].flux;
+      }
+    return;
+  }
+  for (int k = lane; k < n; k += 32) {
+    const clean_component ck = c[k];
+    bool first = true;
+    for (int j = 0; j < k && first; ++j) first = !(c[j].y == ck.y && c[j].x == ck.x);
+    if (!first) continue;
+    float* a = &A[(int64_t)ck.y * pitch + ck.x];
+    float acc = *a + ck.flux;
+    for (int j = k + 1; j < n; ++j)
+      if (c[j].y == ck.y && c[j].x == ck.x) acc = acc + c[j].flux;
+    *a = acc;
   }
 }
 
@@ -857,7 +879,7 @@ cudaError_t fft_build_kernel_image(const PlanDev& d, int Ly, int Lx, float* Kimg
 }
 
 cudaError_t fft_launch_scatter(const PlanDev& d, float* A, int64_t pitch, cudaStream_t s) {
-  fft_scatter<<<(d.T + 127) / 128, 128, 0, s>>>(d, A, pitch);
+  fft_scatter<<<(d.T + 3) / 4, 128, 0, s>>>(d, A, pitch);  // a warp per tile
   return cudaGetLastError();
 }
 
