@@ -563,6 +563,8 @@ def main():
     rec = ncu_traffic()
     traffic = {k: v["bytes_per_launch"] for k, v in rec.items()}
     fb_lts = rec.get("feedback_tma_kernel", {}).get("lts_pct")
+    minor_name = ("minor_pair_kernel" if st.get("minor_pairs") else "minor_pipe_kernel") \
+        if st["minor_pipe"] else "minor_kernel"
     if st["feedback_ms"] >= st["minor_ms"]:
         roof = {"kernel": "feedback_tma_kernel" if st["feedback_tma"] else "feedback_kernel",
                 "bound": "alu", "achieved": fb_tflops, "peak": alu_peak, "unit": "TFLOP/s",
@@ -579,20 +581,20 @@ def main():
                         + (f" (ncu: lts__throughput {fb_lts:.1f} % of peak, "
                            "profiles/feedback_tma_kernel_tiled-4096.md)" if fb_lts else "")}
     else:
-        roof = {"kernel": "minor_pipe_kernel" if st["minor_pipe"] else "minor_kernel",
+        roof = {"kernel": minor_name,
                 "bound": "hbm", "achieved": minor_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": minor_gbs / peaks["hbm_gbs"],
-                "traffic": traffic.get("minor_pipe_kernel") if st["minor_pipe"] else None,
+                "traffic": traffic.get(minor_name),
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs, copy burst)",
                 "bytes_per_launch": minor_b,
                 "note": "12 B per pixel per tile iteration; the hot set is L2-resident"}
     kernels = {
-        "minor": {"kernel": "minor_pipe_kernel" if st["minor_pipe"] else "minor_kernel",
+        "minor": {"kernel": minor_name,
                   "ms_per_step": st["minor_ms"] / args.steps,
                   "launches_per_step": rounds_per_run,
                   "algorithmic_GBps": minor_gbs, "frac_of_hbm_peak": minor_gbs / peaks["hbm_gbs"],
                   "bytes_per_launch": minor_b,
-                  "traffic": traffic.get("minor_pipe_kernel") if st["minor_pipe"] else None},
+                  "traffic": traffic.get(minor_name)},
         "feedback": {"kernel": "feedback_tma_kernel" if st["feedback_tma"] else "feedback_kernel",
                      "ms_per_step": st["feedback_ms"] / args.steps,
                      "launches_per_step": st["feedback_launches"] / args.steps,

@@ -137,6 +137,8 @@ typedef struct {
   double minor_ms;           /* summed CUDA-event time of the timed minor launches */
   double feedback_ms;        /* summed CUDA-event time of the timed feedback launches */
   int64_t graph_launches;    /* two-round CUDA graphs launched (CLEAN_DEBUG_GRAPHS) */
+  int64_t minor_pairs;       /* 1 if the minor loop serves tiles in pairs
+                                (CLEAN_DEBUG_MINOR_PAIR) */
 } clean_stats_t;
 
 /* Fills *p with defaults: gain 0.1, threshold 0, 1 x 1 tiles, K 0, gather
@@ -400,6 +402,13 @@ CLEAN_API const char* clean_strerror(int status);
  *                              configuration allows it (clean_stats_t.
  *                              minor_tmem); 0: stream every chunk.  Same
  *                              results, bit for bit.
+ *   CLEAN_DEBUG_MINOR_PAIR     1 (default): with grid groups, streamed rows and
+ *                              an even number of tiles at least 256 pixels
+ *                              wide, groups of 2G CTAs serve pairs of tiles
+ *                              and alternate between them, so one tile's
+ *                              exchange overlaps the other's pass
+ *                              (clean_stats_t.minor_pairs); 0: a group per
+ *                              tile.  Same results, bit for bit.
  *   CLEAN_DEBUG_TIMING         1: bracket every minor-loop and feedback launch
  *                              with CUDA events on its stream and sum their
  *                              durations into clean_stats (0: off, resets)
@@ -415,7 +424,8 @@ enum {
   CLEAN_DEBUG_PIPE_CHUNK_PX = 6,
   CLEAN_DEBUG_PIPE_STAGES = 7,
   CLEAN_DEBUG_GRAPHS = 8,
-  CLEAN_DEBUG_MINOR_TMEM = 9
+  CLEAN_DEBUG_MINOR_TMEM = 9,
+  CLEAN_DEBUG_MINOR_PAIR = 10
 };
 CLEAN_API int clean_debug_set(clean_plan_t plan, int32_t what, int64_t value);
 CLEAN_API void clean_debug_alloc_limit(int64_t bytes);

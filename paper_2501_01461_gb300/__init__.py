@@ -23,7 +23,8 @@ __all__ = ["CleanError", "Plan", "Batch", "lib", "library_path", "build", "STATU
            "FB_GATHER", "FB_FFT", "FB_AUTO", "TILED", "UNTILED_GRID",
            "SYNC_AUTO", "SYNC_CLUSTER", "SYNC_GRID", "COMPONENT_DTYPE",
            "DEBUG_SPIN_LIMIT_NS", "DEBUG_FORCE_TIMEOUT", "DEBUG_TIMING", "DEBUG_FEEDBACK_PATH", "DEBUG_MINOR_PATH",
-           "DEBUG_PIPE_CHUNK_PX", "DEBUG_PIPE_STAGES", "DEBUG_GRAPHS",
+           "DEBUG_PIPE_CHUNK_PX", "DEBUG_PIPE_STAGES", "DEBUG_GRAPHS", "DEBUG_MINOR_TMEM",
+           "DEBUG_MINOR_PAIR",
            "EXPORTED_SYMBOLS"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -32,7 +33,7 @@ TILED, UNTILED_GRID = 0, 1
 SYNC_AUTO, SYNC_CLUSTER, SYNC_GRID = 0, 1, 2
 DEBUG_SPIN_LIMIT_NS, DEBUG_FORCE_TIMEOUT, DEBUG_TIMING = 1, 2, 3
 DEBUG_FEEDBACK_PATH, DEBUG_MINOR_PATH, DEBUG_PIPE_CHUNK_PX, DEBUG_PIPE_STAGES = 4, 5, 6, 7
-DEBUG_GRAPHS, DEBUG_MINOR_TMEM = 8, 9
+DEBUG_GRAPHS, DEBUG_MINOR_TMEM, DEBUG_MINOR_PAIR = 8, 9, 10
 STATUS = {0: "CLEAN_OK", 1: "CLEAN_ERR_INVALID_ARG", 2: "CLEAN_ERR_NONFINITE",
           3: "CLEAN_ERR_OOM", 4: "CLEAN_ERR_CUDA", 5: "CLEAN_ERR_TIMEOUT",
           6: "CLEAN_ERR_UNSUPPORTED"}
@@ -67,7 +68,7 @@ class Stats(ctypes.Structure):
                 ("minor_tmem", ctypes.c_int32), ("kernel_launches", ctypes.c_int64),
                 ("minor_launches", ctypes.c_int64), ("feedback_launches", ctypes.c_int64),
                 ("minor_ms", ctypes.c_double), ("feedback_ms", ctypes.c_double),
-                ("graph_launches", ctypes.c_int64)]
+                ("graph_launches", ctypes.c_int64), ("minor_pairs", ctypes.c_int64)]
 
 
 # name -> (restype, argtypes); the C ABI of include/cleangb.h

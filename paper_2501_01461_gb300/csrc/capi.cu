@@ -39,6 +39,7 @@ struct clean_plan_s {
   int pipe_chunk_px = 0;     // pipeline tuning (0: defaults)
   int pipe_stages = 0;
   bool tmem_allowed = true;  // CLEAN_DEBUG_MINOR_TMEM
+  bool pair_allowed = true;  // CLEAN_DEBUG_MINOR_PAIR
   int max_rows = 0, max_w = 0;  // largest CTA slab of the minor loop
   float* psf_own = nullptr;
   bool psf_set = false;
@@ -399,7 +400,7 @@ int start_run(clean_plan_s* pl, const float* d_dirty, cudaStream_t s) {
   if (e == cudaSuccess) e = cudaMemsetAsync(pl->d.st, 0, sizeof(DevState), s);
   // grid-barrier key slots start with mark bit 63 set (see exchange_keys)
   if (e == cudaSuccess)
-    e = cudaMemsetAsync(pl->d.gkeys, 0x80, sizeof(uint64_t) * 2 * (size_t)pl->d.T * pl->mc.G, s);
+    e = cudaMemsetAsync(pl->d.gkeys, 0x80, sizeof(uint64_t) * 4 * (size_t)pl->d.T * pl->mc.G, s);
   if (e == cudaSuccess) e = launch_init(pl->d, d_dirty, pl->p.niter, s);
   ++pl->kernel_launches;
   if (e == cudaSuccess && pl->d.trigger > 0.f) {
@@ -417,6 +418,22 @@ int start_run(clean_plan_s* pl, const float* d_dirty, cudaStream_t s) {
   return CLEAN_OK;
 }
 
+// Tile pairs (see minor_loop.cu): streamed rows in grid groups, an even
+// number of tiles, each at least two chunks wide (both column halves hold a
+// chunk), and at most 128 CTAs a tile (the pair's 2G exchange slots are
+// polled by one warp).
+bool pair_ok(const clean_plan_s* pl, const MinorCfg& q) {
+  if (!pl->pair_allowed || q.resident || q.sync != CLEAN_SYNC_GRID || q.G > 128) return false;
+  const int T = pl->p.tiles_y * pl->p.tiles_x;
+  if (T < 2 || (T % 2) != 0) return false;
+  for (int j = 0; j < pl->p.tiles_x; ++j) {
+    const int w = (int)(((int64_t)(j + 1) * pl->p.nx) / pl->p.tiles_x -
+                        ((int64_t)j * pl->p.nx) / pl->p.tiles_x);
+    if (w < 2 * q.chunk_w) return false;
+  }
+  return true;
+}
+
 // Pipeline geometry for the plan's group: resident slab when it fits beside
 // the ring, else streamed rows.
 bool configure_pipe(clean_plan_s* pl) {
@@ -430,6 +447,7 @@ bool configure_pipe(clean_plan_s* pl) {
   }
   if (ok) {
     if (!pl->tmem_allowed) q.tmem = 0;
+    q.pair = pair_ok(pl, q) ? 1 : 0;
     pl->mc_pipe = q;
   }
   return ok;
@@ -755,7 +773,8 @@ int clean_plan(clean_plan_t* out, const clean_params* p, const float* d_psf, voi
       {(void**)&pl->d.rcomps, sizeof(clean_component) * (size_t)(cap_round * T)},
       {(void**)&pl->d.list, sizeof(clean_component) * (size_t)list_cap},
       {(void**)&pl->d.round_off, sizeof(int64_t) * (size_t)(list_cap + 1)},
-      {(void**)&pl->d.gkeys, sizeof(uint64_t) * 2 * (size_t)T * (size_t)mc.G},
+      // 2 slot sets x T tiles x 2G slots (tile pairs exchange over 2G CTAs)
+      {(void**)&pl->d.gkeys, sizeof(uint64_t) * 4 * (size_t)T * (size_t)mc.G},
       {(void**)&pl->d.gbar, sizeof(uint32_t) * (size_t)T},
       {(void**)&pl->d.st, sizeof(DevState)},
       {(void**)&pl->beam_buf, sizeof(float) * (size_t)beam_n},
@@ -1076,7 +1095,7 @@ int clean_resume(clean_plan_t pl, const void* h_buf, int64_t bytes, void* stream
   // the grid exchange restarts its count; its key slots start marked
   if (e == cudaSuccess) e = cudaMemsetAsync(pl->d.gbar, 0, sizeof(uint32_t) * pl->d.T, s);
   if (e == cudaSuccess)
-    e = cudaMemsetAsync(pl->d.gkeys, 0x80, sizeof(uint64_t) * 2 * (size_t)pl->d.T * pl->mc.G, s);
+    e = cudaMemsetAsync(pl->d.gkeys, 0x80, sizeof(uint64_t) * 4 * (size_t)pl->d.T * pl->mc.G, s);
   if (e == cudaSuccess && pl->fft) {
     e = cudaMemcpyAsync(pl->R0, pl->d.R, sizeof(float) * (size_t)npix, cudaMemcpyDeviceToDevice,
                         s);
@@ -1136,6 +1155,7 @@ int clean_stats(clean_plan_t pl, clean_stats_t* out, void* stream) {
   out->resident = pipe ? pl->mc_pipe.resident : pl->mc.resident;
   out->minor_pipe = pipe ? 1 : 0;
   out->minor_tmem = (pipe && tmem_in_use(pl)) ? 1 : 0;
+  out->minor_pairs = (pipe && pl->mc_pipe.pair) ? 1 : 0;
   out->feedback_mode = pl->fft ? CLEAN_FB_FFT : CLEAN_FB_GATHER;
   out->feedback_tma =
       (pl->psf_map_ok && pl->feedback_path != 1 && pl->feedback_path != 3) ? 1 : 0;
@@ -1191,6 +1211,30 @@ int clean_debug_set(clean_plan_t pl, int32_t what, int64_t value) {
         cudaGetLastError();
         pl->pipe_chunk_px = old_chunk;
         pl->pipe_stages = old_stages;
+        pl->mc_pipe = old_cfg;
+        return CLEAN_ERR_INVALID_ARG;
+      }
+      return CLEAN_OK;
+    }
+    case CLEAN_DEBUG_MINOR_PAIR: {
+      if (value < 0 || value > 1) return CLEAN_ERR_INVALID_ARG;
+      const bool old_allowed = pl->pair_allowed;
+      pl->pair_allowed = value != 0;
+      if (!pl->pipe_ok) return CLEAN_OK;
+      const MinorCfg old_cfg = pl->mc_pipe;
+      DeviceGuard g(pl->device);
+      bool ok = configure_pipe(pl) && minor_prepare(pl->mc_pipe) == cudaSuccess;
+      // pairs exchange over 2G slots a tile: a changed layout restarts the
+      // exchange count with every slot marked (as at a run's start)
+      if (ok && pl->mc_pipe.pair != old_cfg.pair)
+        ok = cudaDeviceSynchronize() == cudaSuccess &&
+             cudaMemset(pl->d.gkeys, 0x80, sizeof(uint64_t) * 4 * (size_t)pl->d.T * pl->mc.G) ==
+                 cudaSuccess &&
+             cudaMemset(pl->d.gbar, 0, sizeof(uint32_t) * (size_t)pl->d.T) == cudaSuccess &&
+             cudaDeviceSynchronize() == cudaSuccess;
+      if (!ok) {
+        cudaGetLastError();
+        pl->pair_allowed = old_allowed;
         pl->mc_pipe = old_cfg;
         return CLEAN_ERR_INVALID_ARG;
       }

@@ -137,6 +137,8 @@ struct MinorCfg {
   int32_t res_floats; // resident slab floats (0 when streamed)
   int32_t tmem;       // 1: each CTA's leading full chunks keep their residual
                       // in tensor memory for the launch (streamed pipeline)
+  int32_t pair;       // 1: groups of 2G CTAs serve pairs of tiles, alternating
+                      // between them (streamed pipeline, grid groups, T even)
 };
 
 // Pipeline geometry and shared-memory size for a minor-loop configuration

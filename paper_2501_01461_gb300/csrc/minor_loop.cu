@@ -909,6 +909,463 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
   minor_pipe_body<SYNC, RES, TM>(d, c, parity, &r_map, &p_map, t, rank);
 }
 
+// ---------------------------------------------------------------------------
+// Tile pairs.  The exchange that ends a tile's iteration (every CTA of the
+// group publishes its partial peak, then waits for all of them) and the
+// latency of the next iteration's first window leave the SMs idle for a few
+// microseconds per iteration.  Two tiles have no dependence on each other
+// within a round, so a group of 2G CTAs serves a pair of tiles and
+// alternates between them: while the consumer warps subtract the window of
+// one tile, the producer warp waits for the other tile's exchange and starts
+// loading its next windows.  CTA q of the pair's group owns row band q mod G
+// of column half q / G of both tiles (halves split at a whole number of
+// 128-pixel chunks), so its chunks keep their full 128 x 60 shape and up to
+// 4 chunks of each tile live in tensor memory (columns 64 X + 16 ch of its
+// warp's 128).
+//
+// Step s serves tile X = s mod 2 (steps of a finished tile are skipped on
+// both sides alike).  The producer's lane 0 publishes the step's key in
+// s_key (0: the tile is finished) and arrives on key_bar; the consumers wait
+// on key_bar, process the tile's chunks and leave their partial keys in
+// shared memory; the last warp to finish posts the CTA's key to the tile's
+// exchange slot with the usual phase mark.  The producer warp reads
+// the exchange of the tile's previous iteration, which every CTA posted one
+// step earlier, so the wait overlaps the other tile's pass.  Exchange g of
+// tile t is posted after reading exchange g - 1, so the argument that keeps
+// slots from being overwritten early is the single-tile one.  The last
+// exchange of a launch is posted and never read; the next launch's count
+// continues past it.
+// ---------------------------------------------------------------------------
+struct Piece {
+  int t;                 // tile
+  int ya, yb, x0, x1;    // this CTA's rows and columns of the tile
+  int ncb, nch;          // chunks per row of chunks, chunks per pass
+  int n_tm;              // leading full chunks kept in tensor memory (<= 4)
+  bool vec;              // 16-byte-aligned columns: the vector path is possible
+};
+
+__device__ __forceinline__ Piece pair_piece(const PlanDev& d, int t, int band, int half, int G,
+                                            int BH, int CW, bool tm_ok) {
+  Piece p;
+  const Rect rc = tile_rect(t, d.ny, d.nx, d.ty, d.tx);
+  const int H = rc.y1 - rc.y0, W = rc.x1 - rc.x0;
+  p.t = t;
+  p.ya = rc.y0 + (int)(((int64_t)band * H) / G);
+  p.yb = rc.y0 + (int)(((int64_t)(band + 1) * H) / G);
+  const int w0 = min(W, ((W / 2) + CW - 1) / CW * CW);
+  p.x0 = half == 0 ? rc.x0 : rc.x0 + w0;
+  p.x1 = half == 0 ? rc.x0 + w0 : rc.x1;
+  const int Wp = p.x1 - p.x0;
+  const int nrb = Wp > 0 ? (p.yb - p.ya + BH - 1) / BH : 0;
+  p.ncb = (Wp + CW - 1) / CW;
+  p.nch = nrb * p.ncb;
+  p.vec = (p.x0 % 4) == 0 && (Wp % 4) == 0 && (CW == 32 || CW == 64 || CW == 128);
+  p.n_tm = 0;
+  if (tm_ok && p.vec && CW == 128 && BH == kTmemChunkRows && p.nch > 0 &&
+      p.ya + d.cy - (rc.y1 - 1) >= 0 && p.yb - 1 + d.cy - rc.y0 < d.pny &&
+      p.x0 + d.cx - (rc.x1 - 1) >= 0 && p.x1 - 1 + d.cx - rc.x0 < d.pnx) {
+    while (p.n_tm < kTmemChunks / 2 && p.n_tm < p.nch) {
+      const int rb = p.n_tm / p.ncb, cb = p.n_tm - rb * p.ncb;
+      if (p.ya + (rb + 1) * BH > p.yb || p.x0 + (cb + 1) * CW > p.x1) break;
+      ++p.n_tm;
+    }
+  }
+  return p;
+}
+
+// Exchange g of tile t over the group's G2 slots, read by one whole warp:
+// the maximum key once every slot carries exchange g's mark.  *timed_out on
+// expiry (then the result is 0).
+__device__ __forceinline__ uint64_t pair_poll(const PlanDev& d, const MinorCfg& c, int t, int G2,
+                                              uint32_t g, bool* timed_out) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t* slot = d.gkeys + (int64_t)t * G2 + (int64_t)(g & 1u) * ((int64_t)d.T * G2);
+  const uint64_t mark = (uint64_t)((g >> 1) & 1u) << 63;
+  const uint64_t want = c.force_timeout ? (mark ^ (1ull << 63)) : mark;
+  constexpr int kPoll = 8;  // slots per lane, all loads in flight (G2 <= 256)
+  unsigned pend = 0u;
+#pragma unroll
+  for (int i = 0; i < kPoll; ++i)
+    if (lane + 32 * i < G2) pend |= 1u << i;
+  uint64_t kk = 0ull;
+  int abort = 0;
+  const uint64_t t0 = globaltimer_ns();
+  while (pend) {
+    uint64_t v[kPoll];
+#pragma unroll
+    for (int i = 0; i < kPoll; ++i)
+      v[i] = (pend >> i) & 1u ? ld_relaxed_u64(slot + lane + 32 * i) : 0ull;
+#pragma unroll
+    for (int i = 0; i < kPoll; ++i)
+      if (((pend >> i) & 1u) && (v[i] & (1ull << 63)) == want) {
+        kk = umax64(kk, v[i] & ~(1ull << 63));
+        pend &= ~(1u << i);
+      }
+    if (pend && globaltimer_ns() - t0 > (uint64_t)c.spin_limit_ns) {
+      abort = 1;
+      break;
+    }
+  }
+  abort = __any_sync(0xffffffffu, abort);
+  kk = warp_max_key(kk);
+  *timed_out = abort != 0;
+  return abort ? 0ull : kk;
+}
+
+template <bool TM>
+__device__ __forceinline__ void minor_pair_body(const PlanDev& d, const MinorCfg& c, int parity,
+                                                const CUtensorMap* r_map,
+                                                const CUtensorMap* p_map, int pair, int q) {
+  extern __shared__ __align__(128) float smem[];
+  float* sStage = smem;  // ring of stages (the residual is streamed)
+  constexpr int kW = kPipeConsumers / 32;
+  __shared__ __align__(8) uint64_t full_bar[kPipeMaxStages];
+  __shared__ __align__(8) uint64_t empty_bar[kPipeMaxStages];
+  __shared__ __align__(8) uint64_t key_bar;
+  __shared__ int s_arrived[2];  // consumer warps done with the pass, per key buffer
+  __shared__ uint64_t s_key[2];
+  __shared__ uint64_t s_warp[2][kW];
+  __shared__ int s_abort;    // an exchange or key wait expired: stop both tiles
+  __shared__ int s_dead;     // an mbarrier wait expired: stop working, keep exchanging
+  __shared__ uint32_t s_tmem;
+
+  const int G = c.G, G2 = 2 * G;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool producer = warp == kW;
+  const int S = c.stages, BH = c.chunk_h, CW = c.chunk_w, BW = c.box_w;
+  const int box_floats = (BW * BH + 31) & ~31;
+  const int stage_floats = 2 * box_floats;
+  const uint32_t stage_bytes = (uint32_t)(2 * BW * BH) * 4u;
+  const uint32_t p_box_bytes = (uint32_t)(BW * BH) * 4u;
+  const uint64_t limit = (uint64_t)c.spin_limit_ns;
+
+  if (*(volatile int32_t*)&d.st->status != 0) return;  // uniform, see minor_kernel
+
+  // per-tile state in named pairs (selected per step, no local arrays)
+  const Piece pc0 = pair_piece(d, 2 * pair, q % G, q / G, G, BH, CW, TM && c.tmem);
+  const Piece pc1 = pair_piece(d, 2 * pair + 1, q % G, q / G, G, BH, CW, TM && c.tmem);
+  const bool tm_on = TM && (pc0.n_tm > 0 || pc1.n_tm > 0);
+  if (tm_on && warp == 0) {
+    ptx::tmem_alloc(&s_tmem, kTmemCols);
+    ptx::tmem_relinquish();
+    ptx::tmem_fence_before_sync();
+  }
+
+  const uint64_t key00 = d.peak[parity * d.T + pc0.t], key01 = d.peak[parity * d.T + pc1.t];
+  const int64_t budget0 = d.budget[pc0.t], budget1 = d.budget[pc1.t];
+  const int64_t kmax0 = (d.K > 0 && (int64_t)d.K < budget0) ? (int64_t)d.K : budget0;
+  const int64_t kmax1 = (d.K > 0 && (int64_t)d.K < budget1) ? (int64_t)d.K : budget1;
+  const uint32_t seq00 = d.gbar[pc0.t], seq01 = d.gbar[pc1.t];
+  const float level = d.trigger > 0.f ? *(volatile float*)&d.st->level : 0.f;
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    s_dead = 0;
+    if (q == 0) {
+      d.peak[(parity ^ 1) * d.T + pc0.t] = 0ull;
+      d.peak[(parity ^ 1) * d.T + pc1.t] = 0ull;
+    }
+    for (int i = 0; i < S; ++i) {
+      ptx::mbar_init(&full_bar[i], 1);
+      ptx::mbar_init(&empty_bar[i], kW);
+    }
+    ptx::mbar_init(&key_bar, 1);
+    s_arrived[0] = 0;
+    s_arrived[1] = 0;
+    ptx::fence_barrier_init();
+  }
+  if (producer && lane == 0) {
+    ptx::prefetch_tensormap(r_map);
+    ptx::prefetch_tensormap(p_map);
+  }
+  __syncthreads();
+  if (tm_on) ptx::tmem_fence_after_sync();
+  const uint32_t tm_base =
+      tm_on ? s_tmem + (((uint32_t)(warp & 3) * 32u) << 16) + (uint32_t)(warp >> 2) * 128u : 0u;
+  bool filled0 = false, filled1 = false;
+
+  const int lpr_log2 = CW == 128 ? 5 : CW == 64 ? 4 : 3;
+  const int slabs = (BH + (32 >> lpr_log2) - 1) / (32 >> lpr_log2);
+  int tpr = 1;
+  while (tpr < CW && tpr < kPipeConsumers) tpr <<= 1;
+  const int rpp = kPipeConsumers / tpr;
+  const int crow = threadIdx.x / tpr, ccol = threadIdx.x % tpr;
+  const int rot_step = slabs % kW;
+
+  int p_st = 0, c_st = 0, rot = 0;
+  uint32_t p_ph = 0, c_ph = 0;
+  int64_t jnext = 0;
+  int64_t kx0 = 0, kx1 = 0;
+  bool done0 = false, done1 = false;
+  uint32_t n_pub = 0;   // keys published (producer) / taken (consumers)
+  uint32_t n_pass = 0;  // consumers: passes, for the partial-key buffer
+
+  for (int s = 0; !(done0 && done1); ++s) {
+    const int X = s & 1;
+    if (X ? done1 : done0) continue;
+    const Piece P = X ? pc1 : pc0;
+    const int64_t kX = X ? kx1 : kx0;
+    const uint32_t seqX = X ? seq01 : seq00;
+    if (producer) {
+      // the key of the tile's next iteration: the exchange of its previous
+      // iteration, posted by every CTA one step earlier
+      // one view of the abort flag for the whole warp (the poll is warp-wide)
+      const int ab = __shfl_sync(0xffffffffu, *(volatile int*)&s_abort, 0);
+      bool to = false;
+      uint64_t key = X ? key01 : key00;
+      if (kX > 0 && !ab) key = pair_poll(d, c, P.t, G2, seqX + (uint32_t)(kX - 1), &to);
+      bool active = !to && !ab && kX < (X ? kmax1 : kmax0) && key != 0ull;
+      if (active) {
+        const float v = key_value(key);
+        active = fabsf(v) > d.thr && fabsf(v) > level;  // threshold, flux trigger
+      }
+      if (lane == 0) {
+        if (to) {
+          atomicOr(&d.st->status, ST_TIMEOUT);
+          d.st->timeout_where = ((int64_t)P.t << 32) | (int64_t)kX;
+          s_abort = 1;
+        }
+        s_key[n_pub & 1u] = active ? key : 0ull;
+        ptx::mbar_arrive(&key_bar);
+      }
+      ++n_pub;
+      if (!active) {
+        if (X) done1 = true; else done0 = true;
+        continue;
+      }
+      const int idx = key_index(key);
+      const float f = __fmul_rn(d.gain, key_value(key));  // first equation
+      const int py = idx / d.nx, px = idx - py * d.nx;
+      const int dy = d.cy - py, dx = d.cx - px;
+      if (lane == 0) {
+        if (q == 0) {
+          clean_component cc;
+          cc.y = py;
+          cc.x = px;
+          cc.flux = f;
+          cc.tile = P.t;
+          d.rcomps[(int64_t)P.t * d.cap_round + kX] = cc;
+          d.model[idx] = __fadd_rn(d.model[idx], f);
+        }
+        int rb = 0, cb = 0;
+        for (int ch = 0; ch < P.nch && !*(volatile int*)&s_dead; ++ch) {
+          if (jnext >= S && !pipe_wait(&empty_bar[p_st], p_ph ^ 1u, limit, &s_dead,
+                                       &d.st->status))
+            break;
+          const int r0 = P.ya + rb * BH, c0 = P.x0 + cb * CW;
+          float* stg = sStage + (size_t)p_st * stage_floats;
+          // a tensor-memory chunk needs its residual box only in iteration 0
+          const bool r_box = !(TM && ch < P.n_tm && kX > 0);
+          ptx::mbar_arrive_expect_tx(&full_bar[p_st], r_box ? stage_bytes : p_box_bytes);
+          if (r_box) ptx::tma_load_2d(stg, r_map, c0 & ~3, r0, &full_bar[p_st]);
+          ptx::tma_load_2d(stg + box_floats, p_map, (c0 + dx) & ~3, r0 + dy, &full_bar[p_st]);
+          ++jnext;
+          if (++p_st == S) {
+            p_st = 0;
+            p_ph ^= 1u;
+          }
+          if (++cb == P.ncb) {
+            cb = 0;
+            ++rb;
+          }
+        }
+      }
+      __syncwarp();
+      if (X) ++kx1; else ++kx0;
+      continue;
+    }
+
+    // ---- consumers ----
+    // the producer publishes within its own bounded waits (at most two
+    // limits), so this wait gets four
+    bool got = pipe_wait(&key_bar, n_pub & 1u, 4 * limit, &s_dead, &d.st->status);
+    got = __all_sync(0xffffffffu, got);
+    const uint64_t key = got ? s_key[n_pub & 1u] : 0ull;
+    ++n_pub;
+    if (!got) s_abort = 1;
+    if (key == 0ull) {
+      if (X || !got) done1 = true;
+      if (!X || !got) done0 = true;
+      continue;
+    }
+    const int idx = key_index(key);
+    const float f = __fmul_rn(d.gain, key_value(key));
+    const int py = idx / d.nx, px = idx - py * d.nx;
+    const int dy = d.cy - py, dx = d.cx - px;
+    const bool fast = P.vec && P.ya + dy >= 0 && P.yb - 1 + dy < d.pny && P.x0 + dx >= 0 &&
+                      P.x1 - 1 + dx < d.pnx;
+    float best_a = -1.f, best_v = 0.f;
+    int best_i = 0x7fffffff, best_base = 0x7fffffff;
+    float4 best_r = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (tm_on && kX > 0) {
+      __syncwarp();
+      ptx::tmem_wait_st();
+    }
+    int rb = 0, cb = 0;
+    for (int ch = 0; ch < P.nch; ++ch) {
+      const int st = c_st;
+      bool ok = !*(volatile int*)&s_dead &&
+                pipe_wait(&full_bar[st], c_ph, limit, &s_dead, &d.st->status);
+      if (TM) ok = __all_sync(0xffffffffu, ok);
+      if (!ok) break;
+      if (++c_st == S) {
+        c_st = 0;
+        c_ph ^= 1u;
+      }
+      const int r0 = P.ya + rb * BH, r1 = min(P.yb, r0 + BH);
+      const int c0 = P.x0 + cb * CW, c1 = min(P.x1, c0 + CW);
+      if (++cb == P.ncb) {
+        cb = 0;
+        ++rb;
+      }
+      const float* stgR = sStage + (size_t)st * stage_floats;
+      const float* stgP = stgR + box_floats;
+      const int offR = c0 - (c0 & ~3), offP = (c0 + dx) - ((c0 + dx) & ~3);
+      if (TM && fast && ch < P.n_tm) {
+        const uint32_t ta = tm_base + (uint32_t)(X * 64 + ch * 16);
+        const bool from_box = kX == 0;
+        switch (offP) {
+          case 0:
+            tmem_chunk<0>(d, ta, from_box, stgR, stgP, BW, r0, c0, f, best_a, best_base, best_r);
+            break;
+          case 1:
+            tmem_chunk<1>(d, ta, from_box, stgR, stgP, BW, r0, c0, f, best_a, best_base, best_r);
+            break;
+          case 2:
+            tmem_chunk<2>(d, ta, from_box, stgR, stgP, BW, r0, c0, f, best_a, best_base, best_r);
+            break;
+          default:
+            tmem_chunk<3>(d, ta, from_box, stgR, stgP, BW, r0, c0, f, best_a, best_base, best_r);
+            break;
+        }
+      } else if (fast) {
+        const int s_first = warp >= rot ? warp - rot : warp + kW - rot;
+        switch (offP) {
+          case 0:
+            chunk_slabs<false, 0>(d, nullptr, 0, 0, stgR, stgP, BW, r0, r1, c0, c1, 0, f,
+                                  lpr_log2, s_first, best_a, best_base, best_r);
+            break;
+          case 1:
+            chunk_slabs<false, 1>(d, nullptr, 0, 0, stgR, stgP, BW, r0, r1, c0, c1, 0, f,
+                                  lpr_log2, s_first, best_a, best_base, best_r);
+            break;
+          case 2:
+            chunk_slabs<false, 2>(d, nullptr, 0, 0, stgR, stgP, BW, r0, r1, c0, c1, 0, f,
+                                  lpr_log2, s_first, best_a, best_base, best_r);
+            break;
+          default:
+            chunk_slabs<false, 3>(d, nullptr, 0, 0, stgR, stgP, BW, r0, r1, c0, c1, 0, f,
+                                  lpr_log2, s_first, best_a, best_base, best_r);
+            break;
+        }
+      } else {
+        for (int y = r0 + crow; crow < rpp && y < r1; y += rpp) {
+          const bool yin = (unsigned)(y + dy) < (unsigned)d.pny;
+          const float* rowP = stgP + (y - r0) * BW + offP - c0;  // index by x
+          const float* rowR = stgR + (y - r0) * BW + offR - c0;
+          for (int x = c0 + ccol; x < c1; x += tpr) {
+            float r = rowR[x];
+            if (yin && (unsigned)(x + dx) < (unsigned)d.pnx) r = __fsub_rn(r, __fmul_rn(f, rowP[x]));
+            d.R[(int64_t)y * d.nx + x] = r;
+            take_peak(r, y * d.nx + x, best_a, best_i, best_v);
+          }
+        }
+      }
+      rot += rot_step;
+      if (rot >= kW) rot -= kW;
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive(&empty_bar[st]);
+    }
+    if (fast && best_a >= 0.f) resolve_group(best_a, best_base, best_r, best_i, best_v);
+    const bool fill = tm_on && !*(volatile int*)&s_dead;
+    if (X) filled1 = fill; else filled0 = fill;
+    // residual rows written through the generic proxy are read back by TMA
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    // the CTA's partial key: each consumer warp leaves its maximum and counts
+    // itself in; the last warp to arrive reduces, posts and resets the count,
+    // so no warp waits for another.  Buffers alternate: a warp refills this
+    // one two passes later, after taking a key that needed this pass's post.
+    uint64_t mine = (best_a >= 0.f) ? make_key(best_v, best_i) : 0ull;
+    mine = warp_max_key(mine);
+    const uint32_t buf = n_pass & 1u;
+    if (lane == 0) {
+      s_warp[buf][warp] = mine;
+      __threadfence_block();
+      if (atomicAdd(&s_arrived[buf], 1) == kW - 1) {
+        __threadfence_block();
+        uint64_t m = 0ull;
+        for (int w = 0; w < kW; ++w) m = umax64(m, *(volatile uint64_t*)&s_warp[buf][w]);
+        const uint32_t g = seqX + (uint32_t)kX;
+        uint64_t* slot = d.gkeys + (int64_t)P.t * G2 + (int64_t)(g & 1u) * ((int64_t)d.T * G2);
+        st_relaxed_u64(slot + q, m | ((uint64_t)((g >> 1) & 1u) << 63));
+        s_arrived[buf] = 0;
+      }
+    }
+    __syncwarp();
+    ++n_pass;
+    if (X) ++kx1; else ++kx0;
+  }
+
+  if (tm_on) {
+    // tensor-memory chunks back to global memory, then free the columns
+    if (!producer) {
+      __syncwarp();
+      ptx::tmem_wait_st();
+#pragma unroll
+      for (int X = 0; X < 2; ++X) {
+        const Piece P = X ? pc1 : pc0;
+        const bool wb = __shfl_sync(0xffffffffu,
+                                    (int)((X ? filled1 : filled0) && !*(volatile int*)&s_dead),
+                                    0) != 0;
+        if (!wb) continue;
+        for (int ch = 0; ch < P.n_tm; ++ch) {
+          const int rb = ch / P.ncb, cb = ch - rb * P.ncb;
+          const int r0 = P.ya + rb * BH, c0 = P.x0 + cb * CW;
+          float4 v[kSlabUnroll];
+          __syncwarp();
+          ptx::tmem_ld16(tm_base + (uint32_t)(X * 64 + ch * 16), v);
+#pragma unroll
+          for (int u = 0; u < kSlabUnroll; ++u)
+            *reinterpret_cast<float4*>(d.R + (int64_t)(r0 + warp + u * kW) * d.nx + c0 +
+                                       4 * lane) = v[u];
+        }
+      }
+    }
+    ptx::tmem_fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+      ptx::tmem_fence_after_sync();
+      __syncwarp();
+      ptx::tmem_dealloc(s_tmem, kTmemCols);
+    }
+  }
+  if (producer && lane == 0 && s_dead) {
+    // after an expired wait: let this CTA's own copies in flight land
+    for (int64_t j = max((int64_t)0, jnext - S); j < jnext; ++j) {
+      const uint64_t t0 = ptx::globaltimer_ns();
+      while (!ptx::mbar_try_wait(&full_bar[j % S], (uint32_t)(j / S) & 1u))
+        if (ptx::globaltimer_ns() - t0 > limit) break;
+    }
+  }
+  if (q == 0 && threadIdx.x == 0) {
+    d.rcount[pc0.t] = (int32_t)kx0;
+    d.budget[pc0.t] = budget0 - kx0;
+    d.gbar[pc0.t] = seq00 + (uint32_t)kx0;
+    d.rcount[pc1.t] = (int32_t)kx1;
+    d.budget[pc1.t] = budget1 - kx1;
+    d.gbar[pc1.t] = seq01 + (uint32_t)kx1;
+  }
+}
+
+template <bool TM>
+__global__ void __launch_bounds__(kPipeThreads, 1)
+    minor_pair_kernel(PlanDev d, MinorCfg c, int parity,
+                      const __grid_constant__ CUtensorMap r_map,
+                      const __grid_constant__ CUtensorMap p_map) {
+  const int G2 = 2 * c.G;
+  minor_pair_body<TM>(d, c, parity, &r_map, &p_map, (int)blockIdx.x / G2,
+                      (int)blockIdx.x % G2);
+}
+
 // Batched pipeline launch: one CTA (kSyncNone) or one cluster of G CTAs per
 // (image, tile) item, each image's plan state in `plans` and its residual and
 // PSF box maps in rmaps / pmaps (global memory, indexed like `plans`).
@@ -933,6 +1390,8 @@ void* kernel_ptr(bool pipe, bool tmem) {
 
 void* pick(const MinorCfg& c) {
   const bool p = c.pipe != 0, tm = c.tmem != 0;
+  if (p && c.pair && !c.resident && c.sync == CLEAN_SYNC_GRID)
+    return tm ? (void*)minor_pair_kernel<true> : (void*)minor_pair_kernel<false>;
   if (c.sync == CLEAN_SYNC_CLUSTER)
     return c.resident ? kernel_ptr<CLEAN_SYNC_CLUSTER, true>(p, tm)
                       : kernel_ptr<CLEAN_SYNC_CLUSTER, false>(p, tm);

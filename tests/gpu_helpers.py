@@ -8,7 +8,7 @@ import paper_2501_01461_gb300 as cg
 
 def gpu_clean(dirty, psf, gain, niter, threshold=0.0, tiles=(1, 1), K=0, max_rounds=-1,
               mode=cg.TILED, group_ctas=0, group_sync=cg.SYNC_AUTO, feedback_path=0, minor_path=0,
-              feedback_mode=cg.FB_GATHER, trigger=0.0, minor_tmem=None):
+              feedback_mode=cg.FB_GATHER, trigger=0.0, minor_tmem=None, minor_pair=None):
     import torch
     d_psf = torch.from_numpy(np.ascontiguousarray(psf, np.float32)).cuda()
     d_dirty = torch.from_numpy(np.ascontiguousarray(dirty, np.float32)).cuda()
@@ -23,6 +23,8 @@ def gpu_clean(dirty, psf, gain, niter, threshold=0.0, tiles=(1, 1), K=0, max_rou
             plan.debug_set(cg.DEBUG_MINOR_PATH, minor_path)
         if minor_tmem is not None:
             plan.debug_set(cg.DEBUG_MINOR_TMEM, int(minor_tmem))
+        if minor_pair is not None:
+            plan.debug_set(cg.DEBUG_MINOR_PAIR, int(minor_pair))
         plan.run(d_dirty, max_rounds=max_rounds)
         res, mod, _ = plan.get()
         comps = plan.components_with_rounds()

@@ -177,6 +177,45 @@ def test_minor_tmem_bit_exact(case):
         assert o.n < niter  # the threshold, not the budget, ended the run
 
 
+PAIR_CASES = [
+    # (ny, nx, psf, tiles, K, niter, G, threshold, pairs): tile pairs served
+    # by groups of 2G CTAs (streamed rows, grid groups, an even tile count)
+    (512, 512, (1024, 1024), (1, 2), 0, 400, 2, 0.0, 1),      # one pair, TMEM chunks
+    (1024, 1024, (2048, 2048), (2, 2), 20, 600, 2, 0.0, 1),   # two pairs, feedback
+    (520, 1000, (1040, 2000), (1, 2), 13, 401, 3, 0.0, 1),    # ragged halves, odd budget
+    (512, 512, (600, 700), (2, 2), 10, 600, 1, 0.0, 1),       # clipped windows: scalar path
+    (512, 512, (1024, 1024), (1, 2), 1, 120, 2, 0.0, 1),      # one iteration a launch
+    (512, 512, (1024, 1024), (2, 2), 0, 4000, 1, 0.05, 1),    # tiles stop at different times
+    (768, 512, (1536, 1024), (3, 1), 10, 300, 2, 0.0, 0),     # odd tile count: one group a tile
+]
+
+
+@pytest.mark.parametrize("case", PAIR_CASES, ids=[f"{c[0]}x{c[1]}-psf{c[2][0]}x{c[2][1]}-t{c[3][0]}x{c[3][1]}-K{c[4]}-G{c[6]}"
+                                                  for c in PAIR_CASES])
+def test_minor_tile_pairs_bit_exact(case):
+    """Groups of 2G CTAs alternating between two tiles give the oracle's
+    bits, as does one group per tile."""
+    ny, nx, ps, tiles, K, niter, G, thr, pairs = case
+    rng = np.random.default_rng(ny * 3 + nx + G + K)
+    if ps[0] >= 2 * ny and ps[1] >= 2 * nx:
+        psf = synth.make_psf(*ps)
+        ys, xs, fl = synth.make_sky(min(ny, nx), 12, 0.05, 2.1, rng)
+        d = synth.make_dirty(psf, min(ny, nx), ys, xs, fl, 1e-3, rng)
+        dirty = synth.random_image(ny, nx, rng, 1e-3)
+        dirty[:d.shape[0], :d.shape[1]] += d
+    else:
+        psf = synth.random_psf(*ps, rng)
+        dirty = synth.random_image(ny, nx, rng)
+    o = oracle.clean_f32(dirty, psf, 0.1, niter, thr, tiles, K)
+    for pr in (1, 0):
+        g = gpu_clean(dirty, psf, 0.1, niter, thr, tiles, K, group_ctas=G,
+                      group_sync=cg.SYNC_GRID, minor_path=2, minor_pair=pr)
+        st = g["stats"]
+        assert st["minor_pipe"] == 1 and st["resident"] == 0
+        assert st["minor_pairs"] == (pairs if pr else 0), st
+        assert_bit_exact(g, o, f"{case} pairs={pr}")
+
+
 def test_untiled_grid_256():
     """Plain Hogbom CLEAN on the whole GPU: 256^2 image, 512^2 PSF, 20
     sources, gain 0.1, 2000 iterations, threshold 5 mJy."""
