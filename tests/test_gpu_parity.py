@@ -502,6 +502,36 @@ def test_checkpoint_resume_equals_uninterrupted_run(mode):
     assert np.array_equal(got[2]["flux"].view(np.uint32), want[2]["flux"].view(np.uint32))
 
 
+def test_checkpoint_resume_with_tile_pairs():
+    """Checkpoint and resume under tile pairs (streamed rows, grid groups of
+    2G CTAs, TMEM chunks): the resumed run restarts the exchange count and
+    ends exactly as the uninterrupted run and the oracle."""
+    import torch
+    rng = np.random.default_rng(123)
+    n = 1024
+    psf = synth.make_psf(2 * n, 2 * n)
+    ys, xs, fl = synth.make_sky(n, 30, 0.05, 2.1, rng)
+    dirty = synth.make_dirty(psf, n, ys, xs, fl, 1e-3, rng)
+    d_psf, d_dirty = torch.from_numpy(psf).cuda(), torch.from_numpy(dirty).cuda()
+    kw = dict(gain=0.1, niter=900, tiles=(2, 2), feedback_interval=25, group_ctas=2,
+              group_sync=cg.SYNC_GRID)
+    o = oracle.clean_f32(dirty, psf, 0.1, 900, 0.0, (2, 2), 25)
+    with cg.Plan(d_psf, n, n, **kw) as p:
+        p.debug_set(cg.DEBUG_MINOR_PATH, 2)
+        p.run(d_dirty, max_rounds=3)
+        assert p.stats()["minor_pairs"] == 1 and p.stats()["minor_tmem"] == 1
+        blob = p.checkpoint()
+    with cg.Plan(d_psf, n, n, **kw) as q:
+        q.debug_set(cg.DEBUG_MINOR_PATH, 2)
+        q.resume(blob)
+        q.run(None)
+        r, m, _ = q.get()
+        comps = q.components_with_rounds()
+        g = dict(residual=r.cpu().numpy(), model=m.cpu().numpy(), comps=comps,
+                 n=len(comps["y"]))
+    assert_bit_exact(g, o, "resumed under tile pairs")
+
+
 DEGENERATE = [
     # (ny, nx, psf, tiles, K, niter, threshold): one-pixel images and tiles,
     # strips, a one-pixel PSF, budgets smaller than the tile count, a single
