@@ -218,7 +218,7 @@ cudaError_t launch_feedback_batch(const PlanDev* plans, const BatchImage* imgs, 
 // Feedback block grid of one image (blocks per tile in x and y).
 void feedback_blocks(const PlanDev& d, bool tma, int* bx, int* by);
 int minor_max_cluster_ctas(int G, int resident, int smem, int threads);
-// psf_map: a 2-D tensor map of the PSF (box 68 x 64 floats) selects the TMA
+// psf_map: a 2-D tensor map of the PSF (box 132 x 32 floats) selects the TMA
 // kernel; NULL selects the plain-load kernel.
 cudaError_t launch_feedback(const PlanDev& d, const CUtensorMap* psf_map, int parity,
                             int apply, uint64_t limit_ns, cudaStream_t s);
