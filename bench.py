@@ -401,8 +401,9 @@ def run_reference(args):
 
 def run_sweep(args):
     """The measurement plan's configurations besides the headline: the 256^2
-    untiled workload and the 1024^2 tiled one run in full on the GPU and on
-    the CPU oracle (one thread, and the oracle's arithmetic on all host
+    untiled workload (whole-GPU grid mode, and the library's automatic group
+    choice, a 16-CTA cluster) and the 1024^2 tiled one run in full on the GPU
+    and on the CPU oracle (one thread, and the oracle's arithmetic on all host
     cores), and the 4096^2 workload at feedback intervals 10, 20, 50, 100 and
     200 with exact (gather) and FFT feedback.  GPU figures are the median of
     three CUDA-event-timed runs after one warm-up, with a 512 MiB write
@@ -460,6 +461,7 @@ def run_sweep(args):
     out["untiled-256"] = {
         "config": cfgd(w0, w0.threshold),
         "gpu_untiled_grid": gpu(w0, d0, w0.threshold, 0, mode=cg.UNTILED_GRID),
+        "gpu_automatic_group": gpu(w0, d0, w0.threshold, 0),
         "cpu_oracle_1_thread": cpu(w0, d0, w0.threshold, 0, False),
         "cpu_oracle_all_cores": cpu(w0, d0, w0.threshold, 0, True)}
     w1 = synth.workload("tiled-1024")
