@@ -633,13 +633,17 @@ def main():
             dist.barrier()
         t0 = time.perf_counter()
         ne = 0
+        e2e_steps = []
         for _ in range(args.steps):
+            ts = time.perf_counter()
             ne += host_step()
+            e2e_steps.append((time.perf_counter() - ts) * 1e3)
         te_ms, ne = aggregate(dist, (time.perf_counter() - t0) * 1e3, ne, "cuda")
         hp.close()
         e2e = {"value": ne / (te_ms / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": int(dirty.nbytes + psf.nbytes),
-               "d2h_bytes_per_step": int(2 * dirty.nbytes + 16 * w.niter)}
+               "d2h_bytes_per_step": int(2 * dirty.nbytes + 16 * w.niter),
+               "step_ms": [round(x, 2) for x in e2e_steps]}
 
     # ---- untiled whole-GPU Hogbom on the same image (rate on a prefix) ----
     untiled = None
