@@ -99,3 +99,32 @@ def test_bad_calls():
     with pytest.raises(cg.CleanError) as e:
         cg.Plan(psf, 64, 64, niter=10, feedback_mode=9)
     assert e.value.status == 1
+
+
+def test_forced_grid_timeout_with_tile_pairs():
+    """Tile pairs: an exchange poll that expires (a mark no CTA writes) sets
+    CLEAN_ERR_TIMEOUT, stops both tiles of every pair and returns within
+    bounded time; the plan stays poisoned and a new plan runs normally."""
+    import time
+    import torch
+    n = 512
+    psf = torch.from_numpy(synth.make_psf(2 * n, 2 * n)).cuda()
+    d = torch.from_numpy(synth.random_image(n, n, 3)).cuda()
+    kw = dict(niter=400, tiles=(1, 2), feedback_interval=10, group_ctas=2,
+              group_sync=cg.SYNC_GRID)
+    p = cg.Plan(psf, n, n, **kw)
+    p.debug_set(cg.DEBUG_MINOR_PATH, 2)
+    assert p.stats()["minor_pairs"] == 1
+    p.debug_set(cg.DEBUG_SPIN_LIMIT_NS, 20_000_000)
+    p.debug_set(cg.DEBUG_FORCE_TIMEOUT, 1)
+    t0 = time.time()
+    with pytest.raises(cg.CleanError) as e:
+        p.run(d)
+    assert e.value.status == 5
+    assert time.time() - t0 < 30
+    p.close()
+    q = cg.Plan(psf, n, n, **kw)
+    q.debug_set(cg.DEBUG_MINOR_PATH, 2)
+    q.run(d)
+    assert q.n_components() == 400 and q.stats()["minor_pairs"] == 1
+    q.close()
