@@ -4,8 +4,9 @@ Two kinds of choices are tuned:
 
 * Launch choices that never change a result bit: CTAs per tile and the
   group barrier of the minor loop (thread-block cluster or bounded grid
-  barrier), the minor-loop kernel (plain loads or bulk-copy pipeline) and
-  the feedback kernel (plain loads, TMA windows, pipelined loads).  Every
+  barrier), the minor-loop kernel (plain loads or bulk-copy pipeline, with
+  or without tile pairs and tensor-memory chunks) and the feedback kernel
+  (plain loads, TMA windows, pipelined loads).  Every
   candidate is timed on the problem itself for a few rounds; the fastest
   wins.
 * Choices that change results, only on request: the FFT feedback (within
@@ -25,8 +26,9 @@ import os
 import time
 from dataclasses import asdict, dataclass, field
 
-from . import (DEBUG_FEEDBACK_PATH, DEBUG_MINOR_PATH, DEBUG_TIMING, FB_FFT, FB_GATHER,
-               SYNC_AUTO, SYNC_CLUSTER, SYNC_GRID, CleanError, Plan)
+from . import (DEBUG_FEEDBACK_PATH, DEBUG_MINOR_PAIR, DEBUG_MINOR_PATH, DEBUG_MINOR_TMEM,
+               DEBUG_TIMING, FB_FFT, FB_GATHER, SYNC_AUTO, SYNC_CLUSTER, SYNC_GRID, CleanError,
+               Plan)
 
 PAPER_BAND = (-0.1, 0.04)   # restored(tiled) - restored(untiled), Jy
 
@@ -39,6 +41,8 @@ class Choice:
     minor_path: int = 0        # 0 automatic, 1 plain loads, 2 bulk-copy pipeline
     feedback_path: int = 0     # 0 automatic, 1 plain loads, 2 TMA, 3 pipelined loads
     feedback_mode: int = FB_GATHER
+    minor_pairs: int = 1       # 1 tile pairs where they apply, 0 one group per tile
+    minor_tmem: int = 1        # 1 tensor-memory chunks where they apply, 0 none
 
     def plan_kwargs(self) -> dict:
         return dict(group_ctas=self.group_ctas, group_sync=self.group_sync,
@@ -49,6 +53,10 @@ class Choice:
             plan.debug_set(DEBUG_MINOR_PATH, self.minor_path)
         if self.feedback_path:
             plan.debug_set(DEBUG_FEEDBACK_PATH, self.feedback_path)
+        if not self.minor_pairs:
+            plan.debug_set(DEBUG_MINOR_PAIR, 0)
+        if not self.minor_tmem:
+            plan.debug_set(DEBUG_MINOR_TMEM, 0)
 
 
 @dataclass
@@ -113,6 +121,9 @@ def candidates(tiles, sm_count: int, allow_fft: bool = False) -> list[Choice]:
             out.append(Choice(group_ctas=G, group_sync=SYNC_CLUSTER))
     for fp in (1, 3):
         out.append(Choice(feedback_path=fp))
+    # the automatic minor loop without tile pairs, and without TMEM chunks
+    out.append(Choice(minor_pairs=0))
+    out.append(Choice(minor_tmem=0))
     if allow_fft and T > 1:
         out.append(Choice(feedback_mode=FB_FFT))
     # keep order, drop duplicates

@@ -18,6 +18,7 @@ def test_candidates_cover_paths_and_barriers():
     assert any(k[0] == cg.SYNC_GRID for k in kinds)
     assert any(k[0] == cg.SYNC_CLUSTER for k in kinds)
     assert {1, 3} <= {x.feedback_path for x in c}
+    assert any(not x.minor_pairs for x in c) and any(not x.minor_tmem for x in c)
     assert all(x.feedback_mode == cg.FB_GATHER for x in c)   # exact unless FFT allowed
     assert any(x.feedback_mode == cg.FB_FFT for x in tune.candidates((4, 4), 152, allow_fft=True))
     assert len(c) == len({tuple(vars(x).items()) for x in c})
