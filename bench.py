@@ -631,6 +631,8 @@ def main():
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
+        e2e_sampler = ClockSampler(local)
+        e2e_sampler.start()
         t0 = time.perf_counter()
         ne = 0
         e2e_steps = []
@@ -639,11 +641,12 @@ def main():
             ne += host_step()
             e2e_steps.append((time.perf_counter() - ts) * 1e3)
         te_ms, ne = aggregate(dist, (time.perf_counter() - t0) * 1e3, ne, "cuda")
+        e2e_clocks = e2e_sampler.stop()
         hp.close()
         e2e = {"value": ne / (te_ms / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": int(dirty.nbytes + psf.nbytes),
                "d2h_bytes_per_step": int(2 * dirty.nbytes + 16 * w.niter),
-               "step_ms": [round(x, 2) for x in e2e_steps]}
+               "step_ms": [round(x, 2) for x in e2e_steps], "clocks": e2e_clocks}
 
     # ---- untiled whole-GPU Hogbom on the same image (rate on a prefix) ----
     untiled = None

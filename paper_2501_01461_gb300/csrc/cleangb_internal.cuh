@@ -225,6 +225,7 @@ cudaError_t launch_feedback(const PlanDev& d, const CUtensorMap* psf_map, int pa
 // Feedback with the PSF read through pipelined global loads (no TMA).
 cudaError_t launch_feedback_ldg(const PlanDev& d, int parity, int apply, cudaStream_t s);
 cudaError_t feedback_prepare(int T);
+cudaError_t fft_prepare();  // kernel attributes of the FFT feedback (fft_feedback.cu)
 // FFT feedback pieces (see feedback.cu).  Grids are Ly x Lx floats (pitch Lx).
 cudaError_t fft_build_kernel_image(const PlanDev& d, int Ly, int Lx, float* Kimg,
                                    cudaStream_t s);

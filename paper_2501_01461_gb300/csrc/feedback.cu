@@ -25,6 +25,7 @@
 
 #include "cleangb_internal.cuh"
 #include "ptx.cuh"
+#include "round_close.cuh"
 
 namespace cleangb {
 
@@ -43,124 +44,6 @@ struct __align__(16) Comp4 {
   float f;
   int32_t pad;
 };
-
-__device__ __forceinline__ uint64_t umax64(uint64_t a, uint64_t b) {
-  return a > b ? a : b;
-}
-
-__device__ __forceinline__ uint64_t warp_max_key(uint64_t k) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) k = umax64(k, __shfl_xor_sync(0xffffffffu, k, o));
-  return k;
-}
-
-// Exclusive prefix of cnt[0..T) into pre[0..T]; whole block participates.
-__device__ void block_prefix(const int32_t* cnt, int32_t* pre, int T) {
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-    int carry = 0;
-    for (int b = 0; b < T; b += 32) {
-      int v = (b + lane < T) ? cnt[b + lane] : 0;
-      int incl = v;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        int n = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += n;
-      }
-      if (b + lane < T) pre[b + lane] = carry + incl - v;
-      carry += __shfl_sync(0xffffffffu, incl, 31);
-    }
-    if (lane == 0) pre[T] = carry;
-  }
-  __syncthreads();
-}
-
-// Largest s with pre[s] <= g (pre non-decreasing, pre[0] = 0 <= g < pre[T]).
-__device__ __forceinline__ int find_tile(const int32_t* pre, int T, int g) {
-  int lo = 0, hi = T - 1;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (pre[mid] <= g)
-      lo = mid;
-    else
-      hi = mid - 1;
-  }
-  return lo;
-}
-
-
-// The last CTA of the feedback launch closes the round: appends the round's
-// components to the list (tile order, then iteration), records the round's
-// list offset, and decides whether any tile can run again.  Every thread of
-// every CTA calls this once, after its pixels are final.
-__device__ void close_round_if_last(const PlanDev& d, int parity, int total_blocks,
-                                    int32_t* s_cnt, int32_t* s_pre, float* clear_grid = nullptr,
-                                    int64_t clear_pitch = 0) {
-  __shared__ int s_last;
-  __shared__ int64_t s_mb[32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nthr = blockDim.x, nwarps = (blockDim.x + 31) >> 5;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned done = atomicAdd(&d.st->fb_done, 1u);
-    s_last = (done == (unsigned)total_blocks - 1u);
-  }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-
-  for (int s = threadIdx.x; s < d.T; s += nthr) s_cnt[s] = ((volatile int32_t*)d.rcount)[s];
-  block_prefix(s_cnt, s_pre, d.T);
-  const int n_all = s_pre[d.T];
-  const int64_t total0 = d.st->total;
-  for (int g = threadIdx.x; g < n_all; g += nthr) {
-    const int s = find_tile(s_pre, d.T, g);
-    const clean_component cc = d.rcomps[(int64_t)s * d.cap_round + (g - s_pre[s])];
-    d.list[total0 + g] = cc;
-    if (clear_grid) clear_grid[(int64_t)cc.y * clear_pitch + cc.x] = 0.f;
-  }
-  // any tile that can run next round; largest remaining budget; the largest
-  // |peak| among those tiles (the flux trigger's reference)
-  int act = 0;
-  int64_t mb = 0;
-  uint32_t top = 0u;  // |peak| bits: non-negative floats order like integers
-  for (int s = threadIdx.x; s < d.T; s += nthr) {
-    const int64_t b = ((volatile int64_t*)d.budget)[s];
-    const uint64_t pk = ((volatile unsigned long long*)d.peak)[(parity ^ 1) * d.T + s];
-    if (b > 0 && pk != 0ull && key_abs(pk) > d.thr) {
-      act = 1;
-      top = max(top, (uint32_t)(pk >> 32));
-    }
-    mb = b > mb ? b : mb;
-  }
-  act = __syncthreads_or(act);
-  __shared__ uint32_t s_top;
-  if (threadIdx.x == 0) s_top = 0u;
-  __syncthreads();
-  if (top) atomicMax(&s_top, top);
-  for (int o = 16; o > 0; o >>= 1) {
-    const int64_t other = __shfl_xor_sync(0xffffffffu, mb, o);
-    mb = other > mb ? other : mb;
-  }
-  if (lane == 0) s_mb[warp] = mb;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int64_t m = 0;
-    for (int w = 0; w < nwarps; ++w) m = s_mb[w] > m ? s_mb[w] : m;
-    if (n_all > 0) {
-      d.round_off[d.st->n_rounds] = total0;
-      d.st->n_rounds += 1;
-    }
-    d.st->total = total0 + n_all;
-    d.st->round_comps = n_all;
-    d.st->active = act;
-    d.st->max_budget = m;
-    d.st->level = d.trigger > 0.f ? __fmul_rn(d.trigger, __uint_as_float(s_top)) : 0.f;
-    d.st->fb_done = 0u;
-  }
-}
 
 // Sum of the round's component counts over all tiles (0: the round changed
 // nothing, so the image's residual and peaks need no new pass).
@@ -719,126 +602,6 @@ __global__ void __launch_bounds__(tma::kThreads, tma::kMinBlocks)
 }
 
 
-// ---------------------------------------------------------------------------
-// FFT feedback (tolerance-exact alternative to the gather).  The round's
-// components, scattered onto an L x L grid (L >= 2N - 1 in each axis),
-// convolved circularly with the PSF kernel K[d mod L] = P[d + c] give, at
-// every image pixel q, S[q] = sum_c f_c P[q - p_c + c] with no wrap-around.
-// The residual after the round is then the residual at the round's start
-// minus S on every pixel of every tile (the minor loops' own-tile
-// subtractions included), so no per-tile correction is needed.
-// ---------------------------------------------------------------------------
-constexpr int kFftThreads = 256;
-constexpr int kFftRows = 16;
-
-// K[(dy mod Ly), (dx mod Lx)] = P[dy + cy, dx + cx] for |dy| < ny, |dx| < nx
-// inside the PSF; zero elsewhere.  One thread per grid element.
-__global__ void fft_kernel_image(const float* __restrict__ P, int pny, int pnx, int cy, int cx,
-                                 int ny, int nx, int Ly, int Lx, float* __restrict__ Kimg) {
-  const int64_t n = (int64_t)Ly * Lx;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int my = (int)(i / Lx), mx = (int)(i - (int64_t)my * Lx);
-    const int dy = my < ny ? my : my - Ly;   // represent m as d in (-(L - ny), ny)
-    const int dx = mx < nx ? mx : mx - Lx;
-    float v = 0.f;
-    if (dy > -ny && dx > -nx) {
-      const int sy = dy + cy, sx = dx + cx;
-      if ((unsigned)sy < (unsigned)pny && (unsigned)sx < (unsigned)pnx)
-        v = P[(int64_t)sy * pnx + sx];
-    }
-    Kimg[i] = v;
-  }
-}
-
-// The round's components onto the (zeroed) grid: one warp per tile (a
-// tile's components lie inside it, so tiles never share a cell).  Lane l
-// takes components l, l + 32, ...; the first component at a cell sums every
-// component of the tile at that cell in iteration order and writes the cell
-// once, so each cell gets ((0 + f1) + f2) + ... exactly as one thread adding
-// them in order would.  Above kScatterQuadMax components the quadratic
-// search gives way to one thread in order.
-constexpr int kScatterQuadMax = 4096;
-__global__ void fft_scatter(PlanDev d, float* __restrict__ A, int64_t pitch) {
-  const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (t >= d.T) return;
-  const int n = d.rcount[t];
-  const clean_component* c = d.rcomps + (int64_t)t * d.cap_round;
-  if (n > kScatterQuadMax) {
-    if (lane == 0)
-      for (int k = 0; k < n; ++k) {
-        float* a = &A[(int64_t)c[k].y * pitch + c[k].x];
-        *a = *a + c[k].flux;
-      }
-    return;
-  }
-  for (int k = lane; k < n; k += 32) {
-    const clean_component ck = c[k];
-    bool first = true;
-    for (int j = 0; j < k && first; ++j) first = !(c[j].y == ck.y && c[j].x == ck.x);
-    if (!first) continue;
-    float* a = &A[(int64_t)ck.y * pitch + ck.x];
-    float acc = *a + ck.flux;
-    for (int j = k + 1; j < n; ++j)
-      if (c[j].y == ck.y && c[j].x == ck.x) acc = acc + c[j].flux;
-    *a = acc;
-  }
-}
-
-// X <- X * K / (Ly Lx), complex, element by element.
-__global__ void fft_multiply(float2* __restrict__ X, const float2* __restrict__ Kh, int64_t n,
-                             float scale) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const float2 a = X[i], b = Kh[i];
-    X[i] = make_float2((a.x * b.x - a.y * b.y) * scale, (a.x * b.y + a.y * b.x) * scale);
-  }
-}
-
-// R <- R0 - S on tile t's rows [ya, ya + kFftRows); R0 <- R; the block's
-// peak into the tile's next-round key; the last block closes the round and
-// clears the scattered grid cells.
-__global__ void __launch_bounds__(kFftThreads)
-    fft_subtract(PlanDev d, float* __restrict__ R0, const float* __restrict__ S, int64_t pitch,
-                 float* __restrict__ A, int parity, int blocks_x) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  int32_t* s_cnt = reinterpret_cast<int32_t*>(smem_raw);
-  int32_t* s_pre = s_cnt + d.T;
-  __shared__ uint64_t s_warp[kFftThreads / 32];
-  const int t = blockIdx.y;
-  const Rect rc = tile_rect(t, d.ny, d.nx, d.ty, d.tx);
-  const int ya = rc.y0 + blockIdx.x * kFftRows, yb = min(rc.y1, ya + kFftRows);
-  const bool live = *(volatile int32_t*)&d.st->status == 0;
-  float best_a = -1.f, best_v = 0.f;
-  int best_i = 0x7fffffff;
-  if (live) {
-    for (int y = ya; y < yb; ++y)
-      for (int x = rc.x0 + threadIdx.x; x < rc.x1; x += kFftThreads) {
-        const int64_t gi = (int64_t)y * d.nx + x;
-        const float r = R0[gi] - S[(int64_t)y * pitch + x];
-        d.R[gi] = r;
-        R0[gi] = r;
-        const float a = fabsf(r);
-        if (a > best_a || (a == best_a && (int)gi < best_i)) {
-          best_a = a;
-          best_i = (int)gi;
-          best_v = r;
-        }
-      }
-  }
-  uint64_t k = best_a >= 0.f ? make_key(best_v, best_i) : 0ull;
-  k = warp_max_key(k);
-  if ((threadIdx.x & 31) == 0) s_warp[threadIdx.x >> 5] = k;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    uint64_t m = 0;
-    for (int w = 0; w < kFftThreads / 32; ++w) m = umax64(m, s_warp[w]);
-    if (m) atomicMax((unsigned long long*)&d.peak[(parity ^ 1) * d.T + t], (unsigned long long)m);
-  }
-  close_round_if_last(d, parity, blocks_x * d.T, s_cnt, s_pre, A, pitch);
-}
-
 }  // namespace
 
 cudaError_t launch_feedback_ldg(const PlanDev& d, int parity, int apply, cudaStream_t s) {
@@ -871,35 +634,6 @@ cudaError_t launch_feedback(const PlanDev& d, const CUtensorMap* psf_map, int pa
   return cudaGetLastError();
 }
 
-
-cudaError_t fft_build_kernel_image(const PlanDev& d, int Ly, int Lx, float* Kimg,
-                                   cudaStream_t s) {
-  fft_kernel_image<<<4096, 256, 0, s>>>(d.P, d.pny, d.pnx, d.cy, d.cx, d.ny, d.nx, Ly, Lx, Kimg);
-  return cudaGetLastError();
-}
-
-cudaError_t fft_launch_scatter(const PlanDev& d, float* A, int64_t pitch, cudaStream_t s) {
-  fft_scatter<<<(d.T + 3) / 4, 128, 0, s>>>(d, A, pitch);  // a warp per tile
-  return cudaGetLastError();
-}
-
-cudaError_t fft_launch_multiply(void* X, const void* Kh, int64_t n, float scale,
-                                cudaStream_t s) {
-  fft_multiply<<<4096, 256, 0, s>>>(reinterpret_cast<float2*>(X),
-                                    reinterpret_cast<const float2*>(Kh), n, scale);
-  return cudaGetLastError();
-}
-
-cudaError_t fft_launch_subtract(const PlanDev& d, float* R0, const float* S, int64_t pitch,
-                                float* A, int parity, cudaStream_t s) {
-  int maxH = 0;
-  for (int i = 0; i < d.ty; ++i)
-    maxH = max(maxH, (int)(((int64_t)(i + 1) * d.ny) / d.ty - ((int64_t)i * d.ny) / d.ty));
-  const int bx = (maxH + kFftRows - 1) / kFftRows;
-  const size_t smem = sizeof(int32_t) * (2 * (size_t)d.T + 1);
-  fft_subtract<<<dim3(bx, d.T), kFftThreads, smem, s>>>(d, R0, S, pitch, A, parity, bx);
-  return cudaGetLastError();
-}
 
 void feedback_blocks(const PlanDev& d, bool use_tma, int* bx, int* by) {
   int maxH = 0, maxW = 0;
@@ -941,7 +675,7 @@ cudaError_t feedback_prepare(int T) {
   if (e != cudaSuccess) return e;
   e = allow_max_smem((const void*)ldg::feedback_ldg_kernel);
   if (e != cudaSuccess) return e;
-  return allow_max_smem((const void*)fft_subtract);
+  return fft_prepare();
 }
 
 
