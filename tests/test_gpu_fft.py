@@ -58,6 +58,31 @@ def test_fft_rounds_match_float64_replay(case):
     assert np.abs(ident).max() <= 1e-4
 
 
+def test_fft_with_tile_pairs_and_tmem():
+    """FFT feedback behind the streamed minor loop with tile pairs and TMEM
+    chunks: within 1e-4 Jy of the float64 replay after every round, and bit
+    for bit the same as one group per tile (the minor loops agree exactly and
+    the FFT path is deterministic)."""
+    rng = np.random.default_rng(4242)
+    dirty, psf = _sky(512, 512, (1024, 1024), rng, n_src=20)
+    kw = dict(feedback_mode=cg.FB_FFT, group_ctas=2, group_sync=cg.SYNC_GRID, minor_path=2)
+    for R in (1, 3, -1):
+        g = gpu_clean(dirty, psf, 0.1, 1200, 0.0, (1, 2), 20, max_rounds=R, **kw)
+        st = g["stats"]
+        assert st["feedback_mode"] == cg.FB_FFT and st["minor_pairs"] == 1 and st["minor_tmem"] == 1
+        rep = oracle.clean_f64(dirty, psf, 0.1, 1200, 0.0, (1, 2), 20, max_rounds=R,
+                               replay=g["comps"])
+        assert rep.n == g["n"]
+        assert np.abs(g["residual"].astype(np.float64) - rep.residual).max() <= 1e-4, R
+        assert np.abs(g["model"].astype(np.float64) - rep.model).max() <= 1e-4, R
+    single = gpu_clean(dirty, psf, 0.1, 1200, 0.0, (1, 2), 20, minor_pair=0, **kw)
+    assert single["stats"]["minor_pairs"] == 0
+    assert np.array_equal(single["residual"].view(np.uint32), g["residual"].view(np.uint32))
+    assert np.array_equal(single["model"].view(np.uint32), g["model"].view(np.uint32))
+    for k in ("y", "x", "tile", "round"):
+        assert np.array_equal(single["comps"][k], g["comps"][k])
+
+
 @pytest.mark.slow
 def test_fft_paper_band_1024():
     """1024^2, 2 x 2 tiles, K = 50, threshold 5 mJy: FFT feedback vs the exact
