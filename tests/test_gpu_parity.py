@@ -187,6 +187,8 @@ PAIR_CASES = [
     (512, 512, (1024, 1024), (1, 2), 1, 120, 2, 0.0, 1),      # one iteration a launch
     (512, 512, (1024, 1024), (2, 2), 0, 4000, 1, 0.05, 1),    # tiles stop at different times
     (768, 512, (1536, 1024), (3, 1), 10, 300, 2, 0.0, 0),     # odd tile count: one group a tile
+    (1024, 512, (2048, 1024), (2, 1), 15, 500, 2, 0.0, 1),    # a vertical pair
+    (700, 600, (1400, 1200), (3, 2), 12, 900, 1, 0.0, 1),     # three pairs, ragged heights
 ]
 
 
