@@ -17,6 +17,19 @@
 // The loop stops when the tile's budget or K is reached or |v| <= threshold.
 // With `resident`, a CTA holds its rows in shared memory for the whole round
 // and only the PSF window streams in per iteration.
+//
+// The kernels in this file, as the plan picks them:
+//   minor_kernel         plain loads (resident slabs; the allocation-free
+//                        whole-GPU entry point)
+//   minor_pipe_kernel    a TMA producer warp streams each chunk's residual and
+//                        PSF boxes through an mbarrier ring to 15 consumer
+//                        warps; with TM, each CTA's first chunks keep their
+//                        residual in tensor memory for the launch
+//   minor_pair_kernel    the pipeline with groups of 2G CTAs serving two tiles
+//                        alternately (grid groups, streamed rows, even T)
+//   minor_batch_kernel,  the same bodies over the (image, tile) items of a
+//   minor_pipe_batch_kernel  batch (one CTA or one cluster per item)
+// Every variant gives the same bits.
 #include <algorithm>
 
 #include "cleangb_internal.cuh"
