@@ -679,6 +679,9 @@ cudaError_t feedback_prepare(int T) {
 }
 
 
+// 2-D tiled tensor map of a row-major float array, box_w x box_h floats.
+// L2 misses are promoted to 128-byte lines: with 256-byte promotion the
+// feedback round took 2.606 ms, with 128 bytes or none 2.580 (4096^2).
 bool encode_tensor_map_2d(CUtensorMap* map, const float* base, int rows, int cols, int box_w,
                           int box_h) {
   static std::once_flag once;
@@ -699,7 +702,7 @@ bool encode_tensor_map_2d(CUtensorMap* map, const float* base, int rows, int col
   const cuuint32_t estr[2] = {1, 1};
   const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base),
                             dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
