@@ -8,7 +8,8 @@ the round closes.  Inputs are resident in HBM when the timed region starts.
 
 Prints one JSON line: minor iterations per second (whole job), plus
   roofline      the dominant kernel's algorithmic bytes / CUDA-event time,
-                against the measured HBM copy bandwidth
+                against the L2 -> SM read bandwidth measured in the same run
+                (the kernels' hot data is L2-resident)
   cpu_baseline  the CPU oracle on the host cores, on the first round of the
                 same workload (a bounded sample)
   e2e           the same metric through clean_deconvolve_host with host
@@ -226,6 +227,32 @@ def ncu_traffic() -> dict:
             if h == r.get("sha256_16"):
                 out[name] = r
     return out
+
+
+def l2_peak(cg, torch, local):
+    """L2 -> SM read bandwidth of this GPU, measured by the library's probe
+    (clean_probe_l2_read) on a 48 MiB buffer (inside the 126 MB L2): bulk
+    copies into shared memory (1 and 2 CTAs per SM) and 16-byte vector loads
+    (2 and 4 CTAs per SM), 40 passes each, best of three timed launches.
+    The peak is the fastest form; clocks are sampled while it runs."""
+    buf = torch.ones(48 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    sampler = ClockSampler(local)
+    sampler.start()
+    forms = {}
+    for name, method, ctas in (("bulk_copy_1cta", 0, 1), ("bulk_copy_2cta", 0, 2),
+                               ("vector_load_2cta", 1, 2), ("vector_load_4cta", 1, 4)):
+        best = 0.0
+        for _ in range(3):
+            nb, ms = cg.probe_l2_read(buf, passes=40, method=method, ctas_per_sm=ctas)
+            best = max(best, nb / (ms / 1e3) / 1e9)
+        forms[name] = round(best, 1)
+    clocks = sampler.stop()
+    del buf
+    top = max(forms, key=forms.get)
+    return {"GBps": forms[top], "form": top, "forms_GBps": forms, "buffer_bytes": 48 << 20,
+            "clocks": clocks,
+            "method": "clean_probe_l2_read: 48 MiB buffer read 40 times over after a warm "
+                      "pass, CUDA events, best of 3 per form"}
 
 
 def batch_leg(cg, torch, stream, n_images=64):
@@ -550,58 +577,60 @@ def main():
     total_ms, all_comp = aggregate(dist, float(sum(step_ms)), n_comp * args.steps, "cuda")
     value = all_comp / (total_ms / 1e3)
 
-    # ---- roofline of the dominant kernel ----
+    # ---- roofline of the dominant kernel, at the L2 level ----
     peaks, peak_src = measured_peaks()
+    l2 = l2_peak(cg, torch, local)
+    l2_gbs = l2["GBps"]
     minor_avg = st["minor_ms"] / max(st["minor_launches"], 1)
     fb_avg = st["feedback_ms"] / max(st["feedback_launches"], 1)
     rounds_per_run = st["minor_launches"] / args.steps
     minor_b = minor_bytes_per_run(w) / rounds_per_run           # per launch
     fb_upd = feedback_updates_per_run(w) / rounds_per_run       # per launch
+    fb_b = 8.0 * w.n * w.n + 4.0 * fb_upd                       # per launch
     minor_gbs = minor_b / (minor_avg / 1e3) / 1e9
+    fb_gbs = fb_b / (fb_avg / 1e3) / 1e9
     fb_tflops = 2.0 * fb_upd / (fb_avg / 1e3) / 1e12
-    fb_l2_tbs = 4.0 * fb_upd / (fb_avg / 1e3) / 1e12
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak = st["sm_count"] * 128 * sm_mhz * 1e6 / 1e12
     rec = ncu_traffic()
     traffic = {k: v["bytes_per_launch"] for k, v in rec.items()}
-    fb_lts = rec.get("feedback_tma_kernel", {}).get("lts_pct")
     minor_name = ("minor_pair_kernel" if st.get("minor_pairs") else "minor_pipe_kernel") \
         if st["minor_pipe"] else "minor_kernel"
+    fb_name = "feedback_tma_kernel" if st["feedback_tma"] else "feedback_kernel"
+    l2_src = (f"measured in this run: {l2['form']} ({l2['method']}); MEASURED_PEAKS.json "
+              f"holds no L2 figure (its HBM copy peak is {peaks['hbm_gbs']:.0f} GB/s, {peak_src})")
     if st["feedback_ms"] >= st["minor_ms"]:
-        roof = {"kernel": "feedback_tma_kernel" if st["feedback_tma"] else "feedback_kernel",
-                "bound": "alu", "achieved": fb_tflops, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": fb_tflops / alu_peak,
-                "traffic": traffic.get("feedback_tma_kernel") if st["feedback_tma"] else None,
-                "peak_source": f"derived: {st['sm_count']} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz, "
-                               "one separately rounded multiply or subtract per lane per clock "
-                               "(no fused multiply-add on this path)",
-                "flops_per_launch": 2.0 * fb_upd,
-                "l2": {"psf_bytes_per_launch": 4.0 * fb_upd, "achieved_TBps": fb_l2_tbs,
-                       "ncu_lts_throughput_pct_of_peak": fb_lts},
-                "note": "2 flops per pixel-component update; the kernel is L2-bandwidth bound: "
-                        f"{fb_l2_tbs:.1f} TB/s of PSF windows from L2"
-                        + (f" (ncu: lts__throughput {fb_lts:.1f} % of peak, "
-                           "profiles/feedback_tma_kernel_tiled-4096.md)" if fb_lts else "")}
+        roof = {"kernel": fb_name, "bound": "l2", "achieved": fb_gbs, "peak": l2_gbs,
+                "unit": "GB/s", "frac": fb_gbs / l2_gbs, "traffic": traffic.get(fb_name),
+                "peak_source": l2_src, "bytes_per_launch": fb_b,
+                "alu": {"achieved_TFLOPs": fb_tflops, "peak_TFLOPs": alu_peak,
+                        "frac": fb_tflops / alu_peak,
+                        "peak_source": f"derived: {st['sm_count']} SMs x 128 FP32 lanes x "
+                                       f"{sm_mhz:.0f} MHz, separately rounded multiply and "
+                                       "subtract (no fused multiply-add on this path)"},
+                "note": "algorithmic bytes per launch = 8 N^2 (residual in and out) + 4 B of PSF "
+                        "per pixel-component update; traffic = DRAM bytes per launch from ncu"}
     else:
-        roof = {"kernel": minor_name,
-                "bound": "hbm", "achieved": minor_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": minor_gbs / peaks["hbm_gbs"],
-                "traffic": traffic.get(minor_name),
-                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs, copy burst)",
-                "bytes_per_launch": minor_b,
-                "note": "12 B per pixel per tile iteration; the hot set is L2-resident"}
+        roof = {"kernel": minor_name, "bound": "l2", "achieved": minor_gbs, "peak": l2_gbs,
+                "unit": "GB/s", "frac": minor_gbs / l2_gbs, "traffic": traffic.get(minor_name),
+                "peak_source": l2_src, "bytes_per_launch": minor_b,
+                "note": "12 B per pixel per tile iteration; traffic = DRAM bytes per launch"}
     kernels = {
         "minor": {"kernel": minor_name,
                   "ms_per_step": st["minor_ms"] / args.steps,
                   "launches_per_step": rounds_per_run,
-                  "algorithmic_GBps": minor_gbs, "frac_of_hbm_peak": minor_gbs / peaks["hbm_gbs"],
-                  "bytes_per_launch": minor_b,
-                  "traffic": traffic.get(minor_name)},
-        "feedback": {"kernel": "feedback_tma_kernel" if st["feedback_tma"] else "feedback_kernel",
+                  "bytes_per_launch": minor_b, "algorithmic_GBps": minor_gbs,
+                  "frac_of_l2_peak": minor_gbs / l2_gbs,
+                  "traffic": traffic.get(minor_name),
+                  "note": "12 B per pixel per tile iteration (read R, read the PSF window, "
+                          "write R) over the measured L2 read peak"},
+        "feedback": {"kernel": fb_name,
                      "ms_per_step": st["feedback_ms"] / args.steps,
                      "launches_per_step": st["feedback_launches"] / args.steps,
+                     "bytes_per_launch": fb_b, "algorithmic_GBps": fb_gbs,
+                     "frac_of_l2_peak": fb_gbs / l2_gbs,
                      "updates_per_s": fb_upd / (fb_avg / 1e3), "TFLOPs": fb_tflops,
-                     "psf_TBps_from_l2": fb_l2_tbs},
+                     "traffic": traffic.get(fb_name)},
     }
 
     # ---- end to end through host buffers ----
@@ -635,18 +664,27 @@ def main():
         e2e_sampler.start()
         t0 = time.perf_counter()
         ne = 0
-        e2e_steps = []
+        e2e_steps, phases = [], []
         for _ in range(args.steps):
             ts = time.perf_counter()
             ne += host_step()
             e2e_steps.append((time.perf_counter() - ts) * 1e3)
+            phases.append(hp.stats())
         te_ms, ne = aggregate(dist, (time.perf_counter() - t0) * 1e3, ne, "cuda")
         e2e_clocks = e2e_sampler.stop()
         hp.close()
+        split = [{"wall_ms": round(wl, 2), "in_ms": round(p["host_in_ms"], 2),
+                  "run_ms": round(p["host_run_ms"], 2), "out_ms": round(p["host_out_ms"], 2),
+                  "host_ms": round(wl - p["host_in_ms"] - p["host_run_ms"] - p["host_out_ms"], 2)}
+                 for wl, p in zip(e2e_steps, phases)]
         e2e = {"value": ne / (te_ms / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": int(dirty.nbytes + psf.nbytes),
                "d2h_bytes_per_step": int(2 * dirty.nbytes + 16 * w.niter),
-               "step_ms": [round(x, 2) for x in e2e_steps], "clocks": e2e_clocks}
+               "steps": split,
+               "split_note": "per step: wall time of the call; CUDA-event times on its stream "
+                             "of the input copies with the PSF check, the run, the output "
+                             "copies; host_ms = the rest (host work and gaps)",
+               "clocks": e2e_clocks}
 
     # ---- untiled whole-GPU Hogbom on the same image (rate on a prefix) ----
     untiled = None
@@ -716,7 +754,7 @@ def main():
             "config": config_dict(w),
             "px_iter_per_s": value * px_iter,
             "feedback_px_comp_per_s": world * feedback_updates_per_run(w) * args.steps / (total_ms / 1e3),
-            "roofline": roof, "kernels": kernels,
+            "roofline": roof, "kernels": kernels, "l2_probe": l2,
             "cpu_baseline": cpu, "cpu_parallel_baseline": cpu_par,
             "e2e": e2e, "untiled_gpu": untiled,
             "vs_untiled_gpu": (value / untiled["iters_per_s"]) if untiled else None,

@@ -139,6 +139,10 @@ typedef struct {
   int64_t graph_launches;    /* two-round CUDA graphs launched (CLEAN_DEBUG_GRAPHS) */
   int64_t minor_pairs;       /* 1 if the minor loop serves tiles in pairs
                                 (CLEAN_DEBUG_MINOR_PAIR) */
+  double host_in_ms;         /* last clean_deconvolve_host, CUDA-event times on its
+                                stream: input copies (and the PSF check), */
+  double host_run_ms;        /* the run (set-up, rounds, status reads), */
+  double host_out_ms;        /* output copies */
 } clean_stats_t;
 
 /* Fills *p with defaults: gain 0.1, threshold 0, 1 x 1 tiles, K 0, gather
@@ -237,7 +241,8 @@ CLEAN_API int clean_resume(clean_plan_t plan, const void* h_buf, int64_t bytes, 
 /* One whole deconvolution with host buffers: copies h_dirty (and h_psf if
  * not NULL; the plan must own its PSF then) to the device, runs to
  * completion, copies residual, model and components back.  Outputs may be
- * NULL.  Synchronises `stream` before returning. */
+ * NULL.  Synchronises `stream` before returning.  The CUDA-event times of
+ * its three phases (inputs in, run, outputs out) are kept for clean_stats. */
 CLEAN_API int clean_deconvolve_host(clean_plan_t plan, const float* h_dirty,
                           const float* h_psf, float* h_residual,
                           float* h_model, clean_component* h_comps,
@@ -252,18 +257,21 @@ CLEAN_API int clean_deconvolve_host(clean_plan_t plan, const float* h_dirty,
  * The caller passes the inputs (d_dirty ny x nx, d_psf psf_ny x psf_nx,
  * device, read only) and the outputs (d_residual and d_model ny x nx, device;
  * d_comps room for niter components, device; *n_comps, host, receives the
- * count); gain, niter and threshold as in clean_params; d_residual may equal
- * d_dirty.  Results are identical to clean_plan + clean_run with
- * CLEAN_UNTILED_GRID.  The kernels' other memory (grid-barrier counters,
- * per-CTA partial peak keys, control words: 16.5 KiB) is a fixed array
- * compiled into the library, which every GPU that loads the library holds
- * until the process exits.  The first call on a device looks up that
- * array's device address, so make the first call on each device before any
- * stream capture.  All calls share the array and it keeps the last call's
- * contents (the parts that must start at zero are cleared by each call):
- * calls that overlap on the GPU -- on two streams, or from two threads --
- * race and must be serialised by the caller.  Uses one CTA per SM, at most
- * 1024 (CLEAN_ERR_UNSUPPORTED beyond).  Synchronises `stream`.
+ * count); gain and threshold as in clean_params, niter from 0 to 2^31 - 1
+ * (a tighter cap than clean_params': the whole run is one round, whose
+ * component count is a 32-bit word); d_residual may equal d_dirty.  Results
+ * are identical to clean_plan + clean_run with CLEAN_UNTILED_GRID.  The
+ * kernels' other memory (grid-barrier counters, per-CTA partial peak keys,
+ * control words: 16.5 KiB) is a fixed array compiled into the library,
+ * which every GPU that loads the library holds until the process exits.
+ * Each call looks up that array's device address in the current device's
+ * context (cudaGetSymbolAddress, which allocates nothing).  All calls share
+ * the array and it keeps the last call's contents (the parts that must
+ * start at zero are cleared by each call): calls that overlap on the GPU --
+ * on two streams, or from two threads -- race and must be serialised by the
+ * caller.  Uses one CTA per SM (fewer for images with fewer rows than SMs),
+ * at most 1024 (CLEAN_ERR_UNSUPPORTED beyond).  Synchronises `stream`
+ * between its launches to read the status back.
  * Returns CLEAN_OK, CLEAN_ERR_INVALID_ARG (bad size or pointer, PSF peak not
  * at the centre), CLEAN_ERR_NONFINITE, CLEAN_ERR_UNSUPPORTED, CLEAN_ERR_CUDA
  * or CLEAN_ERR_TIMEOUT; it calls no cudaMalloc or cudaFree. */
@@ -361,6 +369,23 @@ CLEAN_API int clean_server_remove(clean_server_t sv, int64_t job_id);
 /* Frees the server and every job still in it. */
 CLEAN_API void clean_server_destroy(clean_server_t sv);
 
+/* ---- Measurement: read bandwidth of the L2 -> SM path -----------------
+ * The minor loop and the feedback stream PSF windows that stay resident in
+ * L2, so their roofline is the rate at which the SMs pull L2-resident data.
+ * This call measures it on the current device (the paper has no
+ * counterpart).  d_buf (device, 16-byte aligned, caller-owned, read only) of
+ * `bytes` bytes should fit well inside L2.  One untimed launch brings it into
+ * L2, then one launch reads it `passes` times over, timed with CUDA events on
+ * `stream`: method 0 with bulk copies into shared memory (16 KiB each, six
+ * in flight per CTA; bytes a multiple of 16384; ctas_per_sm 1 or 2), method
+ * 1 with 16-byte vector loads (bytes a multiple of 16; ctas_per_sm 1..4).
+ * *bytes_read receives the bytes the timed launch read and *ms its duration.
+ * Synchronises `stream`.  CLEAN_OK, CLEAN_ERR_INVALID_ARG, CLEAN_ERR_CUDA, or
+ * CLEAN_ERR_TIMEOUT (a copy did not complete within 1 s). */
+CLEAN_API int clean_probe_l2_read(const void* d_buf, int64_t bytes, int32_t passes,
+                                  int32_t method, int32_t ctas_per_sm, int64_t* bytes_read,
+                                  float* ms, void* stream);
+
 /* Fills *out (host) with the plan's counters.  Synchronises. */
 CLEAN_API int clean_stats(clean_plan_t plan, clean_stats_t* out, void* stream);
 
@@ -380,8 +405,7 @@ CLEAN_API const char* clean_strerror(int status);
  *   CLEAN_DEBUG_FEEDBACK_PATH  feedback kernel: 0 automatic (TMA when the
  *                              PSF is 16-byte aligned with a row pitch that is
  *                              a multiple of 4 floats), 1 plain loads, 2 TMA
- *                              when possible, 3 pipelined global loads (same
- *                              results, bit for bit)
+ *                              when possible (same results, bit for bit)
  *   CLEAN_DEBUG_GRAPHS         1 (default): clean_run replays each two rounds
  *                              from a CUDA graph captured once per launch
  *                              configuration (not while timing, not for the

@@ -24,7 +24,7 @@ __all__ = ["CleanError", "Plan", "Batch", "lib", "library_path", "build", "STATU
            "SYNC_AUTO", "SYNC_CLUSTER", "SYNC_GRID", "COMPONENT_DTYPE",
            "DEBUG_SPIN_LIMIT_NS", "DEBUG_FORCE_TIMEOUT", "DEBUG_TIMING", "DEBUG_FEEDBACK_PATH", "DEBUG_MINOR_PATH",
            "DEBUG_PIPE_CHUNK_PX", "DEBUG_PIPE_STAGES", "DEBUG_GRAPHS", "DEBUG_MINOR_TMEM",
-           "DEBUG_MINOR_PAIR",
+           "DEBUG_MINOR_PAIR", "probe_l2_read",
            "EXPORTED_SYMBOLS"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -68,7 +68,9 @@ class Stats(ctypes.Structure):
                 ("minor_tmem", ctypes.c_int32), ("kernel_launches", ctypes.c_int64),
                 ("minor_launches", ctypes.c_int64), ("feedback_launches", ctypes.c_int64),
                 ("minor_ms", ctypes.c_double), ("feedback_ms", ctypes.c_double),
-                ("graph_launches", ctypes.c_int64), ("minor_pairs", ctypes.c_int64)]
+                ("graph_launches", ctypes.c_int64), ("minor_pairs", ctypes.c_int64),
+                ("host_in_ms", ctypes.c_double), ("host_run_ms", ctypes.c_double),
+                ("host_out_ms", ctypes.c_double)]
 
 
 # name -> (restype, argtypes); the C ABI of include/cleangb.h
@@ -107,6 +109,7 @@ _SIGS = {
     "clean_server_get": (ctypes.c_int, [_vp, ctypes.c_int64, _vp, _vp, _vp, _i64, _vp, _vp]),
     "clean_server_remove": (ctypes.c_int, [_vp, ctypes.c_int64]),
     "clean_server_destroy": (None, [_vp]),
+    "clean_probe_l2_read": (ctypes.c_int, [_vp, _i64, _i32, _i32, _i32, _vp, _vp, _vp]),
 }
 EXPORTED_SYMBOLS = tuple(_SIGS)
 
@@ -140,6 +143,20 @@ def lib():
                 fn.argtypes = args
             _lib = L
     return _lib
+
+
+def probe_l2_read(buf, passes=40, method=0, ctas_per_sm=2, stream=None):
+    """Read bandwidth of the L2 -> SM path over ``buf`` (a CUDA tensor that
+    fits in L2), measured by clean_probe_l2_read.  Returns (bytes read, ms)."""
+    import torch
+    if not isinstance(buf, torch.Tensor) or not buf.is_cuda or not buf.is_contiguous():
+        raise TypeError("buf must be a contiguous CUDA tensor")
+    nb, ms = ctypes.c_int64(0), ctypes.c_float(0.0)
+    _check(lib().clean_probe_l2_read(ctypes.c_void_p(buf.data_ptr()),
+                                     buf.numel() * buf.element_size(), int(passes), int(method),
+                                     int(ctas_per_sm), ctypes.byref(nb), ctypes.byref(ms),
+                                     _stream_ptr(stream)), "clean_probe_l2_read")
+    return int(nb.value), float(ms.value)
 
 
 def _check(status: int, what: str):

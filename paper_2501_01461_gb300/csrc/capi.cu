@@ -75,7 +75,7 @@ struct clean_plan_s {
   void* fft_X = nullptr;     // spectrum work, Ly x (Lx/2+1) complex
   void* fft_Kh = nullptr;    // PSF kernel spectrum, Ly x (Lx/2+1) complex
   float* R0 = nullptr;       // residual at the start of the current round
-  int feedback_path = 0;  // 0 auto, 1 plain loads, 2 TMA, 3 pipelined loads
+  int feedback_path = 0;  // 0 auto, 1 plain loads, 2 TMA
   // two rounds (minor + feedback, twice) captured as a CUDA graph, one per
   // starting parity, together with the launch configuration they captured
   struct GraphKey {
@@ -90,6 +90,10 @@ struct clean_plan_s {
   bool use_graphs = true;
   bool graphs_refused = false;
   int64_t graph_launches = 0;
+  // phases of the last clean_deconvolve_host call: events before the input
+  // copies, after them, after the run, after the output copies
+  cudaEvent_t host_ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  double host_ms[3] = {0.0, 0.0, 0.0};  // inputs in, run, outputs out
 };
 
 namespace {
@@ -270,12 +274,10 @@ int launch_round_feedback(clean_plan_s* pl, cudaStream_t s) {
     ++pl->rounds_launched;
     return CLEAN_OK;
   }
-  const bool use_tma = pl->psf_map_ok && pl->feedback_path != 1 && pl->feedback_path != 3;
+  const bool use_tma = pl->psf_map_ok && pl->feedback_path != 1;
   const int ev = timed_begin(pl, 1, s);
-  cudaError_t e = pl->feedback_path == 3
-                      ? launch_feedback_ldg(pl->d, pl->parity, apply, s)
-                      : launch_feedback(pl->d, use_tma ? &pl->psf_map : nullptr, pl->parity,
-                                        apply, (uint64_t)pl->mc.spin_limit_ns, s);
+  cudaError_t e = launch_feedback(pl->d, use_tma ? &pl->psf_map : nullptr, pl->parity, apply,
+                                  (uint64_t)pl->mc.spin_limit_ns, s);
   timed_end(pl, ev, s);
   ++pl->kernel_launches;
   if (e != cudaSuccess) return cuda_fail(pl, e);
@@ -327,7 +329,7 @@ clean_plan_s::GraphKey graph_key(const clean_plan_s* pl) {
   k.psf_map = pl->psf_map;
   k.pipe = pipe ? 1 : 0;
   k.fb_path = pl->feedback_path;
-  k.tma = (pl->psf_map_ok && pl->feedback_path != 1 && pl->feedback_path != 3) ? 1 : 0;
+  k.tma = (pl->psf_map_ok && pl->feedback_path != 1) ? 1 : 0;
   k.apply = feedback_on(pl->d) ? 1 : 0;
   return k;
 }
@@ -337,7 +339,6 @@ cudaError_t launch_round_pair_part(const clean_plan_s* pl, const clean_plan_s::G
                                    int q, cudaStream_t s) {
   cudaError_t e = launch_minor(k.d, k.mc, q, &k.r_map, &k.p_map, s);
   if (e != cudaSuccess) return e;
-  if (k.fb_path == 3) return launch_feedback_ldg(k.d, q, k.apply, s);
   return launch_feedback(k.d, k.tma ? &k.psf_map : nullptr, q, k.apply,
                          (uint64_t)pl->mc.spin_limit_ns, s);
 }
@@ -614,6 +615,8 @@ void clean_destroy(clean_plan_t pl) {
     if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
     for (void* a : pl->allocs) cudaFree(a);
     for (cudaEvent_t e : pl->ev_pool) cudaEventDestroy(e);
+    for (cudaEvent_t e : pl->host_ev)
+      if (e) cudaEventDestroy(e);
     if (pl->h_st) cudaFreeHost(pl->h_st);
     cudaGetLastError();
   }
@@ -1119,17 +1122,25 @@ int clean_deconvolve_host(clean_plan_t pl, const float* h_dirty, const float* h_
   DeviceGuard g(pl->device);
   cudaStream_t s = as_stream(stream);
   int rc;
+  cudaError_t e = cudaSuccess;
+  for (cudaEvent_t& ev : pl->host_ev)
+    if (!ev && e == cudaSuccess) e = cudaEventCreate(&ev);
+  if (e == cudaSuccess) e = cudaEventRecord(pl->host_ev[0], s);
+  if (e != cudaSuccess) return cuda_fail(pl, e);
   if (h_psf) {
     if ((rc = clean_set_psf(pl, h_psf, 1, stream)) != CLEAN_OK) return rc;
   }
   if ((rc = common_checks(pl)) != CLEAN_OK) return rc;
   const size_t img = sizeof(float) * (size_t)pl->d.ny * pl->d.nx;
   // the dirty image lands in the residual buffer; set-up copies it in place
-  cudaError_t e = cudaMemcpyAsync(pl->d.R, h_dirty, img, cudaMemcpyHostToDevice, s);
+  e = cudaMemcpyAsync(pl->d.R, h_dirty, img, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaEventRecord(pl->host_ev[1], s);
   if (e != cudaSuccess) return cuda_fail(pl, e);
   if ((rc = start_run(pl, pl->d.R, s)) != CLEAN_OK) return rc;
   if ((rc = run_rounds(pl, -1, s)) != CLEAN_OK) return rc;
-  if (h_residual) e = cudaMemcpyAsync(h_residual, pl->d.R, img, cudaMemcpyDeviceToHost, s);
+  e = cudaEventRecord(pl->host_ev[2], s);
+  if (e == cudaSuccess && h_residual)
+    e = cudaMemcpyAsync(h_residual, pl->d.R, img, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess && h_model)
     e = cudaMemcpyAsync(h_model, pl->d.model, img, cudaMemcpyDeviceToHost, s);
   if (e != cudaSuccess) return cuda_fail(pl, e);
@@ -1141,7 +1152,13 @@ int clean_deconvolve_host(clean_plan_t pl, const float* h_dirty, const float* h_
                         cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return cuda_fail(pl, e);
   }
-  e = cudaStreamSynchronize(s);
+  e = cudaEventRecord(pl->host_ev[3], s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
+    float ms = 0.f;
+    e = cudaEventElapsedTime(&ms, pl->host_ev[i], pl->host_ev[i + 1]);
+    pl->host_ms[i] = ms;
+  }
   if (e != cudaSuccess) return cuda_fail(pl, e);
   return CLEAN_OK;
 }
@@ -1158,10 +1175,13 @@ int clean_stats(clean_plan_t pl, clean_stats_t* out, void* stream) {
   out->minor_pairs = (pipe && pl->mc_pipe.pair) ? 1 : 0;
   out->feedback_mode = pl->fft ? CLEAN_FB_FFT : CLEAN_FB_GATHER;
   out->feedback_tma =
-      (pl->psf_map_ok && pl->feedback_path != 1 && pl->feedback_path != 3) ? 1 : 0;
+      (pl->psf_map_ok && pl->feedback_path != 1) ? 1 : 0;
   out->sm_count = pl->sm_count;
   out->rounds_launched = pl->rounds_launched;
   out->kernel_launches = pl->kernel_launches;
+  out->host_in_ms = pl->host_ms[0];
+  out->host_run_ms = pl->host_ms[1];
+  out->host_out_ms = pl->host_ms[2];
   if (pl->poisoned != CLEAN_OK) return pl->poisoned;
   if (!pl->started) return CLEAN_OK;
   DeviceGuard g(pl->device);
@@ -1257,7 +1277,7 @@ int clean_debug_set(clean_plan_t pl, int32_t what, int64_t value) {
       return CLEAN_OK;
     }
     case CLEAN_DEBUG_FEEDBACK_PATH:
-      if (value < 0 || value > 3) return CLEAN_ERR_INVALID_ARG;
+      if (value < 0 || value > 2) return CLEAN_ERR_INVALID_ARG;
       pl->feedback_path = (int)value;
       return CLEAN_OK;
     case CLEAN_DEBUG_GRAPHS:

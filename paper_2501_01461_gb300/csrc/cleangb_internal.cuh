@@ -222,8 +222,6 @@ int minor_max_cluster_ctas(int G, int resident, int smem, int threads);
 // kernel; NULL selects the plain-load kernel.
 cudaError_t launch_feedback(const PlanDev& d, const CUtensorMap* psf_map, int parity,
                             int apply, uint64_t limit_ns, cudaStream_t s);
-// Feedback with the PSF read through pipelined global loads (no TMA).
-cudaError_t launch_feedback_ldg(const PlanDev& d, int parity, int apply, cudaStream_t s);
 cudaError_t feedback_prepare(int T);
 cudaError_t fft_prepare();  // kernel attributes of the FFT feedback (fft_feedback.cu)
 // FFT feedback pieces (see feedback.cu).  Grids are Ly x Lx floats (pitch Lx).

@@ -166,171 +166,6 @@ __global__ void __launch_bounds__(kThreads)
 
 
 // ---------------------------------------------------------------------------
-// Pipelined-load variant.  The same arithmetic and block layout as
-// feedback_kernel, with the PSF values of the next kDepth components already
-// in flight (register buffers) while the current component is applied, so
-// the read latency of L2 is hidden without staging windows in shared memory.
-// The loads go through L1, where windows of nearby components overlap.
-// Components whose window is clipped by the PSF array take a checked path.
-// ---------------------------------------------------------------------------
-namespace ldg {
-
-constexpr int kDepth = 4;     // components whose PSF values are in flight
-constexpr int kChunk = 1024;  // components staged in shared memory at once
-
-struct __align__(16) Win {
-  int32_t sy0, sx0;  // PSF row and column of the block's first pixel
-  float f;           // component flux
-  int32_t inside;    // the block's whole window lies inside the PSF array
-};
-
-size_t smem_bytes(int T) {
-  return sizeof(Win) * kChunk + sizeof(int32_t) * (2 * (size_t)T + 1);
-}
-
-__device__ __forceinline__ void feedback_ldg_body(const PlanDev& d, int parity, int apply, int t,
-                                                  int bxi, int byi, int blocks_x, int blocks_y) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Win* s_win = reinterpret_cast<Win*>(smem_raw);
-  int32_t* s_cnt = reinterpret_cast<int32_t*>(s_win + kChunk);
-  int32_t* s_pre = s_cnt + d.T;  // [T + 1]
-  __shared__ uint64_t s_warp[kWarps];
-
-  const Rect rc = tile_rect(t, d.ny, d.nx, d.ty, d.tx);
-  const int by0 = rc.y0 + byi * kRows;
-  const int bx0 = rc.x0 + bxi * kCols;
-  const bool live = by0 < rc.y1 && bx0 < rc.x1 && *(volatile int32_t*)&d.st->status == 0 &&
-                    round_total(d) > 0;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-
-  if (live) {
-    const bool fb = apply && feedback_on(d);
-    for (int s = threadIdx.x; s < d.T; s += kThreads) s_cnt[s] = (s == t || !fb) ? 0 : d.rcount[s];
-    block_prefix(s_cnt, s_pre, d.T);
-    const int n_other = s_pre[d.T];
-
-    float r[kRowsPerWarp][kColsPerLane];
-    bool in[kRowsPerWarp][kColsPerLane];
-#pragma unroll
-    for (int i = 0; i < kRowsPerWarp; ++i)
-#pragma unroll
-      for (int j = 0; j < kColsPerLane; ++j) {
-        const int y = by0 + warp * kRowsPerWarp + i;
-        const int x = bx0 + lane + 32 * j;
-        in[i][j] = y < rc.y1 && x < rc.x1;
-        r[i][j] = in[i][j] ? d.R[(int64_t)y * d.nx + x] : 0.f;
-      }
-
-    const float* __restrict__ P = d.P;
-    const int pnx = d.pnx;
-    const int wrow = warp * kRowsPerWarp;
-    float buf[kDepth][kRowsPerWarp][kColsPerLane];
-
-    // PSF values of staged component jj for this thread (whole window inside)
-    auto issue = [&](float(&b)[kRowsPerWarp][kColsPerLane], int jj, int n) {
-      if (jj < n) {
-        const Win w = s_win[jj];
-        if (w.inside) {
-          const float* q = P + ((int64_t)(w.sy0 + wrow) * pnx + w.sx0 + lane);
-#pragma unroll
-          for (int i = 0; i < kRowsPerWarp; ++i)
-#pragma unroll
-            for (int j = 0; j < kColsPerLane; ++j) b[i][j] = __ldg(q + (int64_t)i * pnx + 32 * j);
-        }
-      }
-    };
-
-    for (int base = 0; base < n_other; base += kChunk) {
-      const int n = min(kChunk, n_other - base);
-      __syncthreads();
-      for (int jj = threadIdx.x; jj < n; jj += kThreads) {
-        const int g = base + jj;
-        const int s = find_tile(s_pre, d.T, g);
-        const clean_component cc = d.rcomps[(int64_t)s * d.cap_round + (g - s_pre[s])];
-        Win w;
-        w.sy0 = by0 - cc.y + d.cy;
-        w.sx0 = bx0 - cc.x + d.cx;
-        w.f = cc.flux;
-        w.inside = w.sy0 >= 0 && w.sy0 + kRows <= d.pny && w.sx0 >= 0 && w.sx0 + kCols <= d.pnx;
-        s_win[jj] = w;
-      }
-      __syncthreads();
-#pragma unroll
-      for (int u = 0; u < kDepth; ++u) issue(buf[u], u, n);
-      for (int j0 = 0; j0 < n; j0 += kDepth) {
-#pragma unroll
-        for (int u = 0; u < kDepth; ++u) {
-          const int jj = j0 + u;
-          if (jj < n) {
-            const Win w = s_win[jj];
-            if (w.inside) {
-#pragma unroll
-              for (int i = 0; i < kRowsPerWarp; ++i)
-#pragma unroll
-                for (int j = 0; j < kColsPerLane; ++j)
-                  r[i][j] = __fsub_rn(r[i][j], __fmul_rn(w.f, buf[u][i][j]));
-            } else {
-              // window partly off the PSF array: those pixels stay unchanged
-#pragma unroll
-              for (int i = 0; i < kRowsPerWarp; ++i) {
-                const int sy = w.sy0 + wrow + i;
-                const bool yin = (unsigned)sy < (unsigned)d.pny;
-#pragma unroll
-                for (int j = 0; j < kColsPerLane; ++j) {
-                  const int sx = w.sx0 + lane + 32 * j;
-                  if (in[i][j] && yin && (unsigned)sx < (unsigned)pnx)
-                    r[i][j] = __fsub_rn(r[i][j], __fmul_rn(w.f, __ldg(P + (int64_t)sy * pnx + sx)));
-                }
-              }
-            }
-            issue(buf[u], jj + kDepth, n);
-          }
-        }
-      }
-    }
-
-    // write back and reduce this block's peak key
-    float best_a = -1.f, best_v = 0.f;
-    int best_i = 0x7fffffff;
-#pragma unroll
-    for (int i = 0; i < kRowsPerWarp; ++i)
-#pragma unroll
-      for (int j = 0; j < kColsPerLane; ++j) {
-        if (!in[i][j]) continue;
-        const int y = by0 + wrow + i;
-        const int x = bx0 + lane + 32 * j;
-        const int gi = y * d.nx + x;
-        if (n_other > 0) d.R[(int64_t)gi] = r[i][j];
-        const float a = fabsf(r[i][j]);
-        if (a > best_a || (a == best_a && gi < best_i)) {
-          best_a = a;
-          best_i = gi;
-          best_v = r[i][j];
-        }
-      }
-    uint64_t k = best_a >= 0.f ? make_key(best_v, best_i) : 0ull;
-    k = warp_max_key(k);
-    if (lane == 0) s_warp[warp] = k;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      uint64_t m = 0;
-      for (int w = 0; w < kWarps; ++w) m = umax64(m, s_warp[w]);
-      if (m) atomicMax((unsigned long long*)&d.peak[(parity ^ 1) * d.T + t],
-                       (unsigned long long)m);
-    }
-  }
-
-  close_round_if_last(d, parity, blocks_x * blocks_y * d.T, s_cnt, s_pre);
-}
-
-__global__ void __launch_bounds__(kThreads, 2)
-    feedback_ldg_kernel(PlanDev d, int parity, int apply, int blocks_x, int blocks_y) {
-  feedback_ldg_body(d, parity, apply, blockIdx.z, blockIdx.x, blockIdx.y, blocks_x, blocks_y);
-}
-
-}  // namespace ldg
-
-// ---------------------------------------------------------------------------
 // TMA variant.  The same arithmetic, with the PSF window of every component
 // staged into shared memory by one 2-D TMA box load (kBoxW x kRows floats at
 // an x rounded down to 4 floats) through a ring of kStages buffers.  A
@@ -604,14 +439,6 @@ __global__ void __launch_bounds__(tma::kThreads, tma::kMinBlocks)
 
 }  // namespace
 
-cudaError_t launch_feedback_ldg(const PlanDev& d, int parity, int apply, cudaStream_t s) {
-  int bx, by;
-  feedback_blocks(d, false, &bx, &by);
-  ldg::feedback_ldg_kernel<<<dim3(bx, by, d.T), kThreads, ldg::smem_bytes(d.T), s>>>(
-      d, parity, apply, bx, by);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_feedback(const PlanDev& d, const CUtensorMap* psf_map, int parity,
                             int apply, uint64_t limit_ns, cudaStream_t s) {
   // blocks sized for the largest tile; blocks past a smaller tile's edge
@@ -672,8 +499,6 @@ cudaError_t feedback_prepare(int T) {
   cudaError_t e = allow_max_smem((const void*)feedback_kernel);
   if (e != cudaSuccess) return e;
   e = allow_max_smem((const void*)tma::feedback_tma_kernel);
-  if (e != cudaSuccess) return e;
-  e = allow_max_smem((const void*)ldg::feedback_ldg_kernel);
   if (e != cudaSuccess) return e;
   return fft_prepare();
 }

@@ -15,7 +15,6 @@
 // The arithmetic is that of clean_plan/clean_run with CLEAN_UNTILED_GRID:
 // the same set-up kernel and the same grid-synchronised minor-loop kernel.
 #include <cstring>
-#include <mutex>
 
 #include "cleangb_internal.cuh"
 
@@ -38,25 +37,18 @@ static_assert(kOffBar + sizeof(uint32_t) <= kOffKeys, "counters overlap the key 
 
 // The scratch.  In host code this name is only a stand-in for the symbol,
 // never a device address: the device address comes from
-// cudaGetSymbolAddress, once per device.
+// cudaGetSymbolAddress with the device current.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mutex;
-void* g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of the scratch on `dev` (the current device), looked up on
-// the first call for that device.
-cudaError_t scratch_address(int dev, unsigned char** out) {
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_mutex);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_ptr[dev] = p;
-  }
-  *out = static_cast<unsigned char*>(g_scratch_ptr[dev]);
+// Device address of the scratch in the current device's context.  Looked up
+// on every call rather than cached: after cudaDeviceReset, or from another
+// context on the same device, the module is loaded again and the array may
+// sit at another address.  The lookup allocates nothing.
+cudaError_t scratch_address(unsigned char** out) {
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) return e;
+  *out = static_cast<unsigned char*>(p);
   return cudaSuccess;
 }
 
@@ -98,7 +90,7 @@ extern "C" CLEAN_API int clean_hogbom_noalloc(const float* d_dirty, const float*
   if (G > kNoAllocMaxCtas) return CLEAN_ERR_UNSUPPORTED;
 
   unsigned char* base = nullptr;
-  if (scratch_address(dev, &base) != cudaSuccess) {
+  if (scratch_address(&base) != cudaSuccess) {
     cudaGetLastError();
     return CLEAN_ERR_CUDA;
   }

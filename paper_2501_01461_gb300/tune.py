@@ -6,8 +6,7 @@ Two kinds of choices are tuned:
   group barrier of the minor loop (thread-block cluster or bounded grid
   barrier), the minor-loop kernel (plain loads or bulk-copy pipeline, with
   or without tile pairs and tensor-memory chunks) and the feedback kernel
-  (plain loads, TMA windows, pipelined loads).  Every
-  candidate is timed on the problem itself for a few rounds; the fastest
+  (plain loads or TMA windows).  Every candidate is timed on the problem itself for a few rounds; the fastest
   wins.
 * Choices that change results, only on request: the FFT feedback (within
   tolerance of the exact gather, not bit-exact) with ``allow_fft``, and the
@@ -39,7 +38,7 @@ class Choice:
     group_ctas: int = 0
     group_sync: int = SYNC_AUTO
     minor_path: int = 0        # 0 automatic, 1 plain loads, 2 bulk-copy pipeline
-    feedback_path: int = 0     # 0 automatic, 1 plain loads, 2 TMA, 3 pipelined loads
+    feedback_path: int = 0     # 0 automatic, 1 plain loads, 2 TMA
     feedback_mode: int = FB_GATHER
     minor_pairs: int = 1       # 1 tile pairs where they apply, 0 one group per tile
     minor_tmem: int = 1        # 1 tensor-memory chunks where they apply, 0 none
@@ -119,8 +118,7 @@ def candidates(tiles, sm_count: int, allow_fft: bool = False) -> list[Choice]:
     for G in (4, 8, 16):
         if G * T <= 4 * sm_count:
             out.append(Choice(group_ctas=G, group_sync=SYNC_CLUSTER))
-    for fp in (1, 3):
-        out.append(Choice(feedback_path=fp))
+    out.append(Choice(feedback_path=1))
     # the automatic minor loop without tile pairs, and without TMEM chunks
     out.append(Choice(minor_pairs=0))
     out.append(Choice(minor_tmem=0))

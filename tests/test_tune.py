@@ -17,7 +17,7 @@ def test_candidates_cover_paths_and_barriers():
     kinds = {(x.group_sync, x.minor_path, x.feedback_path, x.feedback_mode) for x in c}
     assert any(k[0] == cg.SYNC_GRID for k in kinds)
     assert any(k[0] == cg.SYNC_CLUSTER for k in kinds)
-    assert {1, 3} <= {x.feedback_path for x in c}
+    assert 1 in {x.feedback_path for x in c}
     assert any(not x.minor_pairs for x in c) and any(not x.minor_tmem for x in c)
     assert all(x.feedback_mode == cg.FB_GATHER for x in c)   # exact unless FFT allowed
     assert any(x.feedback_mode == cg.FB_FFT for x in tune.candidates((4, 4), 152, allow_fft=True))
