@@ -448,11 +448,11 @@ cudaError_t launch_round(clean_engine_s* e, int round, cudaStream_t s, int* n) {
     ++*n;
     if (err != cudaSuccess) return err;
   }
-  // FFT-feedback images: each its own transforms and kernels
+  // FFT-feedback images: each its own transform kernels
   for (int w : e->fft_work) {
     const Job& j = e->jobs[e->work_jobs[w]];
     err = plan_fft_round(j.plan, j.dev, (round - j.dev.round0) & 1, s);
-    *n += 5;
+    *n += 3;
     if (err != cudaSuccess) return err;
   }
   return err;

@@ -9,7 +9,6 @@
 #include <utility>
 #include <vector>
 
-#include <cufft.h>
 #include <nvtx3/nvToolsExt.h>
 
 #include "cleangb_internal.cuh"
@@ -23,6 +22,11 @@ std::atomic<int64_t> g_alloc_limit{-1};
 constexpr int64_t kResidentMaxBytes = 200 * 1024;  // residual rows per CTA in smem
 constexpr int kMaxBeamRadius = 64;
 constexpr int64_t kDefaultSpinNs = 2000000000ll;
+// FFT feedback cost model of AUTO (seconds per spectrum cell, per image
+// pixel, and per round's launches), from GB300 measurements
+constexpr double kFftCellS = 8e-12;
+constexpr double kFftPixelS = 4e-12;
+constexpr double kFftLaunchS = 20e-6;
 
 }  // namespace
 
@@ -68,13 +72,13 @@ struct clean_plan_s {
   // FFT feedback (feedback_mode FFT, or AUTO when it is estimated faster)
   bool fft = false;
   int Ly = 0, Lx = 0;
-  cufftHandle fft_r2c = 0, fft_c2r = 0;
-  bool fft_plans = false;
-  float* fft_A = nullptr;    // component grid, Ly x Lx, kept zero between rounds
-  float* fft_S = nullptr;    // convolution result, Ly x Lx
-  void* fft_X = nullptr;     // spectrum work, Ly x (Lx/2+1) complex
-  void* fft_Kh = nullptr;    // PSF kernel spectrum, Ly x (Lx/2+1) complex
-  float* R0 = nullptr;       // residual at the start of the current round
+  FftAxis fft_ay{}, fft_ax{};
+  float2* fft_twy = nullptr;  // twiddle tables exp(-2 pi i t / L) of both axes
+  float2* fft_twx = nullptr;
+  float2* fft_K = nullptr;    // PSF kernel spectrum, (Lx/2 + 1) x Ly
+  float2* fft_Y = nullptr;    // round work area, (Lx/2 + 1) x ny
+  int4* fft_comps = nullptr;  // round work area: the round's components
+  float* R0 = nullptr;        // residual at the start of the current round
   int feedback_path = 0;  // 0 auto, 1 plain loads, 2 TMA
   // two rounds (minor + feedback, twice) captured as a CUDA graph, one per
   // starting parity, together with the launch configuration they captured
@@ -201,26 +205,13 @@ int read_state(clean_plan_s* pl, cudaStream_t s) {
   return CLEAN_OK;
 }
 
-// Smallest n >= m whose only prime factors are 2, 3, 5 and 7.
-int fft_size(int m) {
-  for (int n = std::max(m, 1);; ++n) {
-    int r = n;
-    for (int f : {2, 3, 5, 7})
-      while (r % f == 0) r /= f;
-    if (r == 1) return n;
-  }
-}
-
 // PSF kernel spectrum for the FFT feedback (after every PSF change).
 int fft_prepare_psf(clean_plan_s* pl, cudaStream_t s) {
   if (!pl->fft) return CLEAN_OK;
-  cudaError_t e = fft_build_kernel_image(pl->d, pl->Ly, pl->Lx, pl->fft_S, s);
+  cudaError_t e = fft_build_psf_spectrum(pl->d, pl->fft_ay, pl->fft_ax, pl->fft_twy, pl->fft_twx,
+                                         pl->fft_K, s);
+  pl->kernel_launches += 2;
   if (e != cudaSuccess) return cuda_fail(pl, e);
-  if (cufftSetStream(pl->fft_r2c, s) != CUFFT_SUCCESS ||
-      cufftExecR2C(pl->fft_r2c, pl->fft_S, reinterpret_cast<cufftComplex*>(pl->fft_Kh)) !=
-          CUFFT_SUCCESS)
-    return poison(pl, CLEAN_ERR_CUDA);
-  pl->kernel_launches += 1;
   return CLEAN_OK;
 }
 
@@ -257,7 +248,7 @@ int check_psf(clean_plan_s* pl, cudaStream_t s) {
 // One FFT feedback: scatter the round's components, convolve with the PSF
 // through the cached spectrum, R <- R0 - S everywhere, next peaks, close.
 cudaError_t launch_fft_feedback(clean_plan_s* pl, cudaStream_t s) {
-  pl->kernel_launches += 2;  // the two transforms
+  pl->kernel_launches += 2;  // component list and columns (the caller counts the rows)
   return plan_fft_round(pl, pl->d, pl->parity, s);
 }
 
@@ -534,21 +525,8 @@ cudaError_t plan_fft_start(clean_plan_s* pl, const PlanDev& d, cudaStream_t s) {
 }
 
 cudaError_t plan_fft_round(clean_plan_s* pl, const PlanDev& d, int parity, cudaStream_t s) {
-  const int64_t pitch = pl->Lx;
-  const int64_t nspec = (int64_t)pl->Ly * (pl->Lx / 2 + 1);
-  cudaError_t e = fft_launch_scatter(d, pl->fft_A, pitch, s);
-  if (e != cudaSuccess) return e;
-  if (cufftSetStream(pl->fft_r2c, s) != CUFFT_SUCCESS ||
-      cufftSetStream(pl->fft_c2r, s) != CUFFT_SUCCESS ||
-      cufftExecR2C(pl->fft_r2c, pl->fft_A, reinterpret_cast<cufftComplex*>(pl->fft_X)) !=
-          CUFFT_SUCCESS)
-    return cudaErrorUnknown;
-  e = fft_launch_multiply(pl->fft_X, pl->fft_Kh, nspec, 1.0f / ((float)pl->Ly * (float)pl->Lx), s);
-  if (e != cudaSuccess) return e;
-  if (cufftExecC2R(pl->fft_c2r, reinterpret_cast<cufftComplex*>(pl->fft_X), pl->fft_S) !=
-      CUFFT_SUCCESS)
-    return cudaErrorUnknown;
-  return fft_launch_subtract(d, pl->R0, pl->fft_S, pitch, pl->fft_A, parity, s);
+  return fft_feedback_round(d, pl->fft_ay, pl->fft_ax, pl->fft_twy, pl->fft_twx, pl->fft_K,
+                            pl->fft_Y, pl->fft_comps, pl->R0, parity, s);
 }
 
 }  // namespace cleangb
@@ -607,10 +585,6 @@ void clean_destroy(clean_plan_t pl) {
   {
     DeviceGuard g(pl->device);
     cudaDeviceSynchronize();
-    if (pl->fft_plans) {
-      cufftDestroy(pl->fft_r2c);
-      cufftDestroy(pl->fft_c2r);
-    }
     drop_graphs(pl);
     if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
     for (void* a : pl->allocs) cudaFree(a);
@@ -750,22 +724,30 @@ int clean_plan(clean_plan_t* out, const clean_params* p, const float* d_psf, voi
   // FFT feedback: a grid of at least (2 ny - 1) x (2 nx - 1) so the circular
   // convolution never wraps onto an image pixel.  AUTO takes it when a round's
   // gather (about 0.21 ns per pixel-component update on GB300) would cost more
-  // than the transforms (estimated 16 ps per grid cell plus 60 us of launches).
+  // than the transforms (estimated per spectrum cell and per image pixel, plus
+  // the launches).  Grids longer than kFftMaxL per axis are not served.
   const bool fb_on = (p->feedback_interval > 0 || p->feedback_trigger > 0.f) && T > 1;
   const int fb_mode = forced_feedback_mode(p->feedback_mode);
-  pl->Ly = fft_size(2 * p->ny - 1);
-  pl->Lx = fft_size(2 * p->nx - 1);
-  if (fb_on && fb_mode == CLEAN_FB_FFT) pl->fft = true;
-  if (fb_on && fb_mode == CLEAN_FB_AUTO) {
+  pl->Ly = fft_grid_size(2 * p->ny - 1);
+  pl->Lx = fft_grid_size(2 * p->nx - 1);
+  const bool fft_ok = fft_axis_init(&pl->fft_ay, pl->Ly) && fft_axis_init(&pl->fft_ax, pl->Lx);
+  if (fb_on && fb_mode == CLEAN_FB_FFT) {
+    if (!fft_ok) {
+      delete pl;
+      return CLEAN_ERR_UNSUPPORTED;
+    }
+    pl->fft = true;
+  }
+  if (fb_on && fb_mode == CLEAN_FB_AUTO && fft_ok) {
     const double comps =
         (double)(p->feedback_interval > 0 ? std::min<int64_t>(p->feedback_interval, per_tile_max)
                                           : per_tile_max) * T;
     const double gather_s = comps * ((double)npix - (double)npix / T) * 0.21e-9;
-    const double fft_s = (double)pl->Ly * pl->Lx * 16e-12 + 60e-6;
+    const double fft_s = (double)pl->Ly * (pl->Lx / 2 + 1) * kFftCellS +
+                         (double)npix * kFftPixelS + kFftLaunchS;
     pl->fft = fft_s < gather_s;
   }
-  const size_t grid_bytes = sizeof(float) * (size_t)pl->Ly * pl->Lx;
-  const size_t spec_bytes = sizeof(cufftComplex) * (size_t)pl->Ly * (pl->Lx / 2 + 1);
+  const size_t spec_bytes = sizeof(float2) * (size_t)pl->Ly * (pl->Lx / 2 + 1);
   const int beam_n = (2 * kMaxBeamRadius + 1) * (2 * kMaxBeamRadius + 1);
   std::vector<Req> req = {
       {(void**)&pl->d.R, sizeof(float) * (size_t)npix},
@@ -784,10 +766,11 @@ int clean_plan(clean_plan_t* out, const clean_params* p, const float* d_psf, voi
   };
   if (!d_psf) req.push_back({(void**)&pl->psf_own, sizeof(float) * (size_t)p->psf_ny * p->psf_nx});
   if (pl->fft) {
-    req.push_back({(void**)&pl->fft_A, grid_bytes});
-    req.push_back({(void**)&pl->fft_S, grid_bytes});
-    req.push_back({(void**)&pl->fft_X, spec_bytes});
-    req.push_back({(void**)&pl->fft_Kh, spec_bytes});
+    req.push_back({(void**)&pl->fft_K, spec_bytes});
+    req.push_back({(void**)&pl->fft_Y, sizeof(float2) * (size_t)(pl->Lx / 2 + 1) * p->ny});
+    req.push_back({(void**)&pl->fft_comps, sizeof(int4) * (size_t)(1 + cap_round * T)});
+    req.push_back({(void**)&pl->fft_twy, sizeof(float2) * (size_t)pl->Ly});
+    req.push_back({(void**)&pl->fft_twx, sizeof(float2) * (size_t)pl->Lx});
     req.push_back({(void**)&pl->R0, sizeof(float) * (size_t)npix});
   }
   size_t total = 0;
@@ -831,22 +814,11 @@ int clean_plan(clean_plan_t* out, const clean_params* p, const float* d_psf, voi
   d.trigger = p->feedback_trigger;
   d.cap_round = (int32_t)cap_round;
 
-  if (pl->fft) {
-    if (cufftPlan2d(&pl->fft_r2c, pl->Ly, pl->Lx, CUFFT_R2C) != CUFFT_SUCCESS) {
-      clean_destroy(pl);
-      return CLEAN_ERR_OOM;
-    }
-    if (cufftPlan2d(&pl->fft_c2r, pl->Ly, pl->Lx, CUFFT_C2R) != CUFFT_SUCCESS) {
-      cufftDestroy(pl->fft_r2c);
-      clean_destroy(pl);
-      return CLEAN_ERR_OOM;
-    }
-    pl->fft_plans = true;
-    if (cudaMemsetAsync(pl->fft_A, 0, grid_bytes, s) != cudaSuccess) {
-      cudaGetLastError();
-      clean_destroy(pl);
-      return CLEAN_ERR_CUDA;
-    }
+  if (pl->fft && (fft_make_twiddles(pl->fft_twy, pl->Ly, s) != cudaSuccess ||
+                  fft_make_twiddles(pl->fft_twx, pl->Lx, s) != cudaSuccess)) {
+    cudaGetLastError();
+    clean_destroy(pl);
+    return CLEAN_ERR_CUDA;
   }
   if (cudaMemsetAsync(d.gbar, 0, sizeof(uint32_t) * T, s) != cudaSuccess ||
       cudaMemsetAsync(d.st, 0, sizeof(DevState), s) != cudaSuccess) {
@@ -1099,12 +1071,9 @@ int clean_resume(clean_plan_t pl, const void* h_buf, int64_t bytes, void* stream
   if (e == cudaSuccess) e = cudaMemsetAsync(pl->d.gbar, 0, sizeof(uint32_t) * pl->d.T, s);
   if (e == cudaSuccess)
     e = cudaMemsetAsync(pl->d.gkeys, 0x80, sizeof(uint64_t) * 4 * (size_t)pl->d.T * pl->mc.G, s);
-  if (e == cudaSuccess && pl->fft) {
+  if (e == cudaSuccess && pl->fft)
     e = cudaMemcpyAsync(pl->R0, pl->d.R, sizeof(float) * (size_t)npix, cudaMemcpyDeviceToDevice,
                         s);
-    if (e == cudaSuccess)
-      e = cudaMemsetAsync(pl->fft_A, 0, sizeof(float) * (size_t)pl->Ly * pl->Lx, s);
-  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the host buffer may go now
   if (e != cudaSuccess) return cuda_fail(pl, e);
   pl->started = true;

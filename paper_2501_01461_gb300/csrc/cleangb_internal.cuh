@@ -223,15 +223,37 @@ int minor_max_cluster_ctas(int G, int resident, int smem, int threads);
 cudaError_t launch_feedback(const PlanDev& d, const CUtensorMap* psf_map, int parity,
                             int apply, uint64_t limit_ns, cudaStream_t s);
 cudaError_t feedback_prepare(int T);
-cudaError_t fft_prepare();  // kernel attributes of the FFT feedback (fft_feedback.cu)
-// FFT feedback pieces (see feedback.cu).  Grids are Ly x Lx floats (pitch Lx).
-cudaError_t fft_build_kernel_image(const PlanDev& d, int Ly, int Lx, float* Kimg,
+// ---- FFT feedback (fft_feedback.cu) -----------------------------------------
+// One axis of the 2-D transforms: length L (even, 7-smooth, <= kFftMaxL),
+// its radices in stage order and the threads of a block that transforms it
+// (every thread holds at most kFftValsPerThread values in a stage).
+constexpr int kFftMaxL = 8192;
+constexpr int kFftMaxThreads = 512;
+constexpr int kFftMaxRadices = 16;
+constexpr int kFftValsPerThread = 16;
+struct FftAxis {
+  int32_t L, nthr, nrad;
+  int32_t rad[kFftMaxRadices];
+};
+// Smallest even n >= m whose prime factors are 2, 3, 5 and 7.
+int fft_grid_size(int m);
+// Fills *a for length L; false if L is odd, above kFftMaxL or not 7-smooth.
+bool fft_axis_init(FftAxis* a, int L);
+// Twiddle table exp(-2 pi i t / L), t < L, computed in double precision on
+// the host and copied to d_tw (L float2); synchronises s.
+cudaError_t fft_make_twiddles(float2* d_tw, int L, cudaStream_t s);
+// Kernel spectrum Kspec[k][m] (k <= Lx / 2, m < Ly) of the PSF kernel image
+// K[d mod L] = P[d + c] (|d| < image size), scaled by 1 / (Ly Lx).
+cudaError_t fft_build_psf_spectrum(const PlanDev& d, const FftAxis& ay, const FftAxis& ax,
+                                   const float2* twy, const float2* twx, float2* Kspec,
                                    cudaStream_t s);
-cudaError_t fft_launch_scatter(const PlanDev& d, float* A, int64_t pitch, cudaStream_t s);
-cudaError_t fft_launch_multiply(void* X, const void* Kh, int64_t n, float scale,
-                                cudaStream_t s);
-cudaError_t fft_launch_subtract(const PlanDev& d, float* R0, const float* S, int64_t pitch,
-                                float* A, int parity, cudaStream_t s);
+// One FFT feedback: R <- R0 - (round components (*) PSF) on every pixel,
+// R0 <- R, next peaks, round close.  Y: (Lx/2 + 1) x ny float2 work area;
+// comps: 1 + T cap_round int4 work area.
+cudaError_t fft_feedback_round(const PlanDev& d, const FftAxis& ay, const FftAxis& ax,
+                               const float2* twy, const float2* twx, const float2* Kspec,
+                               float2* Y, int4* comps, float* R0, int parity, cudaStream_t s);
+cudaError_t fft_prepare();  // kernel attributes of the FFT feedback
 // Encodes the PSF tensor map for the TMA feedback kernel; false if the PSF's
 // address or row pitch is not 16-byte aligned (or the driver lacks TMA).
 bool make_psf_tensor_map(CUtensorMap* map, const float* psf, int pny, int pnx);

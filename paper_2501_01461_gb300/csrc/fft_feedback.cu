@@ -1,8 +1,38 @@
-// FFT feedback (Section 3): the round's components, every tile's, convolved
-// with the full PSF through cuFFT transforms, with this library's scatter,
-// spectrum multiply and subtract kernels around them.
-// Within a tolerance of the exact gather, not bit-exact; the cuFFT plans live
-// with the plan (capi.cu).
+// FFT feedback (Section 3, Figs. 2-3): the round's components, every tile's,
+// convolved with the full PSF by this library's own transforms.  Within a
+// tolerance of the exact gather, not bit-exact.
+//
+// The components, placed on an Ly x Lx grid (Ly >= 2 ny - 1, Lx >= 2 nx - 1),
+// convolved circularly with the PSF kernel K[d mod L] = P[d + c], give at
+// every image pixel q
+//     S[q] = sum_c f_c P[q - p_c + c]
+// with no wrap-around.  The residual after the round is the residual at the
+// round's start minus S on every pixel of every tile (the minor loops'
+// own-tile subtractions included), so no per-tile correction is needed.
+//
+// The 2-D transforms are split by axis and pruned to what the round needs:
+//   columns (one CTA per frequency k of the x axis, k = 0 .. Lx/2):
+//       the column's input is the x-axis DFT of the component grid at k,
+//       sum over the components of a row of f e^{-2 pi i k x / Lx}, evaluated
+//       directly (a round has few components: the grid is sparse); then a
+//       forward FFT along y, the product with the cached kernel spectrum, an
+//       inverse FFT along y, and only rows 0 .. ny - 1 are stored;
+//   rows (one CTA per pair of image rows): the Hermitian half of each row's
+//       x-axis spectrum is extended to the full length, two real rows ride in
+//       one complex inverse FFT (one as the real, one as the imaginary part),
+//       and only columns 0 .. nx - 1 are kept; the same CTA then sets
+//       R <- R_round_start - S, reduces the next peaks and closes the round.
+// The kernel spectrum is built the same way once per PSF (dense rows, two
+// per complex FFT, then columns).
+//
+// Every 1-D transform is a mixed-radix (8, 4, 2, 3, 5, 7) Stockham FFT in
+// shared memory: each stage reads a thread's butterfly inputs into
+// registers, applies the stage twiddles, synchronises, and writes the small
+// DFT's outputs back to the autosorted positions.  Twiddles come from a
+// table exp(-2 pi i t / L) computed in double precision on the host.
+#include <cmath>
+#include <vector>
+
 #include "cleangb_internal.cuh"
 #include "round_close.cuh"
 
@@ -10,186 +40,442 @@ namespace cleangb {
 
 namespace {
 
-// ---------------------------------------------------------------------------
-// FFT feedback (tolerance-exact alternative to the gather).  The round's
-// components, scattered onto an L x L grid (L >= 2N - 1 in each axis),
-// convolved circularly with the PSF kernel K[d mod L] = P[d + c] give, at
-// every image pixel q, S[q] = sum_c f_c P[q - p_c + c] with no wrap-around.
-// The residual after the round is then the residual at the round's start
-// minus S on every pixel of every tile (the minor loops' own-tile
-// subtractions included), so no per-tile correction is needed.
-// ---------------------------------------------------------------------------
-constexpr int kFftThreads = 256;
-constexpr int kFftRows = 16;
+__device__ __forceinline__ int fpad(int i) { return i + (i >> 5); }  // shared-memory padding
 
-// K[(dy mod Ly), (dx mod Lx)] = P[dy + cy, dx + cx] for |dy| < ny, |dx| < nx
-// inside the PSF; zero elsewhere.  One thread per grid element.
-__global__ void fft_kernel_image(const float* __restrict__ P, int pny, int pnx, int cy, int cx,
-                                 int ny, int nx, int Ly, int Lx, float* __restrict__ Kimg) {
-  const int64_t n = (int64_t)Ly * Lx;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int my = (int)(i / Lx), mx = (int)(i - (int64_t)my * Lx);
-    const int dy = my < ny ? my : my - Ly;   // represent m as d in (-(L - ny), ny)
-    const int dx = mx < nx ? mx : mx - Lx;
-    float v = 0.f;
-    if (dy > -ny && dx > -nx) {
-      const int sy = dy + cy, sx = dx + cx;
-      if ((unsigned)sy < (unsigned)pny && (unsigned)sx < (unsigned)pnx)
-        v = P[(int64_t)sy * pnx + sx];
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// multiply by -i (forward) or +i (inverse)
+__device__ __forceinline__ float2 rot(float2 a, bool inv) {
+  return inv ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+// Small DFTs X[m] = sum_r v[r] w^(r m), w = e^(-2 pi i / R) (e^(+...) when inv).
+template <int R>
+struct Dft;
+
+template <>
+struct Dft<2> {
+  __device__ __forceinline__ static void run(float2 (&v)[2], bool, const float2*, int) {
+    const float2 a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+  }
+};
+
+template <>
+struct Dft<4> {
+  __device__ __forceinline__ static void run(float2 (&v)[4], bool inv, const float2*, int) {
+    const float2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+    const float2 t2 = cadd(v[1], v[3]), t3 = rot(csub(v[1], v[3]), inv);
+    v[0] = cadd(t0, t2);
+    v[2] = csub(t0, t2);
+    v[1] = cadd(t1, t3);
+    v[3] = csub(t1, t3);
+  }
+};
+
+template <>
+struct Dft<8> {
+  // radix 2 over (r, r + 4), then two DFT-4s, the odd one after the
+  // twiddles w8^r
+  __device__ __forceinline__ static void run(float2 (&v)[8], bool inv, const float2*, int) {
+    const float h = 0.70710678118654752f;  // sqrt(2) / 2
+    float2 b[4], c[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      b[r] = cadd(v[r], v[r + 4]);
+      c[r] = csub(v[r], v[r + 4]);
     }
-    Kimg[i] = v;
+    // c[r] *= w8^r, w8 = (1 - i) / sqrt(2) forward, (1 + i) / sqrt(2) inverse
+    c[1] = inv ? make_float2((c[1].x - c[1].y) * h, (c[1].x + c[1].y) * h)
+               : make_float2((c[1].x + c[1].y) * h, (c[1].y - c[1].x) * h);
+    c[2] = rot(c[2], inv);
+    c[3] = inv ? make_float2(-(c[3].x + c[3].y) * h, (c[3].x - c[3].y) * h)
+               : make_float2((c[3].y - c[3].x) * h, -(c[3].x + c[3].y) * h);
+    Dft<4>::run(b, inv, nullptr, 0);
+    Dft<4>::run(c, inv, nullptr, 0);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      v[2 * m] = b[m];
+      v[2 * m + 1] = c[m];
+    }
   }
-}
+};
 
-// The round's components onto the (zeroed) grid: one warp per tile (a
-// tile's components lie inside it, so tiles never share a cell).  Lane l
-// takes components l, l + 32, ...; the first component at a cell sums every
-// component of the tile at that cell in iteration order and writes the cell
-// once, so each cell gets ((0 + f1) + f2) + ... exactly as one thread adding
-// them in order would.  Above kScatterQuadMax components the quadratic
-// search gives way to one thread in order.
-constexpr int kScatterQuadMax = 4096;
-__global__ void fft_scatter(PlanDev d, float* __restrict__ A, int64_t pitch) {
-  const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (t >= d.T) return;
-  const int n = d.rcount[t];
-  const clean_component* c = d.rcomps + (int64_t)t * d.cap_round;
-  if (n > kScatterQuadMax) {
-    if (lane == 0)
-      for (int k = 0; k < n; ++k) {
-        float* a = &A[(int64_t)c[k].y * pitch + c[k].x];
-        *a = *a + c[k].flux;
+// Odd radices: the roots of unity from the length-L table (R divides L).
+template <int R>
+struct Dft {
+  __device__ __forceinline__ static void run(float2 (&v)[R], bool inv, const float2* tw, int L) {
+    float2 w[R];
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+      w[m] = __ldg(&tw[m * (L / R)]);
+      if (inv) w[m].y = -w[m].y;
+    }
+    float2 out[R];
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+      float2 acc = v[0];
+#pragma unroll
+      for (int r = 1; r < R; ++r) acc = cadd(acc, cmul(v[r], w[(r * m) % R]));
+      out[m] = acc;
+    }
+#pragma unroll
+    for (int m = 0; m < R; ++m) v[m] = out[m];
+  }
+};
+
+// One Stockham stage of radix R over buf[0 .. L): sub-transforms of size Ns
+// become sub-transforms of size Ns R.  Every thread of the block calls it.
+template <int R>
+__device__ __forceinline__ void fft_stage(float2* buf, int L, int Ns, const float2* __restrict__ tw,
+                                          bool inv) {
+  constexpr int kMaxB = (kFftValsPerThread + R - 1) / R;
+  const int nb = L / R;
+  const int step = L / (Ns * R);
+  const int nthr = blockDim.x;
+  float2 v[kMaxB][R];
+#pragma unroll
+  for (int b = 0; b < kMaxB; ++b) {
+    const int j = threadIdx.x + b * nthr;
+    if (j < nb) {
+      const int k = j % Ns;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        float2 w = __ldg(&tw[r * k * step]);
+        if (inv) w.y = -w.y;
+        v[b][r] = cmul(buf[fpad(j + r * nb)], w);
       }
-    return;
+    }
   }
-  for (int k = lane; k < n; k += 32) {
-    const clean_component ck = c[k];
-    bool first = true;
-    for (int j = 0; j < k && first; ++j) first = !(c[j].y == ck.y && c[j].x == ck.x);
-    if (!first) continue;
-    float* a = &A[(int64_t)ck.y * pitch + ck.x];
-    float acc = *a + ck.flux;
-    for (int j = k + 1; j < n; ++j)
-      if (c[j].y == ck.y && c[j].x == ck.x) acc = acc + c[j].flux;
-    *a = acc;
+  __syncthreads();
+#pragma unroll
+  for (int b = 0; b < kMaxB; ++b) {
+    const int j = threadIdx.x + b * nthr;
+    if (j < nb) {
+      Dft<R>::run(v[b], inv, tw, L);
+      const int k = j % Ns;
+      const int base = (j - k) * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) buf[fpad(base + r * Ns)] = v[b][r];
+    }
+  }
+  __syncthreads();
+}
+
+// Whole 1-D transform of buf (length ax.L, natural order in and out,
+// unnormalised).  The caller synchronises before (inputs written) and the
+// last stage synchronises after.
+__device__ void fft_1d(float2* buf, const FftAxis& ax, const float2* __restrict__ tw, bool inv) {
+  int Ns = 1;
+  for (int s = 0; s < ax.nrad; ++s) {
+    const int R = ax.rad[s];
+    switch (R) {
+      case 8: fft_stage<8>(buf, ax.L, Ns, tw, inv); break;
+      case 4: fft_stage<4>(buf, ax.L, Ns, tw, inv); break;
+      case 2: fft_stage<2>(buf, ax.L, Ns, tw, inv); break;
+      case 3: fft_stage<3>(buf, ax.L, Ns, tw, inv); break;
+      case 5: fft_stage<5>(buf, ax.L, Ns, tw, inv); break;
+      default: fft_stage<7>(buf, ax.L, Ns, tw, inv); break;
+    }
+    Ns *= R;
   }
 }
 
-// X <- X * K / (Ly Lx), complex, element by element.
-__global__ void fft_multiply(float2* __restrict__ X, const float2* __restrict__ Kh, int64_t n,
-                             float scale) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const float2 a = X[i], b = Kh[i];
-    X[i] = make_float2((a.x * b.x - a.y * b.y) * scale, (a.x * b.y + a.y * b.x) * scale);
+// ---- PSF kernel spectrum (once per PSF) -------------------------------------
+
+// Kernel image value K(my, mx) = P[dy + cy, dx + cx] with d the signed
+// representative of m (|dy| < ny, |dx| < nx), zero elsewhere.
+__device__ __forceinline__ float kernel_image(const PlanDev& d, int Ly, int Lx, int my, int mx) {
+  const int dy = my < d.ny ? my : my - Ly;
+  const int dx = mx < d.nx ? mx : mx - Lx;
+  if (dy <= -d.ny || dx <= -d.nx) return 0.f;
+  const int sy = dy + d.cy, sx = dx + d.cx;
+  if ((unsigned)sy >= (unsigned)d.pny || (unsigned)sx >= (unsigned)d.pnx) return 0.f;
+  return d.P[(int64_t)sy * d.pnx + sx];
+}
+
+// Rows 2a and 2a + 1 of the kernel image through one complex FFT along x;
+// their Hermitian halves go to Kspec[k][2a], Kspec[k][2a + 1] (k <= Lx/2).
+__global__ void __launch_bounds__(kFftMaxThreads, 1) fft_psf_rows_kernel(PlanDev d, FftAxis ax, int Ly, const float2* __restrict__ twx,
+                                    float2* __restrict__ Kspec) {
+  extern __shared__ float2 fbuf[];
+  const int Lx = ax.L, a = blockIdx.x;
+  for (int mx = threadIdx.x; mx < Lx; mx += blockDim.x)
+    fbuf[fpad(mx)] = make_float2(kernel_image(d, Ly, Lx, 2 * a, mx),
+                                 kernel_image(d, Ly, Lx, 2 * a + 1, mx));
+  __syncthreads();
+  fft_1d(fbuf, ax, twx, false);
+  for (int k = threadIdx.x; k <= Lx / 2; k += blockDim.x) {
+    const float2 z1 = fbuf[fpad(k)];
+    const float2 z = fbuf[fpad(k == 0 ? 0 : Lx - k)];
+    const float2 z2 = make_float2(z.x, -z.y);  // conj(Z[L - k])
+    const float2 A = make_float2(0.5f * (z1.x + z2.x), 0.5f * (z1.y + z2.y));
+    const float2 B = make_float2(0.5f * (z1.y - z2.y), -0.5f * (z1.x - z2.x));  // (z1 - z2) / 2i
+    Kspec[(int64_t)k * Ly + 2 * a] = A;
+    Kspec[(int64_t)k * Ly + 2 * a + 1] = B;
   }
 }
 
-// R <- R0 - S on tile t's rows [ya, ya + kFftRows); R0 <- R; the block's
-// peak into the tile's next-round key; the last block closes the round and
-// clears the scattered grid cells.
-__global__ void __launch_bounds__(kFftThreads)
-    fft_subtract(PlanDev d, float* __restrict__ R0, const float* __restrict__ S, int64_t pitch,
-                 float* __restrict__ A, int parity, int blocks_x) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  int32_t* s_cnt = reinterpret_cast<int32_t*>(smem_raw);
-  int32_t* s_pre = s_cnt + d.T;
-  __shared__ uint64_t s_warp[kFftThreads / 32];
-  const int t = blockIdx.y;
-  const Rect rc = tile_rect(t, d.ny, d.nx, d.ty, d.tx);
-  const int ya = rc.y0 + blockIdx.x * kFftRows, yb = min(rc.y1, ya + kFftRows);
+// Column k of the row transforms through a forward FFT along y, scaled by
+// 1 / (Ly Lx), in place.
+__global__ void __launch_bounds__(kFftMaxThreads, 1) fft_psf_cols_kernel(FftAxis ay, const float2* __restrict__ twy,
+                                    float2* __restrict__ Kspec, float scale) {
+  extern __shared__ float2 fbuf[];
+  const int Ly = ay.L;
+  float2* col = Kspec + (int64_t)blockIdx.x * Ly;
+  for (int i = threadIdx.x; i < Ly; i += blockDim.x) fbuf[fpad(i)] = col[i];
+  __syncthreads();
+  fft_1d(fbuf, ay, twy, false);
+  for (int i = threadIdx.x; i < Ly; i += blockDim.x) {
+    const float2 v = fbuf[fpad(i)];
+    col[i] = make_float2(v.x * scale, v.y * scale);
+  }
+}
+
+// ---- one round ----------------------------------------------------------------
+
+// The round's components of every tile in list order (tile, then iteration)
+// as (y, x, flux bits, 0) from comps[1]; comps[0].x = their number (0 when
+// the plan's status is bad).  One block.
+__global__ void fft_comp_list_kernel(PlanDev d, int4* __restrict__ comps) {
+  extern __shared__ int32_t s_int[];
+  int32_t* s_cnt = s_int;
+  int32_t* s_pre = s_int + d.T;
   const bool live = *(volatile int32_t*)&d.st->status == 0;
-  float best_a = -1.f, best_v = 0.f;
-  int best_i = 0x7fffffff;
-  // 16-byte rows (tile columns, image width and grid pitch multiples of 4):
-  // four pixels a thread and step, the peak kept per 4-pixel group as in the
-  // minor loop (largest |R|, lowest base index) and resolved once at the end
-  const bool vec = ((rc.x0 | (rc.x1 - rc.x0) | d.nx | (int)pitch) & 3) == 0;
-  if (live && vec) {
-    int best_base = 0x7fffffff;
-    float4 best_r = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int y = ya; y < yb; ++y)
-      for (int x = rc.x0 + 4 * threadIdx.x; x < rc.x1; x += 4 * kFftThreads) {
-        const int64_t gi = (int64_t)y * d.nx + x;
-        const float4 a = *reinterpret_cast<const float4*>(R0 + gi);
-        const float4 b = *reinterpret_cast<const float4*>(S + (int64_t)y * pitch + x);
-        const float4 r = make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
-        *reinterpret_cast<float4*>(d.R + gi) = r;
-        *reinterpret_cast<float4*>(R0 + gi) = r;
-        const float m = fmaxf(fmaxf(fabsf(r.x), fabsf(r.y)), fmaxf(fabsf(r.z), fabsf(r.w)));
-        const bool better = m > best_a || (m == best_a && (int)gi < best_base);
-        best_a = better ? m : best_a;
-        best_base = better ? (int)gi : best_base;
-        best_r = better ? r : best_r;
+  for (int s = threadIdx.x; s < d.T; s += blockDim.x) s_cnt[s] = live ? d.rcount[s] : 0;
+  block_prefix(s_cnt, s_pre, d.T);
+  const int n = s_pre[d.T];
+  for (int g = threadIdx.x; g < n; g += blockDim.x) {
+    const int s = find_tile(s_pre, d.T, g);
+    const clean_component cc = d.rcomps[(int64_t)s * d.cap_round + (g - s_pre[s])];
+    comps[1 + g] = make_int4(cc.y, cc.x, __float_as_int(cc.flux), 0);
+  }
+  if (threadIdx.x == 0) comps[0] = make_int4(n, 0, 0, 0);
+}
+
+// Column k: the components' x-axis DFT at k placed on their rows, forward FFT
+// along y, times the kernel spectrum, inverse FFT along y; rows 0 .. ny - 1
+// to Y[k][.].  Components of one row are summed in a fixed order (chunks of
+// 32 in list order, within a chunk by lane), so the result is deterministic.
+__global__ void __launch_bounds__(kFftMaxThreads, 1) fft_cols_kernel(FftAxis ay, int Lx, int ny, const int4* __restrict__ comps,
+                                const float2* __restrict__ twx, const float2* __restrict__ twy,
+                                const float2* __restrict__ Kspec, float2* __restrict__ Y) {
+  extern __shared__ float2 fbuf[];
+  __shared__ float2 s_c[32];
+  const int Ly = ay.L, k = blockIdx.x;
+  const int n = comps[0].x;
+  for (int i = threadIdx.x; i < Ly; i += blockDim.x) fbuf[fpad(i)] = make_float2(0.f, 0.f);
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    for (int base = 0; base < n; base += 32) {
+      const int j = base + lane;
+      const bool valid = j < n;
+      float2 c = make_float2(0.f, 0.f);
+      int y = -1;
+      if (valid) {
+        const int4 e = comps[1 + j];  // (y, x, flux bits, 0)
+        const float2 w = __ldg(&twx[(int)(((int64_t)k * e.y) % Lx)]);
+        const float f = __int_as_float(e.z);
+        c = make_float2(f * w.x, f * w.y);
+        y = e.x;
       }
-    if (best_a >= 0.f) {
-      const int k4 = fabsf(best_r.x) == best_a   ? 0
-                     : fabsf(best_r.y) == best_a ? 1
-                     : fabsf(best_r.z) == best_a ? 2
-                                                 : 3;
-      best_i = best_base + k4;
-      best_v = k4 == 0 ? best_r.x : k4 == 1 ? best_r.y : k4 == 2 ? best_r.z : best_r.w;
+      s_c[lane] = c;
+      const unsigned act = __ballot_sync(0xffffffffu, valid);
+      const unsigned grp = __match_any_sync(0xffffffffu, y);
+      __syncwarp();
+      if (valid && (__ffs(grp & act) - 1) == lane) {
+        float2 acc = fbuf[fpad(y)];
+        for (unsigned m = grp & act; m; m &= m - 1) acc = cadd(acc, s_c[__ffs(m) - 1]);
+        fbuf[fpad(y)] = acc;
+      }
+      __syncwarp();
     }
-  } else if (live) {
-    for (int y = ya; y < yb; ++y)
-      for (int x = rc.x0 + threadIdx.x; x < rc.x1; x += kFftThreads) {
-        const int64_t gi = (int64_t)y * d.nx + x;
-        const float r = R0[gi] - S[(int64_t)y * pitch + x];
-        d.R[gi] = r;
-        R0[gi] = r;
-        const float a = fabsf(r);
-        if (a > best_a || (a == best_a && (int)gi < best_i)) {
-          best_a = a;
-          best_i = (int)gi;
-          best_v = r;
+  }
+  __syncthreads();
+  fft_1d(fbuf, ay, twy, false);
+  const float2* kcol = Kspec + (int64_t)k * Ly;
+  for (int i = threadIdx.x; i < Ly; i += blockDim.x) fbuf[fpad(i)] = cmul(fbuf[fpad(i)], kcol[i]);
+  __syncthreads();
+  fft_1d(fbuf, ay, twy, true);
+  float2* ycol = Y + (int64_t)k * ny;
+  for (int q = threadIdx.x; q < ny; q += blockDim.x) ycol[q] = fbuf[fpad(q)];
+}
+
+// Rows q0 = 2b and q1 = 2b + 1: their x-axis spectra Y[.][q] extended to
+// length Lx and combined as Z = Y_q0 + i Y_q1; the inverse FFT gives row q0
+// in the real and row q1 in the imaginary part.  R <- R0 - S, R0 <- R on
+// columns 0 .. nx - 1; each tile's peak of these rows into the next-round
+// key; the last block closes the round.
+__global__ void __launch_bounds__(kFftMaxThreads, 1) fft_rows_kernel(PlanDev d, FftAxis ax, const float2* __restrict__ twx,
+                                const float2* __restrict__ Y, float* __restrict__ R0, int parity,
+                                int n_blocks) {
+  extern __shared__ float2 fbuf[];
+  const int Lx = ax.L;
+  int32_t* s_cnt = reinterpret_cast<int32_t*>(fbuf + fpad(Lx) + 1);
+  int32_t* s_pre = s_cnt + d.T;
+  __shared__ uint64_t s_warp[2][32];
+  const int q0 = 2 * blockIdx.x, q1 = q0 + 1;
+  const bool has1 = q1 < d.ny;
+  const bool live = *(volatile int32_t*)&d.st->status == 0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (live) {
+    for (int k = threadIdx.x; k <= Lx / 2; k += blockDim.x) {
+      float2 y0 = Y[(int64_t)k * d.ny + q0];
+      float2 y1 = has1 ? Y[(int64_t)k * d.ny + q1] : make_float2(0.f, 0.f);
+      const bool edge = k == 0 || 2 * k == Lx;  // real in exact arithmetic
+      if (edge) y0.y = y1.y = 0.f;
+      fbuf[fpad(k)] = make_float2(y0.x - y1.y, y0.y + y1.x);
+      if (!edge) fbuf[fpad(Lx - k)] = make_float2(y0.x + y1.y, y1.x - y0.y);
+    }
+    __syncthreads();
+    fft_1d(fbuf, ax, twx, true);
+    // tile rows of q0 and q1
+    int t_row0 = 0, t_row1 = 0;
+    for (int i = 0; i < d.ty; ++i) {
+      const Rect r = tile_rect(i * d.tx, d.ny, d.nx, d.ty, d.tx);
+      if (q0 >= r.y0 && q0 < r.y1) t_row0 = i;
+      if (has1 && q1 >= r.y0 && q1 < r.y1) t_row1 = i;
+    }
+    for (int j = 0; j < d.tx; ++j) {
+      const Rect rc = tile_rect(j, d.ny, d.nx, d.ty, d.tx);
+      float b0a = -1.f, b0v = 0.f, b1a = -1.f, b1v = 0.f;
+      int b0i = 0x7fffffff, b1i = 0x7fffffff;
+      for (int x = rc.x0 + threadIdx.x; x < rc.x1; x += blockDim.x) {
+        const float2 s = fbuf[fpad(x)];
+        const int64_t g0 = (int64_t)q0 * d.nx + x;
+        const float r0 = R0[g0] - s.x;
+        d.R[g0] = r0;
+        R0[g0] = r0;
+        const float a0 = fabsf(r0);
+        if (a0 > b0a || (a0 == b0a && (int)g0 < b0i)) {
+          b0a = a0;
+          b0i = (int)g0;
+          b0v = r0;
+        }
+        if (has1) {
+          const int64_t g1 = g0 + d.nx;
+          const float r1 = R0[g1] - s.y;
+          d.R[g1] = r1;
+          R0[g1] = r1;
+          const float a1 = fabsf(r1);
+          if (a1 > b1a || (a1 == b1a && (int)g1 < b1i)) {
+            b1a = a1;
+            b1i = (int)g1;
+            b1v = r1;
+          }
         }
       }
+      uint64_t k0 = b0a >= 0.f ? make_key(b0v, b0i) : 0ull;
+      uint64_t k1 = b1a >= 0.f ? make_key(b1v, b1i) : 0ull;
+      k0 = warp_max_key(k0);
+      k1 = warp_max_key(k1);
+      if (lane == 0) {
+        s_warp[0][warp] = k0;
+        s_warp[1][warp] = k1;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        uint64_t m0 = 0, m1 = 0;
+        for (int w = 0; w < nw; ++w) {
+          m0 = umax64(m0, s_warp[0][w]);
+          m1 = umax64(m1, s_warp[1][w]);
+        }
+        const int t0 = t_row0 * d.tx + j, t1 = t_row1 * d.tx + j;
+        if (has1 && t1 == t0) m0 = umax64(m0, m1), m1 = 0;
+        if (m0) atomicMax((unsigned long long*)&d.peak[(parity ^ 1) * d.T + t0], (unsigned long long)m0);
+        if (m1) atomicMax((unsigned long long*)&d.peak[(parity ^ 1) * d.T + t1], (unsigned long long)m1);
+      }
+      __syncthreads();
+    }
   }
-  uint64_t k = best_a >= 0.f ? make_key(best_v, best_i) : 0ull;
-  k = warp_max_key(k);
-  if ((threadIdx.x & 31) == 0) s_warp[threadIdx.x >> 5] = k;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    uint64_t m = 0;
-    for (int w = 0; w < kFftThreads / 32; ++w) m = umax64(m, s_warp[w]);
-    if (m) atomicMax((unsigned long long*)&d.peak[(parity ^ 1) * d.T + t], (unsigned long long)m);
-  }
-  close_round_if_last(d, parity, blocks_x * d.T, s_cnt, s_pre, A, pitch);
+  close_round_if_last(d, parity, n_blocks, s_cnt, s_pre);
 }
 
 }  // namespace
 
-cudaError_t fft_build_kernel_image(const PlanDev& d, int Ly, int Lx, float* Kimg,
+// Smallest even n >= m whose only prime factors are 2, 3, 5 and 7.
+int fft_grid_size(int m) {
+  for (int n = std::max(m, 2);; ++n) {
+    if (n & 1) continue;
+    int r = n;
+    for (int f : {2, 3, 5, 7})
+      while (r % f == 0) r /= f;
+    if (r == 1) return n;
+  }
+}
+
+bool fft_axis_init(FftAxis* a, int L) {
+  if (L < 2 || L > kFftMaxL || (L & 1)) return false;
+  FftAxis x{};
+  x.L = L;
+  int r = L;
+  for (int f : {8, 4, 2, 3, 5, 7})
+    while (r % f == 0) {
+      if (x.nrad == kFftMaxRadices) return false;
+      x.rad[x.nrad++] = f;
+      r /= f;
+    }
+  if (r != 1) return false;
+  // at most kFftValsPerThread values a thread in every stage
+  const int need = (L + kFftValsPerThread - 1) / kFftValsPerThread;
+  x.nthr = std::min(kFftMaxThreads, std::max(128, (need + 31) / 32 * 32));
+  *a = x;
+  return true;
+}
+
+size_t fft_smem_bytes(int L) { return sizeof(float2) * ((size_t)L + (size_t)L / 32 + 2); }
+
+cudaError_t fft_make_twiddles(float2* d_tw, int L, cudaStream_t s) {
+  std::vector<float2> h((size_t)L);
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int t = 0; t < L; ++t) {
+    const double a = two_pi * (double)t / (double)L;
+    h[(size_t)t] = make_float2((float)std::cos(a), (float)-std::sin(a));
+  }
+  cudaError_t e = cudaMemcpyAsync(d_tw, h.data(), sizeof(float2) * (size_t)L,
+                                  cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // h goes out of scope
+  return e;
+}
+
+cudaError_t fft_build_psf_spectrum(const PlanDev& d, const FftAxis& ay, const FftAxis& ax,
+                                   const float2* twy, const float2* twx, float2* Kspec,
                                    cudaStream_t s) {
-  fft_kernel_image<<<4096, 256, 0, s>>>(d.P, d.pny, d.pnx, d.cy, d.cx, d.ny, d.nx, Ly, Lx, Kimg);
+  fft_psf_rows_kernel<<<ay.L / 2, ax.nthr, fft_smem_bytes(ax.L), s>>>(d, ax, ay.L, twx, Kspec);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const float scale = (float)(1.0 / ((double)ay.L * (double)ax.L));
+  fft_psf_cols_kernel<<<ax.L / 2 + 1, ay.nthr, fft_smem_bytes(ay.L), s>>>(ay, twy, Kspec, scale);
   return cudaGetLastError();
 }
 
-cudaError_t fft_launch_scatter(const PlanDev& d, float* A, int64_t pitch, cudaStream_t s) {
-  fft_scatter<<<(d.T + 3) / 4, 128, 0, s>>>(d, A, pitch);  // a warp per tile
+cudaError_t fft_feedback_round(const PlanDev& d, const FftAxis& ay, const FftAxis& ax,
+                               const float2* twy, const float2* twx, const float2* Kspec,
+                               float2* Y, int4* comps, float* R0, int parity, cudaStream_t s) {
+  fft_comp_list_kernel<<<1, 256, sizeof(int32_t) * (2 * (size_t)d.T + 1), s>>>(d, comps);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  fft_cols_kernel<<<ax.L / 2 + 1, ay.nthr, fft_smem_bytes(ay.L), s>>>(ay, ax.L, d.ny, comps, twx,
+                                                                     twy, Kspec, Y);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int nb = (d.ny + 1) / 2;
+  const size_t smem = fft_smem_bytes(ax.L) + sizeof(int32_t) * (2 * (size_t)d.T + 1);
+  fft_rows_kernel<<<nb, ax.nthr, smem, s>>>(d, ax, twx, Y, R0, parity, nb);
   return cudaGetLastError();
 }
 
-cudaError_t fft_launch_multiply(void* X, const void* Kh, int64_t n, float scale,
-                                cudaStream_t s) {
-  fft_multiply<<<4096, 256, 0, s>>>(reinterpret_cast<float2*>(X),
-                                    reinterpret_cast<const float2*>(Kh), n, scale);
-  return cudaGetLastError();
+cudaError_t fft_prepare() {
+  cudaError_t e = allow_max_smem((const void*)fft_psf_rows_kernel);
+  if (e == cudaSuccess) e = allow_max_smem((const void*)fft_psf_cols_kernel);
+  if (e == cudaSuccess) e = allow_max_smem((const void*)fft_cols_kernel);
+  if (e == cudaSuccess) e = allow_max_smem((const void*)fft_rows_kernel);
+  return e;
 }
-
-cudaError_t fft_launch_subtract(const PlanDev& d, float* R0, const float* S, int64_t pitch,
-                                float* A, int parity, cudaStream_t s) {
-  int maxH = 0;
-  for (int i = 0; i < d.ty; ++i)
-    maxH = max(maxH, (int)(((int64_t)(i + 1) * d.ny) / d.ty - ((int64_t)i * d.ny) / d.ty));
-  const int bx = (maxH + kFftRows - 1) / kFftRows;
-  const size_t smem = sizeof(int32_t) * (2 * (size_t)d.T + 1);
-  fft_subtract<<<dim3(bx, d.T), kFftThreads, smem, s>>>(d, R0, S, pitch, A, parity, bx);
-  return cudaGetLastError();
-}
-
-cudaError_t fft_prepare() { return allow_max_smem((const void*)fft_subtract); }
 
 }  // namespace cleangb

@@ -25,13 +25,15 @@ from . import (COMPONENT_DTYPE, FB_FFT, FB_GATHER, CleanError, _check, _dptr, _s
 
 
 def _fft_size(m: int) -> int:
-    n = max(m, 1)
+    """The FFT feedback's grid length for 2 n - 1: the smallest even number
+    >= m whose prime factors are 2, 3, 5 and 7 (as the library picks it)."""
+    n = max(m, 2)
     while True:
         r = n
         for f in (2, 3, 5, 7):
             while r % f == 0:
                 r //= f
-        if r == 1:
+        if r == 1 and n % 2 == 0:
             return n
         n += 1
 
@@ -40,8 +42,8 @@ def footprint_bytes(n: int, psf_shape, niter: int, tiles=(1, 1), K: int = 0,
                     feedback_mode: int = FB_GATHER) -> int:
     """Device bytes a job holds while resident: residual and model images,
     its PSF (held by the caller but pinned for the job's lifetime), the
-    component list and the round buffer, and with FFT feedback the
-    convolution grids, spectra and round-start residual."""
+    component list and the round buffer, and with FFT feedback the kernel
+    spectrum, the transforms' work areas and the round-start residual."""
     T = tiles[0] * tiles[1]
     per_tile = niter // T + (1 if niter % T else 0)
     cap = min(K, per_tile) if K > 0 else per_tile
@@ -49,7 +51,10 @@ def footprint_bytes(n: int, psf_shape, niter: int, tiles=(1, 1), K: int = 0,
          + 8 * niter + 4096)
     if feedback_mode == FB_FFT and T > 1:
         L = _fft_size(2 * n - 1)
-        b += 2 * 4 * L * L + 2 * 8 * L * (L // 2 + 1) + 4 * n * n
+        # kernel spectrum, the round's column work area, the component list,
+        # twiddle tables and the round-start residual
+        b += 8 * L * (L // 2 + 1) + 8 * n * (L // 2 + 1) + 16 * (1 + T * max(cap, 1)) + 16 * L \
+            + 4 * n * n
     return int(b)
 
 

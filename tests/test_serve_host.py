@@ -9,8 +9,11 @@ from paper_2501_01461_gb300 import serve
 def test_fft_footprint_counts_the_grids():
     g = serve.footprint_bytes(1024, (2048, 2048), 10000, (2, 2), 50)
     f = serve.footprint_bytes(1024, (2048, 2048), 10000, (2, 2), 50, cg.FB_FFT)
-    L = 2048  # smallest 2-3-5-7-smooth size >= 2 * 1024 - 1
-    assert f - g == 2 * 4 * L * L + 2 * 8 * L * (L // 2 + 1) + 4 * 1024 * 1024
+    L = 2048  # smallest even 2-3-5-7-smooth size >= 2 * 1024 - 1
+    # kernel spectrum, the column work area (image rows only), the round's
+    # components (4 tiles x K 50), both twiddle tables, the round-start residual
+    assert f - g == (8 * L * (L // 2 + 1) + 8 * 1024 * (L // 2 + 1) + 16 * (1 + 4 * 50)
+                     + 16 * L + 4 * 1024 * 1024)
     assert serve.footprint_bytes(512, (1024, 1024), 100, (1, 1), 50, cg.FB_FFT) == \
         serve.footprint_bytes(512, (1024, 1024), 100, (1, 1), 50)
 
