@@ -768,9 +768,9 @@ int clean_plan(clean_plan_t* out, const clean_params* p, const float* d_psf, voi
   if (pl->fft) {
     req.push_back({(void**)&pl->fft_K, spec_bytes});
     req.push_back({(void**)&pl->fft_Y, sizeof(float2) * (size_t)(pl->Lx / 2 + 1) * p->ny});
-    req.push_back({(void**)&pl->fft_comps, sizeof(int4) * (size_t)(1 + cap_round * T)});
-    req.push_back({(void**)&pl->fft_twy, sizeof(float2) * (size_t)pl->Ly});
-    req.push_back({(void**)&pl->fft_twx, sizeof(float2) * (size_t)pl->Lx});
+    req.push_back({(void**)&pl->fft_comps, fft_comps_bytes(cap_round * T)});
+    req.push_back({(void**)&pl->fft_twy, sizeof(float2) * (size_t)pl->fft_ay.tw_len});
+    req.push_back({(void**)&pl->fft_twx, sizeof(float2) * (size_t)pl->fft_ax.tw_len});
     req.push_back({(void**)&pl->R0, sizeof(float) * (size_t)npix});
   }
   size_t total = 0;
@@ -814,8 +814,8 @@ int clean_plan(clean_plan_t* out, const clean_params* p, const float* d_psf, voi
   d.trigger = p->feedback_trigger;
   d.cap_round = (int32_t)cap_round;
 
-  if (pl->fft && (fft_make_twiddles(pl->fft_twy, pl->Ly, s) != cudaSuccess ||
-                  fft_make_twiddles(pl->fft_twx, pl->Lx, s) != cudaSuccess)) {
+  if (pl->fft && (fft_make_twiddles(pl->fft_twy, pl->fft_ay, s) != cudaSuccess ||
+                  fft_make_twiddles(pl->fft_twx, pl->fft_ax, s) != cudaSuccess)) {
     cudaGetLastError();
     clean_destroy(pl);
     return CLEAN_ERR_CUDA;

@@ -234,14 +234,21 @@ constexpr int kFftValsPerThread = 16;
 struct FftAxis {
   int32_t L, nthr, nrad;
   int32_t rad[kFftMaxRadices];
+  // twiddle table: entries [0, L) hold exp(-2 pi i t / L); stage s (radix R,
+  // Ns = product of the earlier radices) reads exp(-2 pi i r k / (Ns R)) at
+  // tw_off[s] + r Ns + k, so neighbouring lanes read neighbouring entries
+  int32_t tw_off[kFftMaxRadices];
+  int32_t tw_len;
 };
 // Smallest even n >= m whose prime factors are 2, 3, 5 and 7.
 int fft_grid_size(int m);
 // Fills *a for length L; false if L is odd, above kFftMaxL or not 7-smooth.
 bool fft_axis_init(FftAxis* a, int L);
-// Twiddle table exp(-2 pi i t / L), t < L, computed in double precision on
-// the host and copied to d_tw (L float2); synchronises s.
-cudaError_t fft_make_twiddles(float2* d_tw, int L, cudaStream_t s);
+// The twiddle table of an axis (a.tw_len float2, layout in FftAxis),
+// computed in double precision on the host and copied to d_tw; synchronises s.
+cudaError_t fft_make_twiddles(float2* d_tw, const FftAxis& a, cudaStream_t s);
+// Bytes of the per-round component work area for up to n_max components.
+size_t fft_comps_bytes(int64_t n_max);
 // Kernel spectrum Kspec[k][m] (k <= Lx / 2, m < Ly) of the PSF kernel image
 // K[d mod L] = P[d + c] (|d| < image size), scaled by 1 / (Ly Lx).
 cudaError_t fft_build_psf_spectrum(const PlanDev& d, const FftAxis& ay, const FftAxis& ax,
@@ -249,7 +256,7 @@ cudaError_t fft_build_psf_spectrum(const PlanDev& d, const FftAxis& ay, const Ff
                                    cudaStream_t s);
 // One FFT feedback: R <- R0 - (round components (*) PSF) on every pixel,
 // R0 <- R, next peaks, round close.  Y: (Lx/2 + 1) x ny float2 work area;
-// comps: 1 + T cap_round int4 work area.
+// comps: fft_comps_bytes(T cap_round) bytes of work area.
 cudaError_t fft_feedback_round(const PlanDev& d, const FftAxis& ay, const FftAxis& ax,
                                const float2* twy, const float2* twx, const float2* Kspec,
                                float2* Y, int4* comps, float* R0, int parity, cudaStream_t s);

@@ -30,6 +30,7 @@
 // registers, applies the stage twiddles, synchronises, and writes the small
 // DFT's outputs back to the autosorted positions.  Twiddles come from a
 // table exp(-2 pi i t / L) computed in double precision on the host.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -129,13 +130,13 @@ struct Dft {
 };
 
 // One Stockham stage of radix R over buf[0 .. L): sub-transforms of size Ns
-// become sub-transforms of size Ns R.  Every thread of the block calls it.
+// become sub-transforms of size Ns R.  tws: the stage's twiddles
+// exp(-2 pi i r k / (Ns R)) at r Ns + k.  Every thread of the block calls it.
 template <int R>
 __device__ __forceinline__ void fft_stage(float2* buf, int L, int Ns, const float2* __restrict__ tw,
-                                          bool inv) {
+                                          const float2* __restrict__ tws, bool inv) {
   constexpr int kMaxB = (kFftValsPerThread + R - 1) / R;
   const int nb = L / R;
-  const int step = L / (Ns * R);
   const int nthr = blockDim.x;
   float2 v[kMaxB][R];
 #pragma unroll
@@ -143,9 +144,10 @@ __device__ __forceinline__ void fft_stage(float2* buf, int L, int Ns, const floa
     const int j = threadIdx.x + b * nthr;
     if (j < nb) {
       const int k = j % Ns;
+      v[b][0] = buf[fpad(j)];
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        float2 w = __ldg(&tw[r * k * step]);
+      for (int r = 1; r < R; ++r) {
+        float2 w = __ldg(&tws[r * Ns + k]);
         if (inv) w.y = -w.y;
         v[b][r] = cmul(buf[fpad(j + r * nb)], w);
       }
@@ -173,13 +175,14 @@ __device__ void fft_1d(float2* buf, const FftAxis& ax, const float2* __restrict_
   int Ns = 1;
   for (int s = 0; s < ax.nrad; ++s) {
     const int R = ax.rad[s];
+    const float2* tws = tw + ax.tw_off[s];
     switch (R) {
-      case 8: fft_stage<8>(buf, ax.L, Ns, tw, inv); break;
-      case 4: fft_stage<4>(buf, ax.L, Ns, tw, inv); break;
-      case 2: fft_stage<2>(buf, ax.L, Ns, tw, inv); break;
-      case 3: fft_stage<3>(buf, ax.L, Ns, tw, inv); break;
-      case 5: fft_stage<5>(buf, ax.L, Ns, tw, inv); break;
-      default: fft_stage<7>(buf, ax.L, Ns, tw, inv); break;
+      case 8: fft_stage<8>(buf, ax.L, Ns, tw, tws, inv); break;
+      case 4: fft_stage<4>(buf, ax.L, Ns, tw, tws, inv); break;
+      case 2: fft_stage<2>(buf, ax.L, Ns, tw, tws, inv); break;
+      case 3: fft_stage<3>(buf, ax.L, Ns, tw, tws, inv); break;
+      case 5: fft_stage<5>(buf, ax.L, Ns, tw, tws, inv); break;
+      default: fft_stage<7>(buf, ax.L, Ns, tw, tws, inv); break;
     }
     Ns *= R;
   }
@@ -239,62 +242,80 @@ __global__ void __launch_bounds__(kFftMaxThreads, 1) fft_psf_cols_kernel(FftAxis
 // ---- one round ----------------------------------------------------------------
 
 // The round's components of every tile in list order (tile, then iteration)
-// as (y, x, flux bits, 0) from comps[1]; comps[0].x = their number (0 when
-// the plan's status is bad).  One block.
-__global__ void fft_comp_list_kernel(PlanDev d, int4* __restrict__ comps) {
+// as comps[1 + g] = (y, x, flux bits, next), where next is the list index of
+// the next component on the same image row (-1: none); comps[0] = (n, number
+// of rows with components); lead[0 .. rows) the first component of each such
+// row (in no particular order).  One block; a row's chain is found by
+// scanning the list, which is short (a round's components).
+constexpr int kCompThreads = 1024;
+constexpr int kCompSmem = 8192;  // components whose rows are kept in shared memory
+__global__ void __launch_bounds__(kCompThreads)
+    fft_comp_list_kernel(PlanDev d, int4* __restrict__ comps, int* __restrict__ lead) {
   extern __shared__ int32_t s_int[];
   int32_t* s_cnt = s_int;
   int32_t* s_pre = s_int + d.T;
+  int32_t* s_y = s_int + 2 * d.T + 1;  // the components' rows, when they fit
+  __shared__ int s_rows;
   const bool live = *(volatile int32_t*)&d.st->status == 0;
   for (int s = threadIdx.x; s < d.T; s += blockDim.x) s_cnt[s] = live ? d.rcount[s] : 0;
+  if (threadIdx.x == 0) s_rows = 0;
   block_prefix(s_cnt, s_pre, d.T);
   const int n = s_pre[d.T];
+  const bool in_smem = n <= kCompSmem;
   for (int g = threadIdx.x; g < n; g += blockDim.x) {
     const int s = find_tile(s_pre, d.T, g);
     const clean_component cc = d.rcomps[(int64_t)s * d.cap_round + (g - s_pre[s])];
-    comps[1 + g] = make_int4(cc.y, cc.x, __float_as_int(cc.flux), 0);
+    comps[1 + g] = make_int4(cc.y, cc.x, __float_as_int(cc.flux), -1);
+    if (in_smem) s_y[g] = cc.y;
   }
-  if (threadIdx.x == 0) comps[0] = make_int4(n, 0, 0, 0);
+  __syncthreads();
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const int y = in_smem ? s_y[j] : comps[1 + j].x;
+    bool first = true;
+    int next = -1;
+    for (int i = 0; i < n; ++i) {
+      const int yi = in_smem ? s_y[i] : comps[1 + i].x;
+      if (yi != y || i == j) continue;
+      if (i < j) {
+        first = false;
+      } else {
+        next = i;
+        break;
+      }
+    }
+    comps[1 + j].w = next;
+    if (first) lead[atomicAdd(&s_rows, 1)] = j;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) comps[0] = make_int4(n, s_rows, 0, 0);
 }
 
 // Column k: the components' x-axis DFT at k placed on their rows, forward FFT
 // along y, times the kernel spectrum, inverse FFT along y; rows 0 .. ny - 1
-// to Y[k][.].  Components of one row are summed in a fixed order (chunks of
-// 32 in list order, within a chunk by lane), so the result is deterministic.
-__global__ void __launch_bounds__(kFftMaxThreads, 1) fft_cols_kernel(FftAxis ay, int Lx, int ny, const int4* __restrict__ comps,
-                                const float2* __restrict__ twx, const float2* __restrict__ twy,
-                                const float2* __restrict__ Kspec, float2* __restrict__ Y) {
+// to Y[k][.].  The components of one row are summed in list order (their
+// chain), so the result is deterministic.
+__global__ void __launch_bounds__(kFftMaxThreads, 1)
+    fft_cols_kernel(FftAxis ay, int Lx, int ny, const int4* __restrict__ comps,
+                    const int* __restrict__ lead, const float2* __restrict__ twx,
+                    const float2* __restrict__ twy, const float2* __restrict__ Kspec,
+                    float2* __restrict__ Y) {
   extern __shared__ float2 fbuf[];
-  __shared__ float2 s_c[32];
   const int Ly = ay.L, k = blockIdx.x;
-  const int n = comps[0].x;
+  const int rows = comps[0].y;
   for (int i = threadIdx.x; i < Ly; i += blockDim.x) fbuf[fpad(i)] = make_float2(0.f, 0.f);
   __syncthreads();
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-    for (int base = 0; base < n; base += 32) {
-      const int j = base + lane;
-      const bool valid = j < n;
-      float2 c = make_float2(0.f, 0.f);
-      int y = -1;
-      if (valid) {
-        const int4 e = comps[1 + j];  // (y, x, flux bits, 0)
-        const float2 w = __ldg(&twx[(int)(((int64_t)k * e.y) % Lx)]);
-        const float f = __int_as_float(e.z);
-        c = make_float2(f * w.x, f * w.y);
-        y = e.x;
-      }
-      s_c[lane] = c;
-      const unsigned act = __ballot_sync(0xffffffffu, valid);
-      const unsigned grp = __match_any_sync(0xffffffffu, y);
-      __syncwarp();
-      if (valid && (__ffs(grp & act) - 1) == lane) {
-        float2 acc = fbuf[fpad(y)];
-        for (unsigned m = grp & act; m; m &= m - 1) acc = cadd(acc, s_c[__ffs(m) - 1]);
-        fbuf[fpad(y)] = acc;
-      }
-      __syncwarp();
+  for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+    int j = lead[i];
+    const int y = comps[1 + j].x;
+    float2 acc = make_float2(0.f, 0.f);
+    while (j >= 0) {
+      const int4 e = comps[1 + j];  // (y, x, flux bits, next)
+      const float2 w = __ldg(&twx[(int)(((int64_t)k * e.y) % Lx)]);
+      const float f = __int_as_float(e.z);
+      acc = cadd(acc, make_float2(f * w.x, f * w.y));
+      j = e.w;
     }
+    fbuf[fpad(y)] = acc;
   }
   __syncthreads();
   fft_1d(fbuf, ay, twy, false);
@@ -421,6 +442,13 @@ bool fft_axis_init(FftAxis* a, int L) {
       r /= f;
     }
   if (r != 1) return false;
+  int off = L, Ns = 1;
+  for (int st = 0; st < x.nrad; ++st) {
+    x.tw_off[st] = off;
+    off += x.rad[st] * Ns;
+    Ns *= x.rad[st];
+  }
+  x.tw_len = off;
   // at most kFftValsPerThread values a thread in every stage
   const int need = (L + kFftValsPerThread - 1) / kFftValsPerThread;
   x.nthr = std::min(kFftMaxThreads, std::max(128, (need + 31) / 32 * 32));
@@ -428,16 +456,29 @@ bool fft_axis_init(FftAxis* a, int L) {
   return true;
 }
 
+size_t fft_comps_bytes(int64_t n_max) {
+  return sizeof(int4) * (size_t)(1 + n_max) + sizeof(int) * (size_t)n_max;
+}
+
 size_t fft_smem_bytes(int L) { return sizeof(float2) * ((size_t)L + (size_t)L / 32 + 2); }
 
-cudaError_t fft_make_twiddles(float2* d_tw, int L, cudaStream_t s) {
-  std::vector<float2> h((size_t)L);
+cudaError_t fft_make_twiddles(float2* d_tw, const FftAxis& a, cudaStream_t s) {
+  std::vector<float2> h((size_t)a.tw_len);
   const double two_pi = 6.283185307179586476925286766559;
-  for (int t = 0; t < L; ++t) {
-    const double a = two_pi * (double)t / (double)L;
-    h[(size_t)t] = make_float2((float)std::cos(a), (float)-std::sin(a));
+  auto root = [&](int64_t t, int64_t n) {  // exp(-2 pi i t / n)
+    const double ang = two_pi * (double)t / (double)n;
+    return make_float2((float)std::cos(ang), (float)-std::sin(ang));
+  };
+  for (int t = 0; t < a.L; ++t) h[(size_t)t] = root(t, a.L);
+  int Ns = 1;
+  for (int st = 0; st < a.nrad; ++st) {
+    const int R = a.rad[st];
+    for (int r = 0; r < R; ++r)
+      for (int k = 0; k < Ns; ++k)
+        h[(size_t)a.tw_off[st] + (size_t)r * Ns + k] = root((int64_t)r * k, (int64_t)Ns * R);
+    Ns *= R;
   }
-  cudaError_t e = cudaMemcpyAsync(d_tw, h.data(), sizeof(float2) * (size_t)L,
+  cudaError_t e = cudaMemcpyAsync(d_tw, h.data(), sizeof(float2) * (size_t)a.tw_len,
                                   cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // h goes out of scope
   return e;
@@ -457,11 +498,15 @@ cudaError_t fft_build_psf_spectrum(const PlanDev& d, const FftAxis& ay, const Ff
 cudaError_t fft_feedback_round(const PlanDev& d, const FftAxis& ay, const FftAxis& ax,
                                const float2* twy, const float2* twx, const float2* Kspec,
                                float2* Y, int4* comps, float* R0, int parity, cudaStream_t s) {
-  fft_comp_list_kernel<<<1, 256, sizeof(int32_t) * (2 * (size_t)d.T + 1), s>>>(d, comps);
+  const int64_t n_max = (int64_t)d.T * d.cap_round;
+  int* lead = reinterpret_cast<int*>(comps + 1 + n_max);
+  const size_t csmem = sizeof(int32_t) * (2 * (size_t)d.T + 1 +
+                                          (size_t)std::min<int64_t>(n_max, kCompSmem));
+  fft_comp_list_kernel<<<1, kCompThreads, csmem, s>>>(d, comps, lead);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  fft_cols_kernel<<<ax.L / 2 + 1, ay.nthr, fft_smem_bytes(ay.L), s>>>(ay, ax.L, d.ny, comps, twx,
-                                                                     twy, Kspec, Y);
+  fft_cols_kernel<<<ax.L / 2 + 1, ay.nthr, fft_smem_bytes(ay.L), s>>>(ay, ax.L, d.ny, comps, lead,
+                                                                     twx, twy, Kspec, Y);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int nb = (d.ny + 1) / 2;
@@ -474,6 +519,7 @@ cudaError_t fft_prepare() {
   cudaError_t e = allow_max_smem((const void*)fft_psf_rows_kernel);
   if (e == cudaSuccess) e = allow_max_smem((const void*)fft_psf_cols_kernel);
   if (e == cudaSuccess) e = allow_max_smem((const void*)fft_cols_kernel);
+  if (e == cudaSuccess) e = allow_max_smem((const void*)fft_comp_list_kernel);
   if (e == cudaSuccess) e = allow_max_smem((const void*)fft_rows_kernel);
   return e;
 }

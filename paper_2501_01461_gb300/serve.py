@@ -38,6 +38,17 @@ def _fft_size(m: int) -> int:
         n += 1
 
 
+def _twiddles(L: int) -> int:
+    """Entries of an FFT axis's twiddle table (L, plus r Ns per stage)."""
+    out, ns = L, 1
+    for f in (8, 4, 2, 3, 5, 7):
+        while L % f == 0:
+            out += f * ns
+            ns *= f
+            L //= f
+    return out
+
+
 def footprint_bytes(n: int, psf_shape, niter: int, tiles=(1, 1), K: int = 0,
                     feedback_mode: int = FB_GATHER) -> int:
     """Device bytes a job holds while resident: residual and model images,
@@ -53,8 +64,8 @@ def footprint_bytes(n: int, psf_shape, niter: int, tiles=(1, 1), K: int = 0,
         L = _fft_size(2 * n - 1)
         # kernel spectrum, the round's column work area, the component list,
         # twiddle tables and the round-start residual
-        b += 8 * L * (L // 2 + 1) + 8 * n * (L // 2 + 1) + 16 * (1 + T * max(cap, 1)) + 16 * L \
-            + 4 * n * n
+        b += 8 * L * (L // 2 + 1) + 8 * n * (L // 2 + 1) + 20 * T * max(cap, 1) + 16 \
+            + 2 * 8 * _twiddles(L) + 4 * n * n
     return int(b)
 
 
