@@ -35,6 +35,7 @@
 #include <vector>
 
 #include "cleangb_internal.cuh"
+#include "ptx.cuh"
 #include "round_close.cuh"
 
 namespace cleangb {
@@ -42,6 +43,29 @@ namespace cleangb {
 namespace {
 
 __device__ __forceinline__ int fpad(int i) { return i + (i >> 5); }  // shared-memory padding
+
+constexpr uint64_t kFftWaitNs = 2000000000ull;  // bound of every bulk-copy wait
+
+// 1-D bulk copy of `bytes` (a multiple of 16; both addresses 16-byte
+// aligned) from global to shared memory, completion on `bar`.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes,
+                                          uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(ptx::smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(ptx::smem_u32(bar))
+      : "memory");
+}
+
+int fft_sm_count() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return std::max(n, 1);
+}
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -271,16 +295,24 @@ __global__ void __launch_bounds__(kCompThreads)
   __syncthreads();
   for (int j = threadIdx.x; j < n; j += blockDim.x) {
     const int y = in_smem ? s_y[j] : comps[1 + j].x;
+    // first: no earlier component on row y; next: the first later one
     bool first = true;
     int next = -1;
-    for (int i = 0; i < n; ++i) {
-      const int yi = in_smem ? s_y[i] : comps[1 + i].x;
-      if (yi != y || i == j) continue;
-      if (i < j) {
-        first = false;
-      } else {
-        next = i;
-        break;
+    constexpr int kScan = 8;
+    for (int i0 = 0; i0 < n && next < 0; i0 += kScan) {
+      int yi[kScan];
+#pragma unroll
+      for (int u = 0; u < kScan; ++u) {
+        const int i = i0 + u;
+        yi[u] = i < n ? (in_smem ? s_y[i] : comps[1 + i].x) : -1;
+      }
+#pragma unroll
+      for (int u = 0; u < kScan; ++u) {
+        const int i = i0 + u;
+        if (yi[u] == y && i != j) {
+          if (i < j) first = false;
+          else if (next < 0) next = i;
+        }
       }
     }
     comps[1 + j].w = next;
@@ -290,71 +322,167 @@ __global__ void __launch_bounds__(kCompThreads)
   if (threadIdx.x == 0) comps[0] = make_int4(n, s_rows, 0, 0);
 }
 
-// Column k: the components' x-axis DFT at k placed on their rows, forward FFT
-// along y, times the kernel spectrum, inverse FFT along y; rows 0 .. ny - 1
-// to Y[k][.].  The components of one row are summed in list order (their
-// chain), so the result is deterministic.
+// Columns k = blockIdx.x, blockIdx.x + gridDim.x, ... (one CTA per SM):
+// the components' x-axis DFT at k placed on their rows, forward FFT along y,
+// times the kernel spectrum, inverse FFT along y; rows 0 .. ny - 1 to
+// Y[k][.].  The components of one row are summed in list order (their
+// chain), so the result is deterministic.  The kernel spectrum's column
+// arrives by one bulk copy into shared memory, issued a column ahead, so
+// its load overlaps the previous column's transforms.
 __global__ void __launch_bounds__(kFftMaxThreads, 1)
-    fft_cols_kernel(FftAxis ay, int Lx, int ny, const int4* __restrict__ comps,
+    fft_cols_kernel(PlanDev d, FftAxis ay, int Lx, const int4* __restrict__ comps,
                     const int* __restrict__ lead, const float2* __restrict__ twx,
                     const float2* __restrict__ twy, const float2* __restrict__ Kspec,
-                    float2* __restrict__ Y) {
-  extern __shared__ float2 fbuf[];
-  const int Ly = ay.L, k = blockIdx.x;
+                    float2* __restrict__ Y, uint64_t limit_ns) {
+  extern __shared__ __align__(128) unsigned char fsm[];
+  const int Ly = ay.L, ny = d.ny, ncols = Lx / 2 + 1;
+  float2* kst = reinterpret_cast<float2*>(fsm);  // the spectrum column, Ly
+  float2* fbuf = kst + Ly;                        // the transform, padded
+  __shared__ __align__(8) uint64_t kbar;
+  __shared__ int s_abort;
+  const uint32_t kbytes = (uint32_t)Ly * (uint32_t)sizeof(float2);
   const int rows = comps[0].y;
-  for (int i = threadIdx.x; i < Ly; i += blockDim.x) fbuf[fpad(i)] = make_float2(0.f, 0.f);
-  __syncthreads();
-  for (int i = threadIdx.x; i < rows; i += blockDim.x) {
-    int j = lead[i];
-    const int y = comps[1 + j].x;
-    float2 acc = make_float2(0.f, 0.f);
-    while (j >= 0) {
-      const int4 e = comps[1 + j];  // (y, x, flux bits, next)
-      const float2 w = __ldg(&twx[(int)(((int64_t)k * e.y) % Lx)]);
-      const float f = __int_as_float(e.z);
-      acc = cadd(acc, make_float2(f * w.x, f * w.y));
-      j = e.w;
+  if (threadIdx.x == 0) {
+    s_abort = *(volatile int32_t*)&d.st->status != 0;
+    ptx::mbar_init(&kbar, 1);
+    ptx::fence_barrier_init();
+    if (!s_abort && blockIdx.x < ncols) {
+      ptx::mbar_arrive_expect_tx(&kbar, kbytes);
+      bulk_load(kst, Kspec + (int64_t)blockIdx.x * Ly, kbytes, &kbar);
     }
-    fbuf[fpad(y)] = acc;
   }
   __syncthreads();
-  fft_1d(fbuf, ay, twy, false);
-  const float2* kcol = Kspec + (int64_t)k * Ly;
-  for (int i = threadIdx.x; i < Ly; i += blockDim.x) fbuf[fpad(i)] = cmul(fbuf[fpad(i)], kcol[i]);
-  __syncthreads();
-  fft_1d(fbuf, ay, twy, true);
-  float2* ycol = Y + (int64_t)k * ny;
-  for (int q = threadIdx.x; q < ny; q += blockDim.x) ycol[q] = fbuf[fpad(q)];
+  if (s_abort) return;  // uniform: written before the barrier
+  uint32_t phase = 0;
+  for (int k = blockIdx.x; k < ncols; k += gridDim.x) {
+#pragma unroll
+    for (int u = 0; u < kFftValsPerThread; ++u) {
+      const int i = threadIdx.x + u * blockDim.x;
+      if (i < Ly) fbuf[fpad(i)] = make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+      int j = lead[i];
+      const int y = comps[1 + j].x;
+      float2 acc = make_float2(0.f, 0.f);
+      while (j >= 0) {
+        const int4 e = comps[1 + j];  // (y, x, flux bits, next)
+        const float2 w = __ldg(&twx[(int)(((int64_t)k * e.y) % Lx)]);
+        const float f = __int_as_float(e.z);
+        acc = cadd(acc, make_float2(f * w.x, f * w.y));
+        j = e.w;
+      }
+      fbuf[fpad(y)] = acc;
+    }
+    __syncthreads();
+    fft_1d(fbuf, ay, twy, false);
+    // the spectrum column: every thread waits (bounded) for the bulk copy
+    if (!ptx::mbar_wait_bounded(&kbar, phase, limit_ns)) {
+      atomicOr(&d.st->status, ST_TIMEOUT);
+      s_abort = 1;
+    }
+    phase ^= 1u;
+    __syncthreads();
+    if (s_abort) return;
+#pragma unroll
+    for (int u = 0; u < kFftValsPerThread; ++u) {
+      const int i = threadIdx.x + u * blockDim.x;
+      if (i < Ly) fbuf[fpad(i)] = cmul(fbuf[fpad(i)], kst[i]);
+    }
+    __syncthreads();
+    // the staging buffer is free: fetch the next column's spectrum
+    if (threadIdx.x == 0 && k + (int)gridDim.x < ncols) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      ptx::mbar_arrive_expect_tx(&kbar, kbytes);
+      bulk_load(kst, Kspec + (int64_t)(k + gridDim.x) * Ly, kbytes, &kbar);
+    }
+    fft_1d(fbuf, ay, twy, true);
+    float2* ycol = Y + (int64_t)k * ny;
+#pragma unroll
+    for (int u = 0; u < kFftValsPerThread; ++u) {
+      const int q = threadIdx.x + u * blockDim.x;
+      if (q < ny) ycol[q] = fbuf[fpad(q)];
+    }
+    __syncthreads();
+  }
 }
 
 // Rows q0 = 2b and q1 = 2b + 1: their x-axis spectra Y[.][q] extended to
 // length Lx and combined as Z = Y_q0 + i Y_q1; the inverse FFT gives row q0
 // in the real and row q1 in the imaginary part.  R <- R0 - S, R0 <- R on
 // columns 0 .. nx - 1; each tile's peak of these rows into the next-round
-// key; the last block closes the round.
-__global__ void __launch_bounds__(kFftMaxThreads, 1) fft_rows_kernel(PlanDev d, FftAxis ax, const float2* __restrict__ twx,
-                                const float2* __restrict__ Y, float* __restrict__ R0, int parity,
-                                int n_blocks) {
-  extern __shared__ float2 fbuf[];
+// key; the last block closes the round.  Every thread issues all of its
+// global loads before it uses any (at most kFftValsPerThread / 2 spectrum
+// bins and image columns a thread).
+__global__ void __launch_bounds__(kFftMaxThreads, 1)
+    fft_rows_kernel(PlanDev d, FftAxis ax, const float2* __restrict__ twx,
+                    const float2* __restrict__ Y, float* __restrict__ R0, int parity,
+                    int n_blocks) {
+  extern __shared__ __align__(128) unsigned char fsm[];
+  float2* fbuf = reinterpret_cast<float2*>(fsm);
   const int Lx = ax.L;
   int32_t* s_cnt = reinterpret_cast<int32_t*>(fbuf + fpad(Lx) + 1);
   int32_t* s_pre = s_cnt + d.T;
   __shared__ uint64_t s_warp[2][32];
+  constexpr int kHalf = kFftValsPerThread / 2;  // Lx / 2 + 1 <= kHalf * blockDim.x + 1
   const int q0 = 2 * blockIdx.x, q1 = q0 + 1;
   const bool has1 = q1 < d.ny;
   const bool live = *(volatile int32_t*)&d.st->status == 0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int nthr = blockDim.x;
   if (live) {
-    for (int k = threadIdx.x; k <= Lx / 2; k += blockDim.x) {
-      float2 y0 = Y[(int64_t)k * d.ny + q0];
-      float2 y1 = has1 ? Y[(int64_t)k * d.ny + q1] : make_float2(0.f, 0.f);
-      const bool edge = k == 0 || 2 * k == Lx;  // real in exact arithmetic
-      if (edge) y0.y = y1.y = 0.f;
-      fbuf[fpad(k)] = make_float2(y0.x - y1.y, y0.y + y1.x);
-      if (!edge) fbuf[fpad(Lx - k)] = make_float2(y0.x + y1.y, y1.x - y0.y);
+    float2 y0[kHalf + 1], y1[kHalf + 1];
+#pragma unroll
+    for (int u = 0; u <= kHalf; ++u) {
+      const int k = threadIdx.x + u * nthr;
+      y0[u] = y1[u] = make_float2(0.f, 0.f);
+      if (k <= Lx / 2) {
+        y0[u] = Y[(int64_t)k * d.ny + q0];
+        if (has1) y1[u] = Y[(int64_t)k * d.ny + q1];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u <= kHalf; ++u) {
+      const int k = threadIdx.x + u * nthr;
+      if (k <= Lx / 2) {
+        float2 a = y0[u], b = y1[u];
+        const bool edge = k == 0 || 2 * k == Lx;  // real in exact arithmetic
+        if (edge) a.y = b.y = 0.f;
+        fbuf[fpad(k)] = make_float2(a.x - b.y, a.y + b.x);
+        if (!edge) fbuf[fpad(Lx - k)] = make_float2(a.x + b.y, b.x - a.y);
+      }
     }
     __syncthreads();
     fft_1d(fbuf, ax, twx, true);
+    // R <- R0 - S for this thread's columns (all loads first), results back
+    // into fbuf as (row q0, row q1) for the per-tile peak scans
+    float r0v[kHalf], r1v[kHalf];
+    const int64_t g0 = (int64_t)q0 * d.nx;
+#pragma unroll
+    for (int u = 0; u < kHalf; ++u) {
+      const int x = threadIdx.x + u * nthr;
+      r0v[u] = r1v[u] = 0.f;
+      if (x < d.nx) {
+        r0v[u] = R0[g0 + x];
+        if (has1) r1v[u] = R0[g0 + d.nx + x];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kHalf; ++u) {
+      const int x = threadIdx.x + u * nthr;
+      if (x < d.nx) {
+        const float2 sv = fbuf[fpad(x)];
+        const float a = r0v[u] - sv.x, b = r1v[u] - sv.y;
+        d.R[g0 + x] = a;
+        R0[g0 + x] = a;
+        if (has1) {
+          d.R[g0 + d.nx + x] = b;
+          R0[g0 + d.nx + x] = b;
+        }
+        fbuf[fpad(x)] = make_float2(a, b);
+      }
+    }
+    __syncthreads();
     // tile rows of q0 and q1
     int t_row0 = 0, t_row1 = 0;
     for (int i = 0; i < d.ty; ++i) {
@@ -366,28 +494,22 @@ __global__ void __launch_bounds__(kFftMaxThreads, 1) fft_rows_kernel(PlanDev d, 
       const Rect rc = tile_rect(j, d.ny, d.nx, d.ty, d.tx);
       float b0a = -1.f, b0v = 0.f, b1a = -1.f, b1v = 0.f;
       int b0i = 0x7fffffff, b1i = 0x7fffffff;
-      for (int x = rc.x0 + threadIdx.x; x < rc.x1; x += blockDim.x) {
-        const float2 s = fbuf[fpad(x)];
-        const int64_t g0 = (int64_t)q0 * d.nx + x;
-        const float r0 = R0[g0] - s.x;
-        d.R[g0] = r0;
-        R0[g0] = r0;
-        const float a0 = fabsf(r0);
-        if (a0 > b0a || (a0 == b0a && (int)g0 < b0i)) {
+      for (int x = rc.x0 + threadIdx.x; x < rc.x1; x += nthr) {
+        const float2 v = fbuf[fpad(x)];
+        const int i0 = (int)g0 + x;
+        const float a0 = fabsf(v.x);
+        if (a0 > b0a || (a0 == b0a && i0 < b0i)) {
           b0a = a0;
-          b0i = (int)g0;
-          b0v = r0;
+          b0i = i0;
+          b0v = v.x;
         }
         if (has1) {
-          const int64_t g1 = g0 + d.nx;
-          const float r1 = R0[g1] - s.y;
-          d.R[g1] = r1;
-          R0[g1] = r1;
-          const float a1 = fabsf(r1);
-          if (a1 > b1a || (a1 == b1a && (int)g1 < b1i)) {
+          const int i1 = i0 + d.nx;
+          const float a1 = fabsf(v.y);
+          if (a1 > b1a || (a1 == b1a && i1 < b1i)) {
             b1a = a1;
-            b1i = (int)g1;
-            b1v = r1;
+            b1i = i1;
+            b1v = v.y;
           }
         }
       }
@@ -505,8 +627,11 @@ cudaError_t fft_feedback_round(const PlanDev& d, const FftAxis& ay, const FftAxi
   fft_comp_list_kernel<<<1, kCompThreads, csmem, s>>>(d, comps, lead);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  fft_cols_kernel<<<ax.L / 2 + 1, ay.nthr, fft_smem_bytes(ay.L), s>>>(ay, ax.L, d.ny, comps, lead,
-                                                                     twx, twy, Kspec, Y);
+  const int ncols = ax.L / 2 + 1;
+  const int grid = std::min(ncols, fft_sm_count());
+  const size_t cs = sizeof(float2) * (size_t)ay.L + fft_smem_bytes(ay.L);
+  fft_cols_kernel<<<grid, ay.nthr, cs, s>>>(d, ay, ax.L, comps, lead, twx, twy, Kspec, Y,
+                                            kFftWaitNs);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int nb = (d.ny + 1) / 2;
