@@ -239,6 +239,7 @@ struct FftAxis {
   // tw_off[s] + r Ns + k, so neighbouring lanes read neighbouring entries
   int32_t tw_off[kFftMaxRadices];
   int32_t tw_len;
+  int32_t p2;  // 1: L is 2048, 4096 or 8192 and takes the radix-16 path (L / 16 threads)
 };
 // Smallest even n >= m whose prime factors are 2, 3, 5 and 7.
 int fft_grid_size(int m);

@@ -192,10 +192,149 @@ __device__ __forceinline__ void fft_stage(float2* buf, int L, int Ns, const floa
   __syncthreads();
 }
 
+// ---- power-of-two lengths 2048 .. 8192: radix-16 stages, L / 16 threads --------
+// Each thread holds one 16-point butterfly per stage in registers; all index
+// arithmetic is compile-time.  A stage's twiddles w^r (w = e^(-2 pi i k /
+// (16 Ns))) are built from w, w^2, w^4, w^8 read from the table (at most three
+// products deep).
+
+// w16^p, p = 0 .. 15 (forward e^(-2 pi i p / 16))
+__device__ __forceinline__ float2 w16(int p, bool inv) {
+  const float C = 0.92387953251128674f, S = 0.38268343236508977f, H = 0.70710678118654752f;
+  float2 w;
+  switch (p & 15) {
+    case 0: w = make_float2(1.f, 0.f); break;
+    case 1: w = make_float2(C, -S); break;
+    case 2: w = make_float2(H, -H); break;
+    case 3: w = make_float2(S, -C); break;
+    case 4: w = make_float2(0.f, -1.f); break;
+    case 5: w = make_float2(-S, -C); break;
+    case 6: w = make_float2(-H, -H); break;
+    case 7: w = make_float2(-C, -S); break;
+    case 8: w = make_float2(-1.f, 0.f); break;
+    case 9: w = make_float2(-C, S); break;
+    case 10: w = make_float2(-H, H); break;
+    case 11: w = make_float2(-S, C); break;
+    case 12: w = make_float2(0.f, 1.f); break;
+    case 13: w = make_float2(S, C); break;
+    case 14: w = make_float2(H, H); break;
+    default: w = make_float2(C, S); break;
+  }
+  if (inv) w.y = -w.y;
+  return w;
+}
+
+// X[m + 4q] = sum_t x[t] w16^(t (m + 4q)): DFT-4s over t = r + 4s for each r,
+// twiddles w16^(r m), DFT-4s over r.
+__device__ __forceinline__ void dft16(float2 (&x)[16], bool inv) {
+  float2 b[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    float2 t[4] = {x[r], x[r + 4], x[r + 8], x[r + 12]};
+    Dft<4>::run(t, inv, nullptr, 0);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) b[r][m] = (r == 0 || m == 0) ? t[m] : cmul(t[m], w16(r * m, inv));
+  }
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    float2 t[4] = {b[0][m], b[1][m], b[2][m], b[3][m]};
+    Dft<4>::run(t, inv, nullptr, 0);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) x[m + 4 * q] = t[q];
+  }
+}
+
+template <int L, int NS>
+__device__ __forceinline__ void p2_stage16(float2* buf, const float2* __restrict__ tws, bool inv) {
+  constexpr int NB = L / 16;  // one butterfly a thread
+  const int j = threadIdx.x;
+  const int k = j & (NS - 1);
+  float2 x[16];
+#pragma unroll
+  for (int r = 0; r < 16; ++r) x[r] = buf[fpad(j + r * NB)];
+  if (NS > 1) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(tws) + 2 * k);
+    const float4 c = __ldg(reinterpret_cast<const float4*>(tws) + 2 * k + 1);
+    const float sg = inv ? -1.f : 1.f;
+    float2 w[16];
+    w[1] = make_float2(a.x, sg * a.y);
+    w[2] = make_float2(a.z, sg * a.w);
+    w[4] = make_float2(c.x, sg * c.y);
+    w[8] = make_float2(c.z, sg * c.w);
+    w[3] = cmul(w[1], w[2]);
+    w[5] = cmul(w[1], w[4]);
+    w[6] = cmul(w[2], w[4]);
+    w[7] = cmul(w[3], w[4]);
+#pragma unroll
+    for (int r = 9; r < 16; ++r) w[r] = cmul(w[r - 8], w[8]);
+#pragma unroll
+    for (int r = 1; r < 16; ++r) x[r] = cmul(x[r], w[r]);
+  }
+  __syncthreads();
+  dft16(x, inv);
+  const int base = (j - k) * 16 + k;
+#pragma unroll
+  for (int r = 0; r < 16; ++r) buf[fpad(base + r * NS)] = x[r];
+  __syncthreads();
+}
+
+// Last stage of radix R = L / NS < 16: 16 / R butterflies a thread; twiddles
+// exp(-2 pi i r k / L) at r NS + k.
+template <int L, int NS>
+__device__ __forceinline__ void p2_tail(float2* buf, const float2* __restrict__ tws, bool inv) {
+  constexpr int R = L / NS, NB = L / R, NT = L / 16, MB = 16 / R;
+  float2 v[MB][R];
+#pragma unroll
+  for (int b = 0; b < MB; ++b) {
+    const int j = threadIdx.x + b * NT;
+    const int k = j & (NS - 1);
+    v[b][0] = buf[fpad(j)];
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      float2 w = __ldg(&tws[r * NS + k]);
+      if (inv) w.y = -w.y;
+      v[b][r] = cmul(buf[fpad(j + r * NB)], w);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int b = 0; b < MB; ++b) {
+    const int j = threadIdx.x + b * NT;
+    const int k = j & (NS - 1);
+    Dft<R>::run(v[b], inv, nullptr, 0);
+    const int base = (j - k) * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) buf[fpad(base + r * NS)] = v[b][r];
+  }
+  __syncthreads();
+}
+
+template <int L, int NS, int S>
+__device__ __forceinline__ void p2_fft(float2* buf, const FftAxis& ax, const float2* __restrict__ tw,
+                                       bool inv) {
+  if constexpr (NS * 16 <= L) {
+    p2_stage16<L, NS>(buf, tw + ax.tw_off[S], inv);
+    p2_fft<L, NS * 16, S + 1>(buf, ax, tw, inv);
+  } else if constexpr (NS < L) {
+    p2_tail<L, NS>(buf, tw + ax.tw_off[S], inv);
+  }
+}
+
 // Whole 1-D transform of buf (length ax.L, natural order in and out,
 // unnormalised).  The caller synchronises before (inputs written) and the
-// last stage synchronises after.
-__device__ void fft_1d(float2* buf, const FftAxis& ax, const float2* __restrict__ tw, bool inv) {
+// last stage synchronises after.  P2: the radix-16 path (ax.p2 set); each
+// kernel is compiled once per path, so neither path's registers burden the
+// other.
+template <bool P2>
+__device__ __forceinline__ void fft_1d(float2* buf, const FftAxis& ax,
+                                       const float2* __restrict__ tw, bool inv) {
+  if constexpr (P2) {
+    switch (ax.L) {
+      case 8192: p2_fft<8192, 1, 0>(buf, ax, tw, inv); return;
+      case 4096: p2_fft<4096, 1, 0>(buf, ax, tw, inv); return;
+      default: p2_fft<2048, 1, 0>(buf, ax, tw, inv); return;
+    }
+  }
   int Ns = 1;
   for (int s = 0; s < ax.nrad; ++s) {
     const int R = ax.rad[s];
@@ -227,6 +366,7 @@ __device__ __forceinline__ float kernel_image(const PlanDev& d, int Ly, int Lx, 
 
 // Rows 2a and 2a + 1 of the kernel image through one complex FFT along x;
 // their Hermitian halves go to Kspec[k][2a], Kspec[k][2a + 1] (k <= Lx/2).
+template <bool P2>
 __global__ void __launch_bounds__(kFftMaxThreads, 1) fft_psf_rows_kernel(PlanDev d, FftAxis ax, int Ly, const float2* __restrict__ twx,
                                     float2* __restrict__ Kspec) {
   extern __shared__ float2 fbuf[];
@@ -235,7 +375,7 @@ __global__ void __launch_bounds__(kFftMaxThreads, 1) fft_psf_rows_kernel(PlanDev
     fbuf[fpad(mx)] = make_float2(kernel_image(d, Ly, Lx, 2 * a, mx),
                                  kernel_image(d, Ly, Lx, 2 * a + 1, mx));
   __syncthreads();
-  fft_1d(fbuf, ax, twx, false);
+  fft_1d<P2>(fbuf, ax, twx, false);
   for (int k = threadIdx.x; k <= Lx / 2; k += blockDim.x) {
     const float2 z1 = fbuf[fpad(k)];
     const float2 z = fbuf[fpad(k == 0 ? 0 : Lx - k)];
@@ -249,6 +389,7 @@ __global__ void __launch_bounds__(kFftMaxThreads, 1) fft_psf_rows_kernel(PlanDev
 
 // Column k of the row transforms through a forward FFT along y, scaled by
 // 1 / (Ly Lx), in place.
+template <bool P2>
 __global__ void __launch_bounds__(kFftMaxThreads, 1) fft_psf_cols_kernel(FftAxis ay, const float2* __restrict__ twy,
                                     float2* __restrict__ Kspec, float scale) {
   extern __shared__ float2 fbuf[];
@@ -256,7 +397,7 @@ __global__ void __launch_bounds__(kFftMaxThreads, 1) fft_psf_cols_kernel(FftAxis
   float2* col = Kspec + (int64_t)blockIdx.x * Ly;
   for (int i = threadIdx.x; i < Ly; i += blockDim.x) fbuf[fpad(i)] = col[i];
   __syncthreads();
-  fft_1d(fbuf, ay, twy, false);
+  fft_1d<P2>(fbuf, ay, twy, false);
   for (int i = threadIdx.x; i < Ly; i += blockDim.x) {
     const float2 v = fbuf[fpad(i)];
     col[i] = make_float2(v.x * scale, v.y * scale);
@@ -329,6 +470,7 @@ __global__ void __launch_bounds__(kCompThreads)
 // chain), so the result is deterministic.  The kernel spectrum's column
 // arrives by one bulk copy into shared memory, issued a column ahead, so
 // its load overlaps the previous column's transforms.
+template <bool P2>
 __global__ void __launch_bounds__(kFftMaxThreads, 1)
     fft_cols_kernel(PlanDev d, FftAxis ay, int Lx, const int4* __restrict__ comps,
                     const int* __restrict__ lead, const float2* __restrict__ twx,
@@ -375,7 +517,7 @@ __global__ void __launch_bounds__(kFftMaxThreads, 1)
       fbuf[fpad(y)] = acc;
     }
     __syncthreads();
-    fft_1d(fbuf, ay, twy, false);
+    fft_1d<P2>(fbuf, ay, twy, false);
     // the spectrum column: every thread waits (bounded) for the bulk copy
     if (!ptx::mbar_wait_bounded(&kbar, phase, limit_ns)) {
       atomicOr(&d.st->status, ST_TIMEOUT);
@@ -396,7 +538,7 @@ __global__ void __launch_bounds__(kFftMaxThreads, 1)
       ptx::mbar_arrive_expect_tx(&kbar, kbytes);
       bulk_load(kst, Kspec + (int64_t)(k + gridDim.x) * Ly, kbytes, &kbar);
     }
-    fft_1d(fbuf, ay, twy, true);
+    fft_1d<P2>(fbuf, ay, twy, true);
     float2* ycol = Y + (int64_t)k * ny;
 #pragma unroll
     for (int u = 0; u < kFftValsPerThread; ++u) {
@@ -414,6 +556,7 @@ __global__ void __launch_bounds__(kFftMaxThreads, 1)
 // key; the last block closes the round.  Every thread issues all of its
 // global loads before it uses any (at most kFftValsPerThread / 2 spectrum
 // bins and image columns a thread).
+template <bool P2>
 __global__ void __launch_bounds__(kFftMaxThreads, 1)
     fft_rows_kernel(PlanDev d, FftAxis ax, const float2* __restrict__ twx,
                     const float2* __restrict__ Y, float* __restrict__ R0, int parity,
@@ -453,7 +596,7 @@ __global__ void __launch_bounds__(kFftMaxThreads, 1)
       }
     }
     __syncthreads();
-    fft_1d(fbuf, ax, twx, true);
+    fft_1d<P2>(fbuf, ax, twx, true);
     // R <- R0 - S for this thread's columns (all loads first), results back
     // into fbuf as (row q0, row q1) for the per-tile peak scans
     float r0v[kHalf], r1v[kHalf];
@@ -564,16 +707,26 @@ bool fft_axis_init(FftAxis* a, int L) {
       r /= f;
     }
   if (r != 1) return false;
+  if (L == 2048 || L == 4096 || L == 8192) {  // radix-16 stages, then the rest
+    x.p2 = 1;
+    x.nrad = 0;
+    for (int m = L; m > 1;) {
+      const int f = m >= 16 ? 16 : m;
+      x.rad[x.nrad++] = f;
+      m /= f;
+    }
+  }
   int off = L, Ns = 1;
   for (int st = 0; st < x.nrad; ++st) {
     x.tw_off[st] = off;
-    off += x.rad[st] * Ns;
+    off += (x.rad[st] == 16 ? 4 : x.rad[st]) * Ns;  // radix 16: w, w^2, w^4, w^8 per k
     Ns *= x.rad[st];
   }
   x.tw_len = off;
-  // at most kFftValsPerThread values a thread in every stage
+  // at most kFftValsPerThread values a thread in every stage (the radix-16
+  // path: exactly one butterfly of 16 a thread)
   const int need = (L + kFftValsPerThread - 1) / kFftValsPerThread;
-  x.nthr = std::min(kFftMaxThreads, std::max(128, (need + 31) / 32 * 32));
+  x.nthr = x.p2 ? L / 16 : std::min(kFftMaxThreads, std::max(128, (need + 31) / 32 * 32));
   *a = x;
   return true;
 }
@@ -595,9 +748,15 @@ cudaError_t fft_make_twiddles(float2* d_tw, const FftAxis& a, cudaStream_t s) {
   int Ns = 1;
   for (int st = 0; st < a.nrad; ++st) {
     const int R = a.rad[st];
-    for (int r = 0; r < R; ++r)
+    if (R == 16) {
       for (int k = 0; k < Ns; ++k)
-        h[(size_t)a.tw_off[st] + (size_t)r * Ns + k] = root((int64_t)r * k, (int64_t)Ns * R);
+        for (int e = 0; e < 4; ++e)
+          h[(size_t)a.tw_off[st] + 4 * (size_t)k + e] = root((int64_t)k << e, (int64_t)Ns * R);
+    } else {
+      for (int r = 0; r < R; ++r)
+        for (int k = 0; k < Ns; ++k)
+          h[(size_t)a.tw_off[st] + (size_t)r * Ns + k] = root((int64_t)r * k, (int64_t)Ns * R);
+    }
     Ns *= R;
   }
   cudaError_t e = cudaMemcpyAsync(d_tw, h.data(), sizeof(float2) * (size_t)a.tw_len,
@@ -609,11 +768,17 @@ cudaError_t fft_make_twiddles(float2* d_tw, const FftAxis& a, cudaStream_t s) {
 cudaError_t fft_build_psf_spectrum(const PlanDev& d, const FftAxis& ay, const FftAxis& ax,
                                    const float2* twy, const float2* twx, float2* Kspec,
                                    cudaStream_t s) {
-  fft_psf_rows_kernel<<<ay.L / 2, ax.nthr, fft_smem_bytes(ax.L), s>>>(d, ax, ay.L, twx, Kspec);
+  if (ax.p2)
+    fft_psf_rows_kernel<true><<<ay.L / 2, ax.nthr, fft_smem_bytes(ax.L), s>>>(d, ax, ay.L, twx, Kspec);
+  else
+    fft_psf_rows_kernel<false><<<ay.L / 2, ax.nthr, fft_smem_bytes(ax.L), s>>>(d, ax, ay.L, twx, Kspec);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const float scale = (float)(1.0 / ((double)ay.L * (double)ax.L));
-  fft_psf_cols_kernel<<<ax.L / 2 + 1, ay.nthr, fft_smem_bytes(ay.L), s>>>(ay, twy, Kspec, scale);
+  if (ay.p2)
+    fft_psf_cols_kernel<true><<<ax.L / 2 + 1, ay.nthr, fft_smem_bytes(ay.L), s>>>(ay, twy, Kspec, scale);
+  else
+    fft_psf_cols_kernel<false><<<ax.L / 2 + 1, ay.nthr, fft_smem_bytes(ay.L), s>>>(ay, twy, Kspec, scale);
   return cudaGetLastError();
 }
 
@@ -630,22 +795,32 @@ cudaError_t fft_feedback_round(const PlanDev& d, const FftAxis& ay, const FftAxi
   const int ncols = ax.L / 2 + 1;
   const int grid = std::min(ncols, fft_sm_count());
   const size_t cs = sizeof(float2) * (size_t)ay.L + fft_smem_bytes(ay.L);
-  fft_cols_kernel<<<grid, ay.nthr, cs, s>>>(d, ay, ax.L, comps, lead, twx, twy, Kspec, Y,
-                                            kFftWaitNs);
+  if (ay.p2)
+    fft_cols_kernel<true><<<grid, ay.nthr, cs, s>>>(d, ay, ax.L, comps, lead, twx, twy, Kspec, Y,
+                                                    kFftWaitNs);
+  else
+    fft_cols_kernel<false><<<grid, ay.nthr, cs, s>>>(d, ay, ax.L, comps, lead, twx, twy, Kspec, Y,
+                                                     kFftWaitNs);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int nb = (d.ny + 1) / 2;
   const size_t smem = fft_smem_bytes(ax.L) + sizeof(int32_t) * (2 * (size_t)d.T + 1);
-  fft_rows_kernel<<<nb, ax.nthr, smem, s>>>(d, ax, twx, Y, R0, parity, nb);
+  if (ax.p2)
+    fft_rows_kernel<true><<<nb, ax.nthr, smem, s>>>(d, ax, twx, Y, R0, parity, nb);
+  else
+    fft_rows_kernel<false><<<nb, ax.nthr, smem, s>>>(d, ax, twx, Y, R0, parity, nb);
   return cudaGetLastError();
 }
 
 cudaError_t fft_prepare() {
-  cudaError_t e = allow_max_smem((const void*)fft_psf_rows_kernel);
-  if (e == cudaSuccess) e = allow_max_smem((const void*)fft_psf_cols_kernel);
-  if (e == cudaSuccess) e = allow_max_smem((const void*)fft_cols_kernel);
-  if (e == cudaSuccess) e = allow_max_smem((const void*)fft_comp_list_kernel);
-  if (e == cudaSuccess) e = allow_max_smem((const void*)fft_rows_kernel);
+  const void* fns[] = {(const void*)fft_psf_rows_kernel<true>, (const void*)fft_psf_rows_kernel<false>,
+                       (const void*)fft_psf_cols_kernel<true>, (const void*)fft_psf_cols_kernel<false>,
+                       (const void*)fft_cols_kernel<true>,     (const void*)fft_cols_kernel<false>,
+                       (const void*)fft_rows_kernel<true>,     (const void*)fft_rows_kernel<false>,
+                       (const void*)fft_comp_list_kernel};
+  cudaError_t e = cudaSuccess;
+  for (const void* f : fns)
+    if (e == cudaSuccess) e = allow_max_smem(f);
   return e;
 }
 
