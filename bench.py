@@ -722,7 +722,8 @@ def main():
             torch.cuda.synchronize()
             fms.append(a.elapsed_time(b))
         fft = {"iters_per_s": w.niter * len(fms) / (sum(fms) / 1e3), "ms_per_step": sum(fms) / len(fms),
-               "note": "feedback by FFT convolution (cuFFT transforms, own kernels around them); "
+               "note": "feedback by FFT convolution with this library's own transforms (sparse "
+                       "row DFT fused into pruned radix-16 column FFTs, paired-row inverse); "
                        "residual within 1e-4 Jy of the float64 replay, not bit-exact"}
         fp.close()
 

@@ -22,11 +22,13 @@ std::atomic<int64_t> g_alloc_limit{-1};
 constexpr int64_t kResidentMaxBytes = 200 * 1024;  // residual rows per CTA in smem
 constexpr int kMaxBeamRadius = 64;
 constexpr int64_t kDefaultSpinNs = 2000000000ll;
-// FFT feedback cost model of AUTO (seconds per spectrum cell, per image
-// pixel, and per round's launches), from GB300 measurements
-constexpr double kFftCellS = 8e-12;
-constexpr double kFftPixelS = 4e-12;
-constexpr double kFftLaunchS = 20e-6;
+// FFT feedback cost model of AUTO: seconds per spectrum cell and per round's
+// launches, fitted to GB300 rounds on 2048- and 8192-point grids (0.087 and
+// 0.665 ms); grids off the radix-16 path take the mixed-radix kernels, about
+// kFftMixedFactor times slower per cell
+constexpr double kFftCellS = 18e-12;
+constexpr double kFftLaunchS = 48e-6;
+constexpr double kFftMixedFactor = 2.5;
 
 }  // namespace
 
@@ -724,8 +726,8 @@ int clean_plan(clean_plan_t* out, const clean_params* p, const float* d_psf, voi
   // FFT feedback: a grid of at least (2 ny - 1) x (2 nx - 1) so the circular
   // convolution never wraps onto an image pixel.  AUTO takes it when a round's
   // gather (about 0.21 ns per pixel-component update on GB300) would cost more
-  // than the transforms (estimated per spectrum cell and per image pixel, plus
-  // the launches).  Grids longer than kFftMaxL per axis are not served.
+  // than the transforms (estimated per spectrum cell, plus the launches).
+  // Grids longer than kFftMaxL per axis are not served.
   const bool fb_on = (p->feedback_interval > 0 || p->feedback_trigger > 0.f) && T > 1;
   const int fb_mode = forced_feedback_mode(p->feedback_mode);
   pl->Ly = fft_grid_size(2 * p->ny - 1);
@@ -743,8 +745,8 @@ int clean_plan(clean_plan_t* out, const clean_params* p, const float* d_psf, voi
         (double)(p->feedback_interval > 0 ? std::min<int64_t>(p->feedback_interval, per_tile_max)
                                           : per_tile_max) * T;
     const double gather_s = comps * ((double)npix - (double)npix / T) * 0.21e-9;
-    const double fft_s = (double)pl->Ly * (pl->Lx / 2 + 1) * kFftCellS +
-                         (double)npix * kFftPixelS + kFftLaunchS;
+    const double per_cell = kFftCellS * (pl->fft_ay.p2 && pl->fft_ax.p2 ? 1.0 : kFftMixedFactor);
+    const double fft_s = (double)pl->Ly * (pl->Lx / 2 + 1) * per_cell + kFftLaunchS;
     pl->fft = fft_s < gather_s;
   }
   const size_t spec_bytes = sizeof(float2) * (size_t)pl->Ly * (pl->Lx / 2 + 1);
