@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-fft", action="store_true", help="skip the FFT-feedback comparison run")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 64-image leg")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
+    ap.add_argument("--serve-jobs", type=int, default=60,
+                    help="jobs of the serving leg (the sweep runs 500 at three loads)")
     ap.add_argument("--untiled-iters", type=int, default=2000,
                     help="iterations of the untiled whole-GPU comparison run (0: skip)")
     ap.add_argument("--sweep", action="store_true",
@@ -233,17 +235,18 @@ def l2_peak(cg, torch, local):
     """L2 -> SM read bandwidth of this GPU, measured by the library's probe
     (clean_probe_l2_read) on a 48 MiB buffer (inside the 126 MB L2): bulk
     copies into shared memory (1 and 2 CTAs per SM) and 16-byte vector loads
-    (2 and 4 CTAs per SM), 40 passes each, best of three timed launches.
+    (2 and 4 CTAs per SM), 100 passes each, best of three timed launches.
     The peak is the fastest form; clocks are sampled while it runs."""
     buf = torch.ones(48 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     sampler = ClockSampler(local)
     sampler.start()
+    time.sleep(0.6)  # the sampler's first readings
     forms = {}
     for name, method, ctas in (("bulk_copy_1cta", 0, 1), ("bulk_copy_2cta", 0, 2),
                                ("vector_load_2cta", 1, 2), ("vector_load_4cta", 1, 4)):
         best = 0.0
         for _ in range(3):
-            nb, ms = cg.probe_l2_read(buf, passes=40, method=method, ctas_per_sm=ctas)
+            nb, ms = cg.probe_l2_read(buf, passes=100, method=method, ctas_per_sm=ctas)
             best = max(best, nb / (ms / 1e3) / 1e9)
         forms[name] = round(best, 1)
     clocks = sampler.stop()
@@ -251,7 +254,7 @@ def l2_peak(cg, torch, local):
     top = max(forms, key=forms.get)
     return {"GBps": forms[top], "form": top, "forms_GBps": forms, "buffer_bytes": 48 << 20,
             "clocks": clocks,
-            "method": "clean_probe_l2_read: 48 MiB buffer read 40 times over after a warm "
+            "method": "clean_probe_l2_read: 48 MiB buffer read 100 times over after a warm "
                       "pass, CUDA events, best of 3 per form"}
 
 
@@ -305,65 +308,82 @@ def batch_leg(cg, torch, stream, n_images=64):
             "rounds": st["rounds_launched"], "kernel_launches": st["kernel_launches"]}
 
 
-def serve_leg(cg, torch, n_jobs=60, load=0.7):
-    """Poisson stream of mixed-size jobs through the continuous-batching
-    server vs one-at-a-time plain (untiled) CLEAN on the same arrivals.  The
-    arrival rate is `load` x the one-at-a-time server's capacity (1 / its
-    mean service time, measured here), so the baseline queue is stable."""
+def serve_leg(cg, torch, psf_full, n_jobs=60, loads=(0.7,), seed=1004):
+    """A Poisson stream of independent deconvolution jobs (sides log-uniform
+    over 256 - 4096 rounded to multiples of 64, 10 - 500 sources, 1000 - 20000
+    iterations, each its own dirty image) through the continuous-batching
+    server, against one-at-a-time plain (untiled) CLEAN on the same arrivals:
+    both run the queue in real time.  Arrival rates are `loads` x the
+    one-at-a-time server's capacity (1 / its mean service time, measured on
+    these jobs), so its queue is stable.  Latency counts from arrival to the
+    job's results being done on the device."""
     from paper_2501_01461_gb300 import serve
-    images, specs = synth.serving_jobs(n_jobs)
-    dev = {n: (torch.from_numpy(p).cuda(), torch.from_numpy(d).cuda()) for n, (p, d) in images.items()}
-    # one-at-a-time plain CLEAN: service time of every job, measured alone
+    t_gen = time.perf_counter()
+    specs = synth.serving_stream(psf_full, n_jobs, seed)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t_gen
+    mk = lambda sp, t=0.0: serve.Job(psf=sp["psf"], dirty=sp["dirty"], niter=sp["niter"],
+                                     tiles=sp["tiles"], feedback_interval=sp["K"], arrival=t)
+
+    def run_plain(job):  # one-at-a-time plain CLEAN: set-up, run, results ready
+        with cg.Plan(job.psf, job.n, job.n, gain=0.1, niter=job.niter, threshold=0.0,
+                     tiles=(1, 1)) as p:
+            p.run(job.dirty)
+            torch.cuda.synchronize()
+
+    # warm-up: every side once each way (kernel attributes, tensor maps)
+    seen = {}
+    for sp in specs:
+        seen.setdefault(sp["n"], sp)
+    for sp in seen.values():
+        w = dict(sp, niter=min(sp["niter"], 1000))
+        run_plain(mk(w))
+    serve.serve([mk(dict(sp, niter=min(sp["niter"], 1000))) for sp in seen.values()],
+                budget_bytes=150e9, keep_results=False)
     service = []
     for sp in specs:
-        psf, dirty = dev[sp["n"]]
-        with cg.Plan(psf, sp["n"], sp["n"], gain=0.1, niter=sp["niter"], threshold=0.0,
-                     tiles=(1, 1)) as p:
-            p.run(dirty)
-            torch.cuda.synchronize()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record()
-            p.run(dirty)
-            b.record()
-            torch.cuda.synchronize()
-            service.append(a.elapsed_time(b) / 1e3)
+        t0 = time.perf_counter()
+        run_plain(mk(sp))
+        service.append(time.perf_counter() - t0)
+    capacity = 1.0 / float(np.mean(service))
     gaps = np.random.default_rng(7).exponential(1.0, size=n_jobs)  # unit-rate Poisson
-
-    def stream(ld):
-        rate = ld / float(np.mean(service))
+    out = {}
+    for ld in loads:
+        rate = ld * capacity
         arrivals = np.cumsum(gaps / rate)
         arrivals -= arrivals[0]
-        base = serve.fifo_latencies(arrivals, service)
-        jobs = [serve.Job(psf=dev[sp["n"]][0], dirty=dev[sp["n"]][1], niter=sp["niter"],
-                          tiles=sp["tiles"], feedback_interval=sp["K"], arrival=float(t))
-                for sp, t in zip(specs, arrivals)]
+        base_jobs = [mk(sp, float(t)) for sp, t in zip(specs, arrivals)]
+        base = serve.serve_one_at_a_time(base_jobs, run_plain)
+        jobs = [mk(sp, float(t)) for sp, t in zip(specs, arrivals)]
         st = serve.serve(jobs, budget_bytes=150e9, rounds_per_step=2, keep_results=False)
-        return rate, base, jobs, st
-
-    stream(1.0)  # warm-up: kernels, tensor maps and graphs of every job shape
-    other = {}
-    for ld in (0.5, 0.9):
-        _, b2, _, s2 = stream(ld)
-        other[f"{ld:.1f}"] = {"p50_s": s2["p50_s"], "p99_s": s2["p99_s"],
-                              "one_at_a_time_plain_p50_s": float(np.percentile(b2, 50)),
-                              "one_at_a_time_plain_p99_s": float(np.percentile(b2, 99))}
-    rate, base, jobs, st = stream(load)
-    # saturated throughput: every job waiting at t = 0
-    for j in jobs:
-        j.arrival, j.admitted, j.finished = 0.0, None, None
-    sat = serve.serve(jobs, budget_bytes=150e9, rounds_per_step=4, keep_results=False)
-    total_iters = sum(sp["niter"] for sp in specs)
-    return {"workload": f"{n_jobs} jobs, sizes 256-4096 (powers of two, log-uniform), "
-                        "1000-20000 iterations, K 50, Poisson arrivals at "
-                        f"{load:.1f} x the one-at-a-time plain-CLEAN capacity, 150 GB budget",
+        model = serve.fifo_latencies(arrivals, service)
+        out[f"{ld:.1f}"] = {
             "arrival_rate_per_s": rate,
             "p50_s": st["p50_s"], "p99_s": st["p99_s"], "jobs_per_s": st["jobs_per_s"],
-            "one_at_a_time_plain_p50_s": float(np.percentile(base, 50)),
-            "one_at_a_time_plain_p99_s": float(np.percentile(base, 99)),
+            "one_at_a_time_plain_p50_s": base["p50_s"], "one_at_a_time_plain_p99_s": base["p99_s"],
+            "one_at_a_time_plain_jobs_per_s": base["jobs_per_s"],
+            "modelled_fifo_p50_s": float(np.percentile(model, 50)),
+            "modelled_fifo_p99_s": float(np.percentile(model, 99))}
+    # saturated: every job waiting at t = 0
+    jobs = [mk(sp) for sp in specs]
+    sat = serve.serve(jobs, budget_bytes=150e9, rounds_per_step=4, keep_results=False)
+    total_iters = sum(sp["niter"] for sp in specs)
+    px_iter = sum(sp["niter"] * (sp["n"] ** 2) / (sp["tiles"][0] * sp["tiles"][1]) for sp in specs)
+    sides = [sp["n"] for sp in specs]
+    return {"workload": f"{n_jobs} jobs, sides log-uniform 256-4096 rounded to multiples of 64 "
+                        f"({sum(1 for n in sides if n & (n - 1))} not powers of two), 10-500 "
+                        "sources each (own dirty image), 1000-20000 iterations, gain 0.1, K 50, "
+                        "tiles 1x1 / 2x2 / 4x4 by side, PSF 2N (crops of the 8192^2 array PSF), "
+                        "Poisson arrivals, 150 GB admission budget",
+            "loads": out,
+            "one_at_a_time_plain_capacity_jobs_per_s": capacity,
             "saturated_jobs_per_s": sat["jobs_per_s"],
             "saturated_iters_per_s": total_iters / sat["makespan_s"],
-            "one_at_a_time_plain_jobs_per_s": n_jobs / float(np.sum(service)),
-            "other_loads": other}
+            "saturated_px_iter_per_s": px_iter / sat["makespan_s"],
+            "generation_s": t_gen,
+            "note": "both servers run the queue in real time on the same arrivals; "
+                    "modelled_fifo_* is the FIFO arithmetic on the measured solo service times, "
+                    "for comparison only"}
 
 
 def cpu_baseline(w, data):
@@ -432,9 +452,11 @@ def run_sweep(args):
     choice, a 16-CTA cluster) and the 1024^2 tiled one run in full on the GPU
     and on the CPU oracle (one thread, and the oracle's arithmetic on all host
     cores), and the 4096^2 workload at feedback intervals 10, 20, 50, 100 and
-    200 with exact (gather) and FFT feedback.  GPU figures are the median of
-    three CUDA-event-timed runs after one warm-up, with a 512 MiB write
-    between runs; each run deconvolves the whole image."""
+    200 with exact (gather) and FFT feedback, and the serving stream in full
+    (500 jobs at 0.5, 0.7 and 0.9 x the one-at-a-time capacity, both servers
+    run in real time).  GPU figures are the median of three CUDA-event-timed
+    runs after one warm-up, with a 512 MiB write between runs; each run
+    deconvolves the whole image."""
     import torch
 
     import oracle
@@ -506,6 +528,8 @@ def run_sweep(args):
         ks[str(K)] = {"gpu_gather": gpu(w2, d2, 0.0, K, reps=2),
                       "gpu_fft": gpu(w2, d2, 0.0, K, fb=cg.FB_FFT, reps=2)}
     out["tiled-4096-K"] = {"config": cfgd(w2, 0.0), "by_K": ks}
+    # the serving workload in full: 500 jobs at 0.5, 0.7 and 0.9 x capacity
+    out["served-500"] = serve_leg(cg, torch, d2["psf"], n_jobs=500, loads=(0.5, 0.7, 0.9))
     print(json.dumps(out))
 
 
@@ -734,7 +758,7 @@ def main():
 
     served = None
     if not args.no_serve:
-        served = serve_leg(cg, torch)
+        served = serve_leg(cg, torch, psf, n_jobs=args.serve_jobs)
 
     cpu = cpu_par = None
     if rank == 0 and world == 1 and not args.no_cpu:

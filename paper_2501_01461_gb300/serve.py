@@ -211,6 +211,28 @@ def serve(jobs: list, budget_bytes: float = 150e9, rounds_per_step: int = 2,
             "mean_s": float(lat.mean())}
 
 
+def serve_one_at_a_time(jobs: list, run_job, clock=time.perf_counter) -> dict:
+    """The baseline server: jobs run one at a time in arrival order, in real
+    time (an idle server waits for the next arrival); run_job(job) runs one
+    job to completion and returns when its results are on the host side of
+    the stream (synchronised).  Fills each job's admitted / finished times and
+    returns latency statistics as serve() does."""
+    order = sorted(range(len(jobs)), key=lambda i: jobs[i].arrival)
+    t0 = clock()
+    for i in order:
+        job = jobs[i]
+        while clock() - t0 < job.arrival:
+            time.sleep(min(job.arrival - (clock() - t0), 0.01))
+        job.admitted = clock() - t0
+        run_job(job)
+        job.finished = clock() - t0
+    lat = np.array([j.latency for j in jobs])
+    span = max(j.finished for j in jobs) - min(j.arrival for j in jobs)
+    return {"jobs": len(jobs), "makespan_s": span, "jobs_per_s": len(jobs) / span,
+            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "mean_s": float(lat.mean())}
+
+
 def fifo_latencies(arrivals, service_s) -> np.ndarray:
     """Latencies of a one-at-a-time FIFO server with the given service times."""
     t = 0.0

@@ -22,7 +22,7 @@ import numpy as np
 __all__ = [
     "y_array_enu", "uv_tracks", "make_psf", "make_sky", "make_dirty",
     "fit_beam", "Workload", "workload", "WORKLOADS",
-    "random_psf", "random_image", "tie_image",
+    "random_psf", "random_image", "tie_image", "batch_jobs", "serving_stream",
 ]
 
 # ---------------------------------------------------------------------------
@@ -302,22 +302,46 @@ def batch_jobs(n_images: int = 64, seed: int = 1003, niter: int = 2000, n_source
     return jobs
 
 
-def serving_jobs(n_jobs: int = 60, seed: int = 1004, sizes=(256, 512, 1024, 2048, 4096)):
-    """Serving stream: sizes log-uniform over {256 .. 4096} (uniform over the
-    five powers of two), 10 - 500 sources, 1000 - 20000 iterations, gain 0.1,
-    K 50, tiles 1x1 up to 256, 2x2 up to 1024, 4x4 above.  One PSF and one
-    dirty image per size (each job draws its own source count for the record
-    but shares its size's image, which keeps the generator fast).  Returns
-    (images_by_size, job specs)."""
+def serving_stream(psf_full, n_jobs: int = 500, seed: int = 1004, lo: int = 256,
+                   hi: int = 4096, step: int = 64, device: str = "cuda"):
+    """Serving stream of independent jobs, built on the GPU (torch).
+
+    Each job: side n log-uniform over [lo, hi] rounded to a multiple of
+    ``step`` (so most sides are not powers of two), 10 - 500 point sources
+    (log-uniform 10 mJy .. 2.1 Jy, one at 2.1 Jy), 1000 - 20000 iterations,
+    gain 0.1, K 50, tiles 1x1 up to 256, 2x2 up to 1024, 4x4 above, its own
+    dirty image = sum of flux * PSF shifted (float64) + white noise
+    sigma = 1 mJy (a torch generator seeded 10000 + job).  The PSF of a side n
+    is the central 2n x 2n crop of ``psf_full`` (the Y-array PSF on a grid of
+    at least 2 hi: its main lobe and near sidelobes sit at the same pixel
+    scale for every size); jobs of one side share it.  Returns a list of dicts
+    (n, n_sources, niter, tiles, K, gain, psf, dirty) with CUDA float32
+    tensors."""
+    import torch
     rng = np.random.default_rng(seed)
-    images = {}
-    for n in sizes:
-        psf = make_psf(2 * n, 2 * n)
-        ys, xs, fl = make_sky(n, int(rng.integers(10, 501)), 0.01, 2.1, rng)
-        images[n] = (psf, make_dirty(psf, n, ys, xs, fl, 1e-3, rng))
-    specs = []
-    for _ in range(n_jobs):
-        n = int(rng.choice(sizes))
+    P = torch.as_tensor(psf_full, device=device)
+    cy, cx = P.shape[0] // 2, P.shape[1] // 2
+    sides = np.exp(rng.uniform(math.log(lo), math.log(hi), size=n_jobs))
+    sides = np.clip(np.rint(sides / step) * step, lo, hi).astype(np.int64)
+    crops, crops64 = {}, {}
+    jobs = []
+    for j in range(n_jobs):
+        n = int(sides[j])
+        if n not in crops:
+            c = P[cy - n:cy + n, cx - n:cx + n].contiguous()
+            crops[n], crops64[n] = c, c.double()
+        ns = int(rng.integers(10, 501))
+        niter = int(rng.integers(1000, 20001))
+        ys, xs, fl = make_sky(n, ns, 0.01, 2.1, rng)
+        p64 = crops64[n]
+        d = torch.zeros((n, n), dtype=torch.float64, device=device)
+        for y, x, f in zip(ys.tolist(), xs.tolist(), fl.tolist()):
+            # pixel q takes P[q - source + centre]; the crop's centre is (n, n)
+            d += f * p64[n - y:2 * n - y, n - x:2 * n - x]
+        g = torch.Generator(device=device)
+        g.manual_seed(10000 + j)
+        d += 1e-3 * torch.randn((n, n), generator=g, dtype=torch.float64, device=device)
         tiles = (1, 1) if n <= 256 else (2, 2) if n <= 1024 else (4, 4)
-        specs.append(dict(n=n, niter=int(rng.integers(1000, 20001)), tiles=tiles, K=50))
-    return images, specs
+        jobs.append(dict(n=n, n_sources=ns, niter=niter, tiles=tiles, K=50, gain=0.1,
+                         psf=crops[n], dirty=d.float().contiguous()))
+    return jobs

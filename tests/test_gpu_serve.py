@@ -129,3 +129,34 @@ def test_served_fft_job_equals_solo_fft_run():
         assert np.array_equal(res.cpu().numpy().view(np.uint32), solo["residual"].view(np.uint32))
         assert np.array_equal(comps["flux"].view(np.uint32), solo["comps"]["flux"].view(np.uint32))
 
+
+
+def test_serving_stream_non_power_of_two_jobs_equal_solo_runs():
+    """Jobs of the serving stream's kind (sides log-uniform, rounded to
+    multiples of 64, so mostly not powers of two; each its own sky and dirty
+    image; crops of one large PSF) served together in real time equal their
+    solo runs bit for bit, and the one-at-a-time baseline server runs the
+    same jobs in arrival order."""
+    import torch
+    psf_full = synth.make_psf(1024, 1024)
+    specs = synth.serving_stream(psf_full, n_jobs=6, seed=77, lo=192, hi=512, step=64)
+    sides = [sp["n"] for sp in specs]
+    assert all(n % 64 == 0 and 192 <= n <= 512 for n in sides)
+    assert any(n & (n - 1) for n in sides)             # a side that is not a power of two
+    jobs = [serve.Job(psf=sp["psf"], dirty=sp["dirty"], niter=min(sp["niter"], 1500),
+                      tiles=sp["tiles"], feedback_interval=sp["K"], arrival=0.003 * i)
+            for i, sp in enumerate(specs)]
+    serve.serve(jobs, budget_bytes=4e9)
+    for j in jobs:
+        _same(j.result, gpu_clean(j.dirty.cpu().numpy(), j.psf.cpu().numpy(), 0.1, j.niter, 0.0,
+                                  j.tiles, j.feedback_interval))
+    ran = []
+
+    def run(job):
+        with cg.Plan(job.psf, job.n, job.n, niter=job.niter, tiles=(1, 1)) as p:
+            p.run(job.dirty)
+            torch.cuda.synchronize()
+        ran.append(job.arrival)
+    st = serve.serve_one_at_a_time(jobs, run)
+    assert ran == sorted(ran) and st["jobs"] == len(jobs)
+    assert all(j.finished >= j.admitted >= j.arrival - 1e-9 for j in jobs)
