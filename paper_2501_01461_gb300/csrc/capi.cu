@@ -78,7 +78,7 @@ struct clean_plan_s {
   float2* fft_twy = nullptr;  // twiddle tables exp(-2 pi i t / L) of both axes
   float2* fft_twx = nullptr;
   float2* fft_K = nullptr;    // PSF kernel spectrum, (Lx/2 + 1) x Ly
-  float2* fft_Y = nullptr;    // round work area, (Lx/2 + 1) x ny
+  float2* fft_Y = nullptr;    // round work area, (Lx/2 + 1) x ny rounded up to even
   int4* fft_comps = nullptr;  // round work area: the round's components
   float* R0 = nullptr;        // residual at the start of the current round
   int feedback_path = 0;  // 0 auto, 1 plain loads, 2 TMA
@@ -769,7 +769,9 @@ int clean_plan(clean_plan_t* out, const clean_params* p, const float* d_psf, voi
   if (!d_psf) req.push_back({(void**)&pl->psf_own, sizeof(float) * (size_t)p->psf_ny * p->psf_nx});
   if (pl->fft) {
     req.push_back({(void**)&pl->fft_K, spec_bytes});
-    req.push_back({(void**)&pl->fft_Y, sizeof(float2) * (size_t)(pl->Lx / 2 + 1) * p->ny});
+    // pair-major rows: room for a whole last pair when ny is odd
+    req.push_back({(void**)&pl->fft_Y,
+                   sizeof(float2) * (size_t)(pl->Lx / 2 + 1) * (size_t)(p->ny + (p->ny & 1))});
     req.push_back({(void**)&pl->fft_comps, fft_comps_bytes(cap_round * T)});
     req.push_back({(void**)&pl->fft_twy, sizeof(float2) * (size_t)pl->fft_ay.tw_len});
     req.push_back({(void**)&pl->fft_twx, sizeof(float2) * (size_t)pl->fft_ax.tw_len});

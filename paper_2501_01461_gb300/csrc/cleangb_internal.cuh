@@ -256,7 +256,8 @@ cudaError_t fft_build_psf_spectrum(const PlanDev& d, const FftAxis& ay, const Ff
                                    const float2* twy, const float2* twx, float2* Kspec,
                                    cudaStream_t s);
 // One FFT feedback: R <- R0 - (round components (*) PSF) on every pixel,
-// R0 <- R, next peaks, round close.  Y: (Lx/2 + 1) x ny float2 work area;
+// R0 <- R, next peaks, round close.  Y: (Lx/2 + 1) x (ny rounded up to
+// even) float2 work area;
 // comps: fft_comps_bytes(T cap_round) bytes of work area.
 cudaError_t fft_feedback_round(const PlanDev& d, const FftAxis& ay, const FftAxis& ax,
                                const float2* twy, const float2* twx, const float2* Kspec,

@@ -410,19 +410,26 @@ __global__ void __launch_bounds__(kFftMaxThreads, 1) fft_psf_cols_kernel(FftAxis
 // as comps[1 + g] = (y, x, flux bits, next), where next is the list index of
 // the next component on the same image row (-1: none); comps[0] = (n, number
 // of rows with components); lead[0 .. rows) the first component of each such
-// row (in no particular order).  One block; a row's chain is found by
-// scanning the list, which is short (a round's components).
+// row (in no particular order).  One block: a histogram of the rows and its
+// prefix give each row its range of `bucket`; one warp then places the
+// components 32 at a time in list order (within a step, lanes of one row by
+// lane), so every row's range holds its components in list order, and the
+// chains follow the ranges.
 constexpr int kCompThreads = 1024;
 constexpr int kCompSmem = 8192;  // components whose rows are kept in shared memory
 __global__ void __launch_bounds__(kCompThreads)
-    fft_comp_list_kernel(PlanDev d, int4* __restrict__ comps, int* __restrict__ lead) {
+    fft_comp_list_kernel(PlanDev d, int4* __restrict__ comps, int* __restrict__ lead,
+                         int* __restrict__ bucket) {
   extern __shared__ int32_t s_int[];
-  int32_t* s_cnt = s_int;
-  int32_t* s_pre = s_int + d.T;
-  int32_t* s_y = s_int + 2 * d.T + 1;  // the components' rows, when they fit
+  int32_t* s_cnt = s_int;               // [T] then reused: [ny] row counts
+  int32_t* s_pre = s_int + d.T;         // [T + 1]
+  int32_t* s_rc = s_pre + d.T + 1;      // [ny] row counts, then running fill
+  int32_t* s_ro = s_rc + d.ny;          // [ny + 1] row offsets
+  int32_t* s_y = s_ro + d.ny + 1;       // the components' rows, when they fit
   __shared__ int s_rows;
   const bool live = *(volatile int32_t*)&d.st->status == 0;
   for (int s = threadIdx.x; s < d.T; s += blockDim.x) s_cnt[s] = live ? d.rcount[s] : 0;
+  for (int y = threadIdx.x; y < d.ny; y += blockDim.x) s_rc[y] = 0;
   if (threadIdx.x == 0) s_rows = 0;
   block_prefix(s_cnt, s_pre, d.T);
   const int n = s_pre[d.T];
@@ -432,32 +439,34 @@ __global__ void __launch_bounds__(kCompThreads)
     const clean_component cc = d.rcomps[(int64_t)s * d.cap_round + (g - s_pre[s])];
     comps[1 + g] = make_int4(cc.y, cc.x, __float_as_int(cc.flux), -1);
     if (in_smem) s_y[g] = cc.y;
+    atomicAdd(&s_rc[cc.y], 1);
+  }
+  block_prefix(s_rc, s_ro, d.ny);  // synchronises before and after
+  for (int y = threadIdx.x; y < d.ny; y += blockDim.x) s_rc[y] = 0;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    for (int base = 0; base < n; base += 32) {
+      const int g = base + lane;
+      const bool valid = g < n;
+      const int y = valid ? (in_smem ? s_y[g] : comps[1 + g].x) : -1 - lane;
+      const unsigned grp = __match_any_sync(0xffffffffu, y);
+      const int rank = __popc(grp & ((1u << lane) - 1u));
+      const int filled = valid ? s_rc[y] : 0;
+      __syncwarp();
+      if (valid) {
+        bucket[s_ro[y] + filled + rank] = g;
+        if ((grp >> lane) == 1u) s_rc[y] = filled + rank + 1;  // the group's last lane
+      }
+      __syncwarp();
+    }
   }
   __syncthreads();
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    const int y = in_smem ? s_y[j] : comps[1 + j].x;
-    // first: no earlier component on row y; next: the first later one
-    bool first = true;
-    int next = -1;
-    constexpr int kScan = 8;
-    for (int i0 = 0; i0 < n && next < 0; i0 += kScan) {
-      int yi[kScan];
-#pragma unroll
-      for (int u = 0; u < kScan; ++u) {
-        const int i = i0 + u;
-        yi[u] = i < n ? (in_smem ? s_y[i] : comps[1 + i].x) : -1;
-      }
-#pragma unroll
-      for (int u = 0; u < kScan; ++u) {
-        const int i = i0 + u;
-        if (yi[u] == y && i != j) {
-          if (i < j) first = false;
-          else if (next < 0) next = i;
-        }
-      }
-    }
-    comps[1 + j].w = next;
-    if (first) lead[atomicAdd(&s_rows, 1)] = j;
+  for (int p = threadIdx.x; p < n; p += blockDim.x) {
+    const int g = bucket[p];
+    const int y = in_smem ? s_y[g] : comps[1 + g].x;
+    comps[1 + g].w = p + 1 < s_ro[y + 1] ? bucket[p + 1] : -1;
+    if (p == s_ro[y]) lead[atomicAdd(&s_rows, 1)] = g;
   }
   __syncthreads();
   if (threadIdx.x == 0) comps[0] = make_int4(n, s_rows, 0, 0);
@@ -465,8 +474,8 @@ __global__ void __launch_bounds__(kCompThreads)
 
 // Columns k = blockIdx.x, blockIdx.x + gridDim.x, ... (one CTA per SM):
 // the components' x-axis DFT at k placed on their rows, forward FFT along y,
-// times the kernel spectrum, inverse FFT along y; rows 0 .. ny - 1 to
-// Y[k][.].  The components of one row are summed in list order (their
+// times the kernel spectrum, inverse FFT along y; rows 0 .. ny - 1 to Y
+// (pair-major, below).  The components of one row are summed in list order (their
 // chain), so the result is deterministic.  The kernel spectrum's column
 // arrives by one bulk copy into shared memory, issued a column ahead, so
 // its load overlaps the previous column's transforms.
@@ -539,102 +548,119 @@ __global__ void __launch_bounds__(kFftMaxThreads, 1)
       bulk_load(kst, Kspec + (int64_t)(k + gridDim.x) * Ly, kbytes, &kbar);
     }
     fft_1d<P2>(fbuf, ay, twy, true);
-    float2* ycol = Y + (int64_t)k * ny;
+    // pair-major: row q's bin k at ((q / 2) ncols + k) 2 + q % 2, so a pair
+    // of rows is one contiguous run for the row pass
 #pragma unroll
     for (int u = 0; u < kFftValsPerThread; ++u) {
       const int q = threadIdx.x + u * blockDim.x;
-      if (q < ny) ycol[q] = fbuf[fpad(q)];
+      if (q < ny) Y[(((int64_t)(q >> 1) * ncols + k) << 1) + (q & 1)] = fbuf[fpad(q)];
     }
     __syncthreads();
   }
 }
 
-// Rows q0 = 2b and q1 = 2b + 1: their x-axis spectra Y[.][q] extended to
-// length Lx and combined as Z = Y_q0 + i Y_q1; the inverse FFT gives row q0
-// in the real and row q1 in the imaginary part.  R <- R0 - S, R0 <- R on
-// columns 0 .. nx - 1; each tile's peak of these rows into the next-round
-// key; the last block closes the round.  Every thread issues all of its
-// global loads before it uses any (at most kFftValsPerThread / 2 spectrum
-// bins and image columns a thread).
+// Pairs of rows b = blockIdx.x, blockIdx.x + gridDim.x, ... (one CTA per
+// SM), rows q0 = 2b and q1 = 2b + 1: their x-axis spectra (one contiguous
+// run of Y) extended to length Lx and combined as Z = Y_q0 + i Y_q1; the
+// inverse FFT gives row q0 in the real and row q1 in the imaginary part.
+// R <- R0 - S, R0 <- R on columns 0 .. nx - 1; each tile's peak of these
+// rows into the next-round key; the last CTA closes the round.  The pair's
+// spectra and its R0 rows (when nx is a multiple of 4) arrive by bulk
+// copies into shared memory issued a pair ahead, overlapping the current
+// pair's transform.
 template <bool P2>
 __global__ void __launch_bounds__(kFftMaxThreads, 1)
     fft_rows_kernel(PlanDev d, FftAxis ax, const float2* __restrict__ twx,
                     const float2* __restrict__ Y, float* __restrict__ R0, int parity,
-                    int n_blocks) {
+                    uint64_t limit_ns) {
   extern __shared__ __align__(128) unsigned char fsm[];
-  float2* fbuf = reinterpret_cast<float2*>(fsm);
-  const int Lx = ax.L;
+  const int Lx = ax.L, ncols = Lx / 2 + 1, nx = d.nx, ny = d.ny;
+  const int npairs = (ny + 1) / 2;
+  float2* ystg = reinterpret_cast<float2*>(fsm);                    // 2 ncols
+  float* rstg = reinterpret_cast<float*>(ystg + 2 * ((ncols + 1) & ~1));  // 2 nx
+  float2* fbuf = reinterpret_cast<float2*>(rstg + 2 * ((nx + 3) & ~3));
   int32_t* s_cnt = reinterpret_cast<int32_t*>(fbuf + fpad(Lx) + 1);
   int32_t* s_pre = s_cnt + d.T;
   __shared__ uint64_t s_warp[2][32];
-  constexpr int kHalf = kFftValsPerThread / 2;  // Lx / 2 + 1 <= kHalf * blockDim.x + 1
-  const int q0 = 2 * blockIdx.x, q1 = q0 + 1;
-  const bool has1 = q1 < d.ny;
-  const bool live = *(volatile int32_t*)&d.st->status == 0;
+  __shared__ __align__(8) uint64_t ybar, rbar;
+  __shared__ int s_abort;
+  const bool bulk_r = (nx & 3) == 0;
+  const uint32_t ybytes = (uint32_t)ncols * 16u;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int nthr = blockDim.x;
-  if (live) {
-    float2 y0[kHalf + 1], y1[kHalf + 1];
-#pragma unroll
-    for (int u = 0; u <= kHalf; ++u) {
-      const int k = threadIdx.x + u * nthr;
-      y0[u] = y1[u] = make_float2(0.f, 0.f);
-      if (k <= Lx / 2) {
-        y0[u] = Y[(int64_t)k * d.ny + q0];
-        if (has1) y1[u] = Y[(int64_t)k * d.ny + q1];
-      }
+  auto issue = [&](int b) {  // thread 0: the pair's spectra and R0 rows
+    const int rows = 2 * b + 1 < ny ? 2 : 1;
+    ptx::mbar_arrive_expect_tx(&ybar, ybytes);
+    bulk_load(ystg, Y + (int64_t)b * ncols * 2, ybytes, &ybar);
+    if (bulk_r) {
+      ptx::mbar_arrive_expect_tx(&rbar, (uint32_t)(rows * nx) * 4u);
+      bulk_load(rstg, R0 + (int64_t)2 * b * nx, (uint32_t)(rows * nx) * 4u, &rbar);
     }
-#pragma unroll
-    for (int u = 0; u <= kHalf; ++u) {
-      const int k = threadIdx.x + u * nthr;
-      if (k <= Lx / 2) {
-        float2 a = y0[u], b = y1[u];
-        const bool edge = k == 0 || 2 * k == Lx;  // real in exact arithmetic
-        if (edge) a.y = b.y = 0.f;
-        fbuf[fpad(k)] = make_float2(a.x - b.y, a.y + b.x);
-        if (!edge) fbuf[fpad(Lx - k)] = make_float2(a.x + b.y, b.x - a.y);
-      }
+  };
+  if (threadIdx.x == 0) {
+    s_abort = *(volatile int32_t*)&d.st->status != 0;
+    ptx::mbar_init(&ybar, 1);
+    ptx::mbar_init(&rbar, 1);
+    ptx::fence_barrier_init();
+    if (!s_abort && (int)blockIdx.x < npairs) issue(blockIdx.x);
+  }
+  __syncthreads();
+  uint32_t phase = 0;
+  for (int b = blockIdx.x; b < npairs && !s_abort; b += gridDim.x) {
+    const int q0 = 2 * b, q1 = q0 + 1;
+    const bool has1 = q1 < ny;
+    if (!ptx::mbar_wait_bounded(&ybar, phase, limit_ns)) {
+      atomicOr(&d.st->status, ST_TIMEOUT);
+      s_abort = 1;
+    }
+    __syncthreads();
+    if (s_abort) break;
+    for (int k = threadIdx.x; k < ncols; k += nthr) {
+      float2 a = ystg[2 * k], c = has1 ? ystg[2 * k + 1] : make_float2(0.f, 0.f);
+      const bool edge = k == 0 || 2 * k == Lx;  // real in exact arithmetic
+      if (edge) a.y = c.y = 0.f;
+      fbuf[fpad(k)] = make_float2(a.x - c.y, a.y + c.x);
+      if (!edge) fbuf[fpad(Lx - k)] = make_float2(a.x + c.y, c.x - a.y);
     }
     __syncthreads();
     fft_1d<P2>(fbuf, ax, twx, true);
-    // R <- R0 - S for this thread's columns (all loads first), results back
-    // into fbuf as (row q0, row q1) for the per-tile peak scans
-    float r0v[kHalf], r1v[kHalf];
-    const int64_t g0 = (int64_t)q0 * d.nx;
-#pragma unroll
-    for (int u = 0; u < kHalf; ++u) {
-      const int x = threadIdx.x + u * nthr;
-      r0v[u] = r1v[u] = 0.f;
-      if (x < d.nx) {
-        r0v[u] = R0[g0 + x];
-        if (has1) r1v[u] = R0[g0 + d.nx + x];
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < kHalf; ++u) {
-      const int x = threadIdx.x + u * nthr;
-      if (x < d.nx) {
-        const float2 sv = fbuf[fpad(x)];
-        const float a = r0v[u] - sv.x, b = r1v[u] - sv.y;
-        d.R[g0 + x] = a;
-        R0[g0 + x] = a;
-        if (has1) {
-          d.R[g0 + d.nx + x] = b;
-          R0[g0 + d.nx + x] = b;
-        }
-        fbuf[fpad(x)] = make_float2(a, b);
-      }
+    // R <- R0 - S; the results back into fbuf as (row q0, row q1)
+    if (bulk_r && !ptx::mbar_wait_bounded(&rbar, phase, limit_ns)) {
+      atomicOr(&d.st->status, ST_TIMEOUT);
+      s_abort = 1;
     }
     __syncthreads();
+    if (s_abort) break;
+    const int64_t g0 = (int64_t)q0 * nx;
+    for (int x = threadIdx.x; x < nx; x += nthr) {
+      const float r0 = bulk_r ? rstg[x] : R0[g0 + x];
+      const float r1 = has1 ? (bulk_r ? rstg[nx + x] : R0[g0 + nx + x]) : 0.f;
+      const float2 sv = fbuf[fpad(x)];
+      const float a = r0 - sv.x, c = r1 - sv.y;
+      d.R[g0 + x] = a;
+      R0[g0 + x] = a;
+      if (has1) {
+        d.R[g0 + nx + x] = c;
+        R0[g0 + nx + x] = c;
+      }
+      fbuf[fpad(x)] = make_float2(a, c);
+    }
+    __syncthreads();
+    phase ^= 1u;
+    // both staging buffers are free: the next pair's copies
+    if (threadIdx.x == 0 && b + (int)gridDim.x < npairs) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(b + gridDim.x);
+    }
     // tile rows of q0 and q1
     int t_row0 = 0, t_row1 = 0;
     for (int i = 0; i < d.ty; ++i) {
-      const Rect r = tile_rect(i * d.tx, d.ny, d.nx, d.ty, d.tx);
+      const Rect r = tile_rect(i * d.tx, ny, nx, d.ty, d.tx);
       if (q0 >= r.y0 && q0 < r.y1) t_row0 = i;
       if (has1 && q1 >= r.y0 && q1 < r.y1) t_row1 = i;
     }
     for (int j = 0; j < d.tx; ++j) {
-      const Rect rc = tile_rect(j, d.ny, d.nx, d.ty, d.tx);
+      const Rect rc = tile_rect(j, ny, nx, d.ty, d.tx);
       float b0a = -1.f, b0v = 0.f, b1a = -1.f, b1v = 0.f;
       int b0i = 0x7fffffff, b1i = 0x7fffffff;
       for (int x = rc.x0 + threadIdx.x; x < rc.x1; x += nthr) {
@@ -647,7 +673,7 @@ __global__ void __launch_bounds__(kFftMaxThreads, 1)
           b0v = v.x;
         }
         if (has1) {
-          const int i1 = i0 + d.nx;
+          const int i1 = i0 + nx;
           const float a1 = fabsf(v.y);
           if (a1 > b1a || (a1 == b1a && i1 < b1i)) {
             b1a = a1;
@@ -679,7 +705,7 @@ __global__ void __launch_bounds__(kFftMaxThreads, 1)
       __syncthreads();
     }
   }
-  close_round_if_last(d, parity, n_blocks, s_cnt, s_pre);
+  close_round_if_last(d, parity, gridDim.x, s_cnt, s_pre);
 }
 
 }  // namespace
@@ -732,7 +758,7 @@ bool fft_axis_init(FftAxis* a, int L) {
 }
 
 size_t fft_comps_bytes(int64_t n_max) {
-  return sizeof(int4) * (size_t)(1 + n_max) + sizeof(int) * (size_t)n_max;
+  return sizeof(int4) * (size_t)(1 + n_max) + 2 * sizeof(int) * (size_t)n_max;
 }
 
 size_t fft_smem_bytes(int L) { return sizeof(float2) * ((size_t)L + (size_t)L / 32 + 2); }
@@ -787,9 +813,10 @@ cudaError_t fft_feedback_round(const PlanDev& d, const FftAxis& ay, const FftAxi
                                float2* Y, int4* comps, float* R0, int parity, cudaStream_t s) {
   const int64_t n_max = (int64_t)d.T * d.cap_round;
   int* lead = reinterpret_cast<int*>(comps + 1 + n_max);
-  const size_t csmem = sizeof(int32_t) * (2 * (size_t)d.T + 1 +
+  int* bucket = lead + n_max;
+  const size_t csmem = sizeof(int32_t) * (2 * (size_t)d.T + 2 + 2 * (size_t)d.ny +
                                           (size_t)std::min<int64_t>(n_max, kCompSmem));
-  fft_comp_list_kernel<<<1, kCompThreads, csmem, s>>>(d, comps, lead);
+  fft_comp_list_kernel<<<1, kCompThreads, csmem, s>>>(d, comps, lead, bucket);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int ncols = ax.L / 2 + 1;
@@ -803,12 +830,15 @@ cudaError_t fft_feedback_round(const PlanDev& d, const FftAxis& ay, const FftAxi
                                                      kFftWaitNs);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int nb = (d.ny + 1) / 2;
-  const size_t smem = fft_smem_bytes(ax.L) + sizeof(int32_t) * (2 * (size_t)d.T + 1);
+  const int npairs = (d.ny + 1) / 2;
+  const int rgrid = std::min(npairs, fft_sm_count());
+  const size_t smem = sizeof(float2) * 2 * (size_t)((ncols + 1) & ~1) +
+                      sizeof(float) * 2 * (size_t)((d.nx + 3) & ~3) + fft_smem_bytes(ax.L) +
+                      sizeof(int32_t) * (2 * (size_t)d.T + 1);
   if (ax.p2)
-    fft_rows_kernel<true><<<nb, ax.nthr, smem, s>>>(d, ax, twx, Y, R0, parity, nb);
+    fft_rows_kernel<true><<<rgrid, ax.nthr, smem, s>>>(d, ax, twx, Y, R0, parity, kFftWaitNs);
   else
-    fft_rows_kernel<false><<<nb, ax.nthr, smem, s>>>(d, ax, twx, Y, R0, parity, nb);
+    fft_rows_kernel<false><<<rgrid, ax.nthr, smem, s>>>(d, ax, twx, Y, R0, parity, kFftWaitNs);
   return cudaGetLastError();
 }
 

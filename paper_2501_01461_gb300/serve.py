@@ -64,7 +64,7 @@ def footprint_bytes(n: int, psf_shape, niter: int, tiles=(1, 1), K: int = 0,
         L = _fft_size(2 * n - 1)
         # kernel spectrum, the round's column work area, the component list,
         # twiddle tables and the round-start residual
-        b += 8 * L * (L // 2 + 1) + 8 * n * (L // 2 + 1) + 20 * T * max(cap, 1) + 16 \
+        b += 8 * L * (L // 2 + 1) + 8 * (n + n % 2) * (L // 2 + 1) + 24 * T * max(cap, 1) + 16 \
             + 2 * 8 * _twiddles(L) + 4 * n * n
     return int(b)
 

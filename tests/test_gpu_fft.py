@@ -24,6 +24,8 @@ CASES = [
     (256, 256, (512, 512), (2, 2), 20, 1200),
     (200, 260, (400, 520), (3, 2), 15, 1500),    # non-square, ragged tiles
     (192, 192, (160, 200), (2, 3), 10, 600),     # PSF smaller than 2N: clipped kernel
+    (195, 230, (390, 460), (3, 2), 12, 900),     # odd rows (a last half pair), nx not a multiple of 4
+    (1024, 1024, (2048, 2048), (2, 2), 25, 1000),  # 2048-point radix-16 axes
 ]
 
 

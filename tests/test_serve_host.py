@@ -14,7 +14,7 @@ def test_fft_footprint_counts_the_grids():
     # components (4 tiles x K 50), both twiddle tables, the round-start residual
     # twiddles of 2048 = 8 x 8 x 8 x 4: the L roots, then r Ns entries a stage
     tw = L + 8 + 64 + 512 + 2048
-    assert f - g == (8 * L * (L // 2 + 1) + 8 * 1024 * (L // 2 + 1) + 20 * 4 * 50 + 16
+    assert f - g == (8 * L * (L // 2 + 1) + 8 * 1024 * (L // 2 + 1) + 24 * 4 * 50 + 16
                      + 2 * 8 * tw + 4 * 1024 * 1024)
     assert serve.footprint_bytes(512, (1024, 1024), 100, (1, 1), 50, cg.FB_FFT) == \
         serve.footprint_bytes(512, (1024, 1024), 100, (1, 1), 50)
