@@ -244,14 +244,25 @@ __device__ __forceinline__ void dft16(float2 (&x)[16], bool inv) {
   }
 }
 
-template <int L, int NS>
-__device__ __forceinline__ void p2_stage16(float2* buf, const float2* __restrict__ tws, bool inv) {
+// The default input of a transform's first stage and output of its last:
+// the shared-memory buffer itself.  Kernels pass their own to fuse the pass
+// before the transform into its first loads, or the pass after it into its
+// last stores.
+struct BufIO {
+  float2* buf;
+  __device__ __forceinline__ float2 load(int i) const { return buf[fpad(i)]; }
+  __device__ __forceinline__ void store(int i, float2 v) const { buf[fpad(i)] = v; }
+};
+
+template <int L, int NS, bool FIRST, bool LAST, class Pro, class Epi>
+__device__ __forceinline__ void p2_stage16(float2* buf, const float2* __restrict__ tws, bool inv,
+                                           const Pro& pro, const Epi& epi) {
   constexpr int NB = L / 16;  // one butterfly a thread
   const int j = threadIdx.x;
   const int k = j & (NS - 1);
   float2 x[16];
 #pragma unroll
-  for (int r = 0; r < 16; ++r) x[r] = buf[fpad(j + r * NB)];
+  for (int r = 0; r < 16; ++r) x[r] = FIRST ? pro.load(j + r * NB) : buf[fpad(j + r * NB)];
   if (NS > 1) {
     const float4 a = __ldg(reinterpret_cast<const float4*>(tws) + 2 * k);
     const float4 c = __ldg(reinterpret_cast<const float4*>(tws) + 2 * k + 1);
@@ -274,14 +285,20 @@ __device__ __forceinline__ void p2_stage16(float2* buf, const float2* __restrict
   dft16(x, inv);
   const int base = (j - k) * 16 + k;
 #pragma unroll
-  for (int r = 0; r < 16; ++r) buf[fpad(base + r * NS)] = x[r];
+  for (int r = 0; r < 16; ++r) {
+    if (LAST)
+      epi.store(base + r * NS, x[r]);
+    else
+      buf[fpad(base + r * NS)] = x[r];
+  }
   __syncthreads();
 }
 
 // Last stage of radix R = L / NS < 16: 16 / R butterflies a thread; twiddles
 // exp(-2 pi i r k / L) at r NS + k.
-template <int L, int NS>
-__device__ __forceinline__ void p2_tail(float2* buf, const float2* __restrict__ tws, bool inv) {
+template <int L, int NS, class Epi>
+__device__ __forceinline__ void p2_tail(float2* buf, const float2* __restrict__ tws, bool inv,
+                                        const Epi& epi) {
   constexpr int R = L / NS, NB = L / R, NT = L / 16, MB = 16 / R;
   float2 v[MB][R];
 #pragma unroll
@@ -304,19 +321,35 @@ __device__ __forceinline__ void p2_tail(float2* buf, const float2* __restrict__ 
     Dft<R>::run(v[b], inv, nullptr, 0);
     const int base = (j - k) * R + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) buf[fpad(base + r * NS)] = v[b][r];
+    for (int r = 0; r < R; ++r) epi.store(base + r * NS, v[b][r]);
   }
   __syncthreads();
 }
 
-template <int L, int NS, int S>
+// Radix-16 stages, then a smaller last one if L is not a power of 16 (the
+// first stage is always radix 16: L >= 2048).  pro feeds the first stage,
+// epi takes the last stage's outputs.
+template <int L, int NS, int S, class Pro, class Epi>
 __device__ __forceinline__ void p2_fft(float2* buf, const FftAxis& ax, const float2* __restrict__ tw,
-                                       bool inv) {
+                                       bool inv, const Pro& pro, const Epi& epi) {
   if constexpr (NS * 16 <= L) {
-    p2_stage16<L, NS>(buf, tw + ax.tw_off[S], inv);
-    p2_fft<L, NS * 16, S + 1>(buf, ax, tw, inv);
+    constexpr bool last = NS * 16 == L;
+    p2_stage16<L, NS, NS == 1, last>(buf, tw + ax.tw_off[S], inv, pro, epi);
+    p2_fft<L, NS * 16, S + 1>(buf, ax, tw, inv, pro, epi);
   } else if constexpr (NS < L) {
-    p2_tail<L, NS>(buf, tw + ax.tw_off[S], inv);
+    p2_tail<L, NS>(buf, tw + ax.tw_off[S], inv, epi);
+  }
+}
+
+// The radix-16 transform of one length with fused first loads / last stores.
+template <class Pro, class Epi>
+__device__ __forceinline__ void fft_p2_io(float2* buf, const FftAxis& ax,
+                                          const float2* __restrict__ tw, bool inv, const Pro& pro,
+                                          const Epi& epi) {
+  switch (ax.L) {
+    case 8192: p2_fft<8192, 1, 0>(buf, ax, tw, inv, pro, epi); return;
+    case 4096: p2_fft<4096, 1, 0>(buf, ax, tw, inv, pro, epi); return;
+    default: p2_fft<2048, 1, 0>(buf, ax, tw, inv, pro, epi); return;
   }
 }
 
@@ -329,11 +362,8 @@ template <bool P2>
 __device__ __forceinline__ void fft_1d(float2* buf, const FftAxis& ax,
                                        const float2* __restrict__ tw, bool inv) {
   if constexpr (P2) {
-    switch (ax.L) {
-      case 8192: p2_fft<8192, 1, 0>(buf, ax, tw, inv); return;
-      case 4096: p2_fft<4096, 1, 0>(buf, ax, tw, inv); return;
-      default: p2_fft<2048, 1, 0>(buf, ax, tw, inv); return;
-    }
+    fft_p2_io(buf, ax, tw, inv, BufIO{buf}, BufIO{buf});
+    return;
   }
   int Ns = 1;
   for (int s = 0; s < ax.nrad; ++s) {
@@ -479,6 +509,27 @@ __global__ void __launch_bounds__(kCompThreads)
 // chain), so the result is deterministic.  The kernel spectrum's column
 // arrives by one bulk copy into shared memory, issued a column ahead, so
 // its load overlaps the previous column's transforms.
+// Fused first loads / last stores of the radix-16 path (see BufIO).
+struct RowsIn {  // the column's input: component rows from rowv, zero elsewhere
+  const float2* rowv;
+  int ny;
+  __device__ __forceinline__ float2 load(int i) const {
+    return i < ny ? rowv[i] : make_float2(0.f, 0.f);
+  }
+};
+struct TimesK {  // the forward transform's outputs times the spectrum column
+  float2* buf;
+  const float2* kst;
+  __device__ __forceinline__ void store(int i, float2 v) const { buf[fpad(i)] = cmul(v, kst[i]); }
+};
+struct ToY {  // the inverse transform's image rows, pair-major into Y
+  float2* Y;
+  int ny, ncols, k;
+  __device__ __forceinline__ void store(int q, float2 v) const {
+    if (q < ny) Y[(((int64_t)(q >> 1) * ncols + k) << 1) + (q & 1)] = v;
+  }
+};
+
 template <bool P2>
 __global__ void __launch_bounds__(kFftMaxThreads, 1)
     fft_cols_kernel(PlanDev d, FftAxis ay, int Lx, const int4* __restrict__ comps,
@@ -489,6 +540,7 @@ __global__ void __launch_bounds__(kFftMaxThreads, 1)
   const int Ly = ay.L, ny = d.ny, ncols = Lx / 2 + 1;
   float2* kst = reinterpret_cast<float2*>(fsm);  // the spectrum column, Ly
   float2* fbuf = kst + Ly;                        // the transform, padded
+  float2* rowv = fbuf + fpad(Ly) + 2;             // radix-16 path: the component rows' inputs
   __shared__ __align__(8) uint64_t kbar;
   __shared__ int s_abort;
   const uint32_t kbytes = (uint32_t)Ly * (uint32_t)sizeof(float2);
@@ -502,16 +554,20 @@ __global__ void __launch_bounds__(kFftMaxThreads, 1)
       bulk_load(kst, Kspec + (int64_t)blockIdx.x * Ly, kbytes, &kbar);
     }
   }
+  if (P2)  // rows without components stay zero for every column
+    for (int q = threadIdx.x; q < ny; q += blockDim.x) rowv[q] = make_float2(0.f, 0.f);
   __syncthreads();
   if (s_abort) return;  // uniform: written before the barrier
   uint32_t phase = 0;
   for (int k = blockIdx.x; k < ncols; k += gridDim.x) {
+    if (!P2) {
 #pragma unroll
-    for (int u = 0; u < kFftValsPerThread; ++u) {
-      const int i = threadIdx.x + u * blockDim.x;
-      if (i < Ly) fbuf[fpad(i)] = make_float2(0.f, 0.f);
+      for (int u = 0; u < kFftValsPerThread; ++u) {
+        const int i = threadIdx.x + u * blockDim.x;
+        if (i < Ly) fbuf[fpad(i)] = make_float2(0.f, 0.f);
+      }
+      __syncthreads();
     }
-    __syncthreads();
     for (int i = threadIdx.x; i < rows; i += blockDim.x) {
       int j = lead[i];
       const int y = comps[1 + j].x;
@@ -523,7 +579,30 @@ __global__ void __launch_bounds__(kFftMaxThreads, 1)
         acc = cadd(acc, make_float2(f * w.x, f * w.y));
         j = e.w;
       }
-      fbuf[fpad(y)] = acc;
+      if (P2)
+        rowv[y] = acc;
+      else
+        fbuf[fpad(y)] = acc;
+    }
+    if (P2) {
+      // the spectrum column (every thread waits, bounded), then the forward
+      // transform from the rows, times the column in its last stage
+      if (!ptx::mbar_wait_bounded(&kbar, phase, limit_ns)) {
+        atomicOr(&d.st->status, ST_TIMEOUT);
+        s_abort = 1;
+      }
+      phase ^= 1u;
+      __syncthreads();
+      if (s_abort) return;
+      fft_p2_io(fbuf, ay, twy, false, RowsIn{rowv, ny}, TimesK{fbuf, kst});
+      // the staging buffer is free: fetch the next column's spectrum
+      if (threadIdx.x == 0 && k + (int)gridDim.x < ncols) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        ptx::mbar_arrive_expect_tx(&kbar, kbytes);
+        bulk_load(kst, Kspec + (int64_t)(k + gridDim.x) * Ly, kbytes, &kbar);
+      }
+      fft_p2_io(fbuf, ay, twy, true, BufIO{fbuf}, ToY{Y, ny, ncols, k});
+      continue;
     }
     __syncthreads();
     fft_1d<P2>(fbuf, ay, twy, false);
@@ -558,6 +637,41 @@ __global__ void __launch_bounds__(kFftMaxThreads, 1)
     __syncthreads();
   }
 }
+
+struct PairIn {  // Z = Y_q0 + i Y_q1 over the whole length, from the staged half spectra
+  const float2* ystg;
+  int L;
+  bool has1;
+  __device__ __forceinline__ float2 load(int i) const {
+    const bool lo = 2 * i <= L;
+    const int k = lo ? i : L - i;
+    float2 a = ystg[2 * k], c = has1 ? ystg[2 * k + 1] : make_float2(0.f, 0.f);
+    if (k == 0 || 2 * k == L) a.y = c.y = 0.f;  // real in exact arithmetic
+    return lo ? make_float2(a.x - c.y, a.y + c.x) : make_float2(a.x + c.y, c.x - a.y);
+  }
+};
+struct PairOut {  // R <- R0 - S for the pair's image columns; (R q0, R q1) back to buf
+  float2* buf;
+  float* R;
+  float* R0;
+  const float* rstg;
+  int64_t g0;
+  int nx;
+  bool bulk, has1;
+  __device__ __forceinline__ void store(int x, float2 v) const {
+    if (x >= nx) return;
+    const float r0 = bulk ? rstg[x] : R0[g0 + x];
+    const float r1 = has1 ? (bulk ? rstg[nx + x] : R0[g0 + nx + x]) : 0.f;
+    const float a = r0 - v.x, c = r1 - v.y;
+    R[g0 + x] = a;
+    R0[g0 + x] = a;
+    if (has1) {
+      R[g0 + nx + x] = c;
+      R0[g0 + nx + x] = c;
+    }
+    buf[fpad(x)] = make_float2(a, c);
+  }
+};
 
 // Pairs of rows b = blockIdx.x, blockIdx.x + gridDim.x, ... (one CTA per
 // SM), rows q0 = 2b and q1 = 2b + 1: their x-axis spectra (one contiguous
@@ -613,26 +727,38 @@ __global__ void __launch_bounds__(kFftMaxThreads, 1)
       atomicOr(&d.st->status, ST_TIMEOUT);
       s_abort = 1;
     }
-    __syncthreads();
-    if (s_abort) break;
-    for (int k = threadIdx.x; k < ncols; k += nthr) {
-      float2 a = ystg[2 * k], c = has1 ? ystg[2 * k + 1] : make_float2(0.f, 0.f);
-      const bool edge = k == 0 || 2 * k == Lx;  // real in exact arithmetic
-      if (edge) a.y = c.y = 0.f;
-      fbuf[fpad(k)] = make_float2(a.x - c.y, a.y + c.x);
-      if (!edge) fbuf[fpad(Lx - k)] = make_float2(a.x + c.y, c.x - a.y);
-    }
-    __syncthreads();
-    fft_1d<P2>(fbuf, ax, twx, true);
-    // R <- R0 - S; the results back into fbuf as (row q0, row q1)
-    if (bulk_r && !ptx::mbar_wait_bounded(&rbar, phase, limit_ns)) {
+    if (P2 && bulk_r && !ptx::mbar_wait_bounded(&rbar, phase, limit_ns)) {
       atomicOr(&d.st->status, ST_TIMEOUT);
       s_abort = 1;
     }
     __syncthreads();
     if (s_abort) break;
     const int64_t g0 = (int64_t)q0 * nx;
-    for (int x = threadIdx.x; x < nx; x += nthr) {
+    if (P2) {
+      // the pair's spectrum feeds the first stage, the subtraction takes the
+      // last stage's outputs
+      fft_p2_io(fbuf, ax, twx, true, PairIn{ystg, Lx, has1},
+                PairOut{fbuf, d.R, R0, rstg, g0, nx, bulk_r, has1});
+    }
+    for (int k = threadIdx.x; k < ncols && !P2; k += nthr) {
+      float2 a = ystg[2 * k], c = has1 ? ystg[2 * k + 1] : make_float2(0.f, 0.f);
+      const bool edge = k == 0 || 2 * k == Lx;  // real in exact arithmetic
+      if (edge) a.y = c.y = 0.f;
+      fbuf[fpad(k)] = make_float2(a.x - c.y, a.y + c.x);
+      if (!edge) fbuf[fpad(Lx - k)] = make_float2(a.x + c.y, c.x - a.y);
+    }
+    if (!P2) {
+      __syncthreads();
+      fft_1d<P2>(fbuf, ax, twx, true);
+      // R <- R0 - S; the results back into fbuf as (row q0, row q1)
+      if (bulk_r && !ptx::mbar_wait_bounded(&rbar, phase, limit_ns)) {
+        atomicOr(&d.st->status, ST_TIMEOUT);
+        s_abort = 1;
+      }
+      __syncthreads();
+      if (s_abort) break;
+    }
+    for (int x = threadIdx.x; x < nx && !P2; x += nthr) {
       const float r0 = bulk_r ? rstg[x] : R0[g0 + x];
       const float r1 = has1 ? (bulk_r ? rstg[nx + x] : R0[g0 + nx + x]) : 0.f;
       const float2 sv = fbuf[fpad(x)];
@@ -821,7 +947,8 @@ cudaError_t fft_feedback_round(const PlanDev& d, const FftAxis& ay, const FftAxi
   if (e != cudaSuccess) return e;
   const int ncols = ax.L / 2 + 1;
   const int grid = std::min(ncols, fft_sm_count());
-  const size_t cs = sizeof(float2) * (size_t)ay.L + fft_smem_bytes(ay.L);
+  const size_t cs = sizeof(float2) * (size_t)ay.L + fft_smem_bytes(ay.L) +
+                    sizeof(float2) * (size_t)d.ny;
   if (ay.p2)
     fft_cols_kernel<true><<<grid, ay.nthr, cs, s>>>(d, ay, ax.L, comps, lead, twx, twy, Kspec, Y,
                                                     kFftWaitNs);
