@@ -1,12 +1,15 @@
 // Many deconvolutions on one GPU at once: fixed batches (clean_batch_*) and
 // continuous batching for serving (clean_server_*).
 //
-// Every resident image's round runs in shared launches: minor-loop launches
-// grouped by kernel, CTAs per tile and residual placement (one CTA per small
-// tile, a thread-block cluster of up to 16 CTAs per large one, largest tiles
-// first; images whose residual and PSF allow 2-D TMA boxes take the TMA
-// pipeline, the others plain loads), then one feedback launch over every
-// image's blocks.  Each image
+// Every resident image's round runs in shared launches.  The minor loops of
+// all images whose residual and PSF allow 2-D TMA boxes run in ONE
+// persistent launch (one CTA per SM working through a schedule of waves:
+// each tile of each image is a unit of G CTAs in one wave, exchanging its
+// peaks through the bounded grid exchange; largest tiles first); the other
+// images' minor loops run in launches grouped by CTAs per tile and residual
+// placement (plain loads, one CTA per small tile, a thread-block cluster per
+// large one).  Then one feedback launch covers every image's blocks (two if
+// some images need the plain-load feedback).  Each image
 // keeps its own round phase (it may have joined later), its own budgets,
 // peaks and component list, so its results are bit for bit those of its own
 // clean_plan + clean_run.  Images that finish leave the work lists; new ones
@@ -31,6 +34,11 @@ using namespace cleangb;
 namespace {
 
 constexpr int64_t kGroupSmemMax = 200 * 1024;  // resident rows per CTA
+constexpr int kMaxUnitG = 16;                   // CTAs per tile in the persistent minor loop
+// dynamic shared memory floor of the persistent launch: above half an SM, so
+// each SM holds one CTA (units that keep residual chunks in tensor memory
+// take all of its columns)
+constexpr int kPersistSmemMin = 116 * 1024;
 
 struct Job {
   clean_plan_t plan = nullptr;
@@ -40,6 +48,9 @@ struct Job {
   // residual and PSF box maps of the batched minor-loop pipeline
   CUtensorMap rmap{}, pmap{};
   bool pipe = false;
+  // grid-exchange slots of the persistent minor loop: 2 sets x T tiles x
+  // kMaxUnitG CTAs, owned by the engine
+  uint64_t* bkeys = nullptr;
   bool fft = false;  // feedback by FFT convolution (the job's own launches)
   int64_t id = 0;
   int slot = 0;
@@ -74,6 +85,12 @@ struct clean_engine_s {
   std::vector<Group> groups;
   int n_work = 0, n_tma = 0, n_gather = 0, blocks_tma = 0, blocks_plain = 0, max_T = 1;
   std::vector<int> fft_work;            // work positions of FFT-feedback jobs
+  // persistent minor loop of the pipelined images (n_waves = 0: none)
+  BatchUnitItem* d_uitems = nullptr;
+  int uitems_cap = 0;
+  int2* d_units = nullptr;
+  int units_cap = 0;
+  int n_waves = 0, p_grid = 0, p_smem = 0;
   std::vector<int> work_jobs;           // job index of each work position
   bool dirty = true;                    // work lists need a rebuild
   int round = 0;                        // rounds launched so far (global)
@@ -110,7 +127,12 @@ void engine_free(clean_engine_s* e) {
   cudaDeviceSynchronize();
   drop_graphs(e);
   if (e->cap_stream) cudaStreamDestroy(e->cap_stream);
-  for (Job& j : e->jobs) clean_destroy(j.plan);
+  for (Job& j : e->jobs) {
+    clean_destroy(j.plan);
+    cudaFree(j.bkeys);
+  }
+  cudaFree(e->d_uitems);
+  cudaFree(e->d_units);
   cudaFree(e->d_states);
   cudaFree(e->d_plans);
   cudaFree(e->d_items);
@@ -155,6 +177,10 @@ int engine_start(clean_engine_s* e, Job& j, const float* d_dirty, cudaStream_t s
   ++e->kernel_launches;
   if (err == cudaSuccess) err = launch_first_level(j.dev, s);
   if (err == cudaSuccess && j.fft) err = plan_fft_start(j.plan, j.dev, s);
+  // the persistent minor loop's exchange slots start marked (bit 63 set), as
+  // in a single plan's run; set-up zeroed the exchange counts
+  if (err == cudaSuccess && j.bkeys)
+    err = cudaMemsetAsync(j.bkeys, 0x80, sizeof(uint64_t) * 2 * (size_t)j.dev.T * kMaxUnitG, s);
   if (err != cudaSuccess) return eng_fail(e, CLEAN_ERR_CUDA);
   std::memset(&e->h_states[j.slot], 0, sizeof(DevState));
   e->h_states[j.slot].active = 1;  // refreshed at the next status read
@@ -183,6 +209,15 @@ int engine_register(clean_engine_s* e, const clean_params* p, const float* d_psf
            p->psf_nx >= kBatchBoxW &&
            make_box_tensor_map(&j.pmap, d_psf, p->psf_ny, p->psf_nx, kBatchBoxW, kBatchBoxRows) &&
            make_box_tensor_map(&j.rmap, j.dev.R, p->ny, p->nx, kBatchBoxW, kBatchBoxRows);
+  if (j.pipe) {
+    if (cudaMalloc(&j.bkeys, sizeof(uint64_t) * 2 * (size_t)j.dev.T * kMaxUnitG) != cudaSuccess) {
+      cudaGetLastError();
+      e->free_slots.push_back(j.slot);
+      clean_destroy(j.plan);
+      return CLEAN_ERR_OOM;
+    }
+    j.dev.gkeys = j.bkeys;
+  }
   j.id = e->next_id++;
   j.finished = true;  // not running until started
   e->jobs.push_back(j);
@@ -280,9 +315,45 @@ int engine_rebuild(clean_engine_s* e, cudaStream_t s) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, e->device);
     fast = ctas <= sms;
   }
+  // the pipelined images' minor loops go to the persistent launch when it can
+  // be resident
+  const int p_grid = minor_batch_persistent_grid(kPersistSmemMin);
+  std::vector<BatchUnitItem> uitems;
+  std::vector<int64_t> upx;  // pixels of each unit item's tile (scheduling order)
+  int p_smem = kPersistSmemMin;
   e->blocks_tma = e->blocks_plain = 0;
   for (int w = 0; w < (int)work.size(); ++w) {
     const Job& j = e->jobs[work[w]];
+    if (p_grid > 0 && j.pipe) {
+      // one G for the whole image (its tiles share the exchange slots), the
+      // largest any of its tiles asks for
+      int Gi = 1;
+      for (int t = 0; t < j.dev.T; ++t) {
+        const Rect r = tile_rect(t, j.dev.ny, j.dev.nx, j.dev.ty, j.dev.tx);
+        int g = 1, res = 0, rows = 0;
+        pipe_tile_group(r.y1 - r.y0, r.x1 - r.x0, fast, &g, &res, &rows);
+        Gi = std::max(Gi, g);
+      }
+      for (int t = 0; t < j.dev.T; ++t) {
+        const Rect r = tile_rect(t, j.dev.ny, j.dev.nx, j.dev.ty, j.dev.tx);
+        const int rows = (r.y1 - r.y0 + Gi - 1) / Gi, wd = r.x1 - r.x0;
+        BatchUnitItem u{};
+        if (minor_pipe_batch_geometry(u.cfg, Gi, 1, rows, wd)) {
+          u.kind = kUnitResident;
+        } else if (minor_pipe_batch_geometry(u.cfg, Gi, 0, rows, wd)) {
+          u.kind = u.cfg.tmem ? kUnitTmem : kUnitStreamed;
+        } else {
+          return CLEAN_ERR_UNSUPPORTED;
+        }
+        u.cfg.sync = CLEAN_SYNC_GRID;
+        u.cfg.G = Gi;
+        u.image = w;
+        u.tile = t;
+        p_smem = std::max(p_smem, u.cfg.smem);
+        uitems.push_back(u);
+        upx.push_back((int64_t)(r.y1 - r.y0) * wd);
+      }
+    }
     plans.push_back(j.dev);
     maps.push_back(j.map);
     rmaps.push_back(j.rmap);
@@ -293,7 +364,7 @@ int engine_rebuild(clean_engine_s* e, cudaStream_t s) {
       ++e->n_gather;
     if (j.tma && !j.fft) ++e->n_tma;
     e->max_T = std::max(e->max_T, j.dev.T);
-    for (int t = 0; t < j.dev.T; ++t) {
+    for (int t = 0; t < j.dev.T && !(p_grid > 0 && j.pipe); ++t) {
       const Rect r = tile_rect(t, j.dev.ny, j.dev.nx, j.dev.ty, j.dev.tx);
       Sized z;
       z.px = (int64_t)(r.y1 - r.y0) * (r.x1 - r.x0);
@@ -389,6 +460,48 @@ int engine_rebuild(clean_engine_s* e, cudaStream_t s) {
   if (err == cudaSuccess && !items.empty())
     err = cudaMemcpyAsync(e->d_items, items.data(), sizeof(BatchItem) * items.size(),
                           cudaMemcpyHostToDevice, s);
+  // the persistent schedule: items largest first, each item's G ranks into
+  // the first wave with G idle CTAs (first fit)
+  std::vector<int2> units;
+  e->n_waves = 0;
+  if (!uitems.empty()) {
+    std::vector<int> order(uitems.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return upx[a] > upx[b]; });
+    std::vector<int> used;  // CTAs taken in each wave
+    for (int i : order) {
+      const int G = uitems[i].cfg.G;
+      size_t w = 0;
+      while (w < used.size() && used[w] + G > p_grid) ++w;
+      if (w == used.size()) {
+        used.push_back(0);
+        units.resize(units.size() + p_grid, make_int2(-1, 0));
+      }
+      for (int r = 0; r < G; ++r) units[w * p_grid + used[w] + r] = make_int2(i, r);
+      used[w] += G;
+    }
+    e->n_waves = (int)used.size();
+    if ((int)uitems.size() > e->uitems_cap) {
+      cudaFree(e->d_uitems);
+      e->uitems_cap = std::max<int>((int)uitems.size(), 2 * e->uitems_cap);
+      if (cudaMalloc(&e->d_uitems, sizeof(BatchUnitItem) * e->uitems_cap) != cudaSuccess)
+        return eng_fail(e, CLEAN_ERR_OOM);
+    }
+    if ((int)units.size() > e->units_cap) {
+      cudaFree(e->d_units);
+      e->units_cap = std::max<int>((int)units.size(), 2 * e->units_cap);
+      if (cudaMalloc(&e->d_units, sizeof(int2) * e->units_cap) != cudaSuccess)
+        return eng_fail(e, CLEAN_ERR_OOM);
+    }
+    if (err == cudaSuccess)
+      err = cudaMemcpyAsync(e->d_uitems, uitems.data(), sizeof(BatchUnitItem) * uitems.size(),
+                            cudaMemcpyHostToDevice, s);
+    if (err == cudaSuccess)
+      err = cudaMemcpyAsync(e->d_units, units.data(), sizeof(int2) * units.size(),
+                            cudaMemcpyHostToDevice, s);
+  }
+  e->p_grid = p_grid;
+  e->p_smem = p_smem;
   // the host vectors die here: make the copies complete first
   if (err == cudaSuccess) err = cudaStreamSynchronize(s);
   if (err != cudaSuccess) return eng_fail(e, CLEAN_ERR_CUDA);
@@ -427,6 +540,12 @@ int engine_mark(clean_engine_s* e) {
 // The kernels of one round (round index `round`) on stream s; *n counts them.
 cudaError_t launch_round(clean_engine_s* e, int round, cudaStream_t s, int* n) {
   cudaError_t err = cudaSuccess;
+  if (e->n_waves > 0) {
+    err = launch_minor_batch_persistent(e->d_plans, e->d_uitems, e->d_units, e->n_waves,
+                                        e->p_grid, e->p_smem, e->d_rmaps, e->d_pmaps, round, s);
+    ++*n;
+    if (err != cudaSuccess) return err;
+  }
   for (const Group& g : e->groups) {
     err = g.pipe ? launch_minor_pipe_batch(e->d_plans, e->d_items + g.offset, g.count, g.cfg,
                                            e->d_rmaps, e->d_pmaps, round, s)
@@ -750,6 +869,7 @@ int clean_server_remove(clean_server_t sv, int64_t job_id) {
     if (e->jobs[k].id == job_id) {
       cudaDeviceSynchronize();
       clean_destroy(e->jobs[k].plan);
+      cudaFree(e->jobs[k].bkeys);
       e->free_slots.push_back(e->jobs[k].slot);
       e->jobs.erase(e->jobs.begin() + (long)k);
       e->dirty = true;

@@ -196,6 +196,23 @@ cudaError_t launch_minor_batch(const PlanDev* plans, const BatchItem* items, int
 // Largest cluster size <= want that can be scheduled for the batched kernel.
 int minor_batch_cluster(int want, int resident, int smem);
 
+// One tile of one image in the persistent batched minor loop: its launch
+// configuration (G CTAs with the grid exchange) and the body it takes.
+enum { kUnitResident = 0, kUnitTmem = 1, kUnitStreamed = 2 };
+struct BatchUnitItem {
+  MinorCfg cfg;
+  int32_t image, tile, kind, pad;
+};
+// CTAs of the persistent launch with `smem` bytes of dynamic shared memory
+// (one per SM; 0 if it cannot be resident).
+int minor_batch_persistent_grid(int smem);
+// One round of every item: units[w * grid + b] = (item, rank) of CTA b in
+// wave w, item -1 idle.  Cooperative launch.
+cudaError_t launch_minor_batch_persistent(const PlanDev* plans, const BatchUnitItem* items,
+                                          const int2* units, int n_waves, int grid, int smem,
+                                          const CUtensorMap* rmaps, const CUtensorMap* pmaps,
+                                          int round, cudaStream_t s);
+
 // Batched TMA pipeline: every image's residual and PSF box maps have boxes of
 // kBatchBoxW x kBatchBoxRows floats (chunks of 128 columns x 60 rows).
 constexpr int kBatchBoxW = 132;

@@ -593,7 +593,10 @@ constexpr int kTmemCols = 512;
 constexpr int kTmemChunks = 8;       // 4 warps per lane quarter x 8 chunks x 16 columns
 constexpr int kTmemChunkRows = 60;   // 15 warps x 4 slabs of one row
 
-template <int SYNC, bool RES, bool TM = false>
+// PERSIST: one unit of a persistent launch (the caller checks the plan's
+// status uniformly before; at the end the barriers are invalidated so the
+// next unit can initialise the same shared memory again).
+template <int SYNC, bool RES, bool TM = false, bool PERSIST = false>
 __device__ __forceinline__ void minor_pipe_body(const PlanDev& d, const MinorCfg& c, int parity,
                                                 const CUtensorMap* r_map,
                                                 const CUtensorMap* p_map, int t, int rank) {
@@ -627,7 +630,7 @@ __device__ __forceinline__ void minor_pipe_body(const PlanDev& d, const MinorCfg
   const uint64_t limit = (uint64_t)c.spin_limit_ns;
   const int WR = (W + 3) & ~3;              // resident slab row stride
 
-  if (*(volatile int32_t*)&d.st->status != 0) return;  // uniform, see minor_kernel
+  if (!PERSIST && *(volatile int32_t*)&d.st->status != 0) return;  // uniform, see minor_kernel
 
   // consumer geometry within a chunk: row slabs of 4-pixel groups (vector
   // path, CW = 32, 64 or 128) or single pixels, threads per row a power of two
@@ -648,7 +651,9 @@ __device__ __forceinline__ void minor_pipe_body(const PlanDev& d, const MinorCfg
   const bool tm_on = TM && n_tm > 0;
   if (tm_on && warp == 0) {
     ptx::tmem_alloc(&s_tmem, kTmemCols);
-    ptx::tmem_relinquish();
+    // a persistent CTA allocates again for its next unit: it keeps the permit
+    // (it owns its SM, so no other CTA waits for the columns)
+    if (!PERSIST) ptx::tmem_relinquish();
     ptx::tmem_fence_before_sync();
   }
 
@@ -909,6 +914,15 @@ __device__ __forceinline__ void minor_pipe_body(const PlanDev& d, const MinorCfg
     d.rcount[t] = (int32_t)k;
     d.budget[t] = budget - k;
     d.gbar[t] = seq0 + (uint32_t)k;
+  }
+  if (PERSIST) {
+    __syncthreads();
+    if (threadIdx.x == 0)
+      for (int i = 0; i < S; ++i) {
+        ptx::mbar_inval(&full_bar[i]);
+        ptx::mbar_inval(&empty_bar[i]);
+      }
+    __syncthreads();
   }
 }
 
@@ -1394,6 +1408,50 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
                                  pmaps + it.image, it.tile, rank);
 }
 
+// Persistent batched minor loop: one CTA per SM, each working through its
+// column of a host-built schedule of waves.  units[w * gridDim.x + b] is the
+// (item, rank) that CTA b serves in wave w (item -1: idle).  An item is one
+// tile of one image with its own launch configuration; its G ranks sit in
+// one wave, so they run at the same time on distinct CTAs (the launch is
+// cooperative: every CTA is resident) and exchange their peaks through the
+// bounded grid exchange.  A CTA goes on to its next wave as soon as its unit
+// ends.  A CTA can only wait for the ranks of its own unit, and the ranks of
+// the earliest unfinished wave are all resident and at that unit, so the
+// schedule always progresses.  Each unit runs the pipelined body of the
+// single-plan and clustered kernels, so the results are bit for bit theirs.
+__global__ void __launch_bounds__(kPipeThreads, 1)
+    minor_batch_persistent_kernel(const PlanDev* __restrict__ plans,
+                                  const BatchUnitItem* __restrict__ items,
+                                  const int2* __restrict__ units, int n_waves,
+                                  const CUtensorMap* rmaps, const CUtensorMap* pmaps, int round) {
+  __shared__ int s_skip;
+  for (int w = 0; w < n_waves; ++w) {
+    const int2 u = units[(int64_t)w * gridDim.x + blockIdx.x];
+    if (u.x < 0) continue;  // the same for the whole CTA
+    const BatchUnitItem it = items[u.x];
+    const PlanDev d = plans[it.image];
+    if (threadIdx.x == 0) s_skip = *(volatile int32_t*)&d.st->status != 0;
+    __syncthreads();
+    const bool skip = s_skip != 0;
+    __syncthreads();
+    if (skip) continue;
+    const int parity = (round - d.round0) & 1;
+    const CUtensorMap* rm = rmaps + it.image;
+    const CUtensorMap* pm = pmaps + it.image;
+    switch (it.kind) {
+      case kUnitResident:
+        minor_pipe_body<CLEAN_SYNC_GRID, true, false, true>(d, it.cfg, parity, rm, pm, it.tile, u.y);
+        break;
+      case kUnitTmem:
+        minor_pipe_body<CLEAN_SYNC_GRID, false, true, true>(d, it.cfg, parity, rm, pm, it.tile, u.y);
+        break;
+      default:
+        minor_pipe_body<CLEAN_SYNC_GRID, false, false, true>(d, it.cfg, parity, rm, pm, it.tile, u.y);
+        break;
+    }
+  }
+}
+
 template <int SYNC, bool RES>
 void* kernel_ptr(bool pipe, bool tmem) {
   if (!pipe) return (void*)minor_kernel<SYNC, RES>;
@@ -1539,6 +1597,43 @@ cudaError_t launch_minor_pipe_batch(const PlanDev* plans, const BatchItem* items
   void* args[] = {const_cast<PlanDev**>(&plans), const_cast<BatchItem**>(&items),
                   const_cast<CUtensorMap**>(&rmaps), const_cast<CUtensorMap**>(&pmaps), &cc,
                   &round};
+  return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
+int minor_batch_persistent_grid(int smem) {
+  const void* fn = (const void*)minor_batch_persistent_kernel;
+  int dev = 0, sms = 0, per_sm = 0;
+  if (allow_max_smem(fn) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kPipeThreads, smem) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return per_sm >= 1 ? sms : 0;  // one CTA per SM (the tensor-memory units own their SM)
+}
+
+cudaError_t launch_minor_batch_persistent(const PlanDev* plans, const BatchUnitItem* items,
+                                          const int2* units, int n_waves, int grid, int smem,
+                                          const CUtensorMap* rmaps, const CUtensorMap* pmaps,
+                                          int round, cudaStream_t s) {
+  if (n_waves <= 0 || grid <= 0) return cudaSuccess;
+  const void* fn = (const void*)minor_batch_persistent_kernel;
+  cudaError_t e = allow_max_smem(fn);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)grid, 1, 1);
+  cfg.blockDim = dim3(kPipeThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  void* args[] = {const_cast<PlanDev**>(&plans), const_cast<BatchUnitItem**>(&items),
+                  const_cast<int2**>(&units), &n_waves, const_cast<CUtensorMap**>(&rmaps),
+                  const_cast<CUtensorMap**>(&pmaps), &round};
   return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
