@@ -51,6 +51,10 @@ struct Job {
   // grid-exchange slots of the persistent minor loop: 2 sets x T tiles x
   // kMaxUnitG CTAs, owned by the engine
   uint64_t* bkeys = nullptr;
+  // CTAs per tile in the persistent minor loop, fixed from the run's first
+  // schedule to its end: the exchange slots of tile t are t G .. t G + G - 1,
+  // and the exchange count runs on across rounds (0: not chosen yet)
+  int unit_G = 0;
   bool fft = false;  // feedback by FFT convolution (the job's own launches)
   int64_t id = 0;
   int slot = 0;
@@ -171,6 +175,7 @@ int engine_create(clean_engine_s** out, int cap) {
 int engine_start(clean_engine_s* e, Job& j, const float* d_dirty, cudaStream_t s) {
   j.dev.round0 = e->round;
   j.finished = false;
+  j.unit_G = 0;
   cudaError_t err = cudaMemsetAsync(j.dev.st, 0, sizeof(DevState), s);
   if (err == cudaSuccess) err = cudaMemsetAsync(j.dev.peak, 0, sizeof(uint64_t) * 2 * j.dev.T, s);
   if (err == cudaSuccess) err = launch_init(j.dev, d_dirty, plan_niter(j.plan), s);
@@ -323,17 +328,21 @@ int engine_rebuild(clean_engine_s* e, cudaStream_t s) {
   int p_smem = kPersistSmemMin;
   e->blocks_tma = e->blocks_plain = 0;
   for (int w = 0; w < (int)work.size(); ++w) {
-    const Job& j = e->jobs[work[w]];
+    Job& j = e->jobs[work[w]];
     if (p_grid > 0 && j.pipe) {
       // one G for the whole image (its tiles share the exchange slots), the
-      // largest any of its tiles asks for
-      int Gi = 1;
-      for (int t = 0; t < j.dev.T; ++t) {
-        const Rect r = tile_rect(t, j.dev.ny, j.dev.nx, j.dev.ty, j.dev.tx);
-        int g = 1, res = 0, rows = 0;
-        pipe_tile_group(r.y1 - r.y0, r.x1 - r.x0, fast, &g, &res, &rows);
-        Gi = std::max(Gi, g);
+      // largest any of its tiles asks for, kept while the run lasts
+      if (j.unit_G == 0) {
+        int Gi = 1;
+        for (int t = 0; t < j.dev.T; ++t) {
+          const Rect r = tile_rect(t, j.dev.ny, j.dev.nx, j.dev.ty, j.dev.tx);
+          int g = 1, res = 0, rows = 0;
+          pipe_tile_group(r.y1 - r.y0, r.x1 - r.x0, fast, &g, &res, &rows);
+          Gi = std::max(Gi, g);
+        }
+        j.unit_G = Gi;
       }
+      const int Gi = j.unit_G;
       for (int t = 0; t < j.dev.T; ++t) {
         const Rect r = tile_rect(t, j.dev.ny, j.dev.nx, j.dev.ty, j.dev.tx);
         const int rows = (r.y1 - r.y0 + Gi - 1) / Gi, wd = r.x1 - r.x0;
