@@ -285,7 +285,11 @@ def batch_leg(cg, torch, stream, n_images=64):
 
     with cg.Batch(spec) as bt:
         ms_batch = timed(lambda: bt.run(dirties))
-        st = bt.stats()
+        st0 = bt.stats()
+        bt.run(dirties)  # one more run, counted alone
+        torch.cuda.synchronize()
+        st1 = bt.stats()
+    st = {k: st1[k] - st0[k] for k in ("rounds_launched", "kernel_launches")}
     solo = [cg.Plan(psfs[i], j["n"], j["n"], gain=j["gain"], niter=j["niter"], threshold=0.0,
                     tiles=j["tiles"], feedback_interval=j["K"]) for i, j in enumerate(jobs)]
     ms_solo = timed(lambda: [p.run(dirties[i]) for i, p in enumerate(solo)])
@@ -297,6 +301,16 @@ def batch_leg(cg, torch, stream, n_images=64):
     for p in plain:
         p.close()
     sides = [j["n"] for j in jobs]
+    # algorithmic bytes of one run: minor loop 12 B per pixel-iteration (of
+    # the iteration's tile), feedback 4 B per pixel-component update + 8 N^2
+    # per round; the iteration budget is spent in full (threshold 0)
+    px_iter = bytes_ = 0.0
+    for j in jobs:
+        n, (ty, tx), nit, K = j["n"], j["tiles"], j["niter"], j["K"]
+        T = ty * tx
+        M = n * n / T
+        px_iter += nit * M
+        bytes_ += 12.0 * nit * M + 4.0 * nit * (n * n - M) + 8.0 * n * n * (-(-nit // (K * T)))
     return {"workload": f"{n_images} images, sides {sorted(set(sides))} (counts "
                         f"{[sides.count(v) for v in sorted(set(sides))]}), PSF 2N, freq scale 1-2, "
                         "2x2 tiles up to 1024 else 4x4, K 50, 2000 iterations each",
@@ -305,7 +319,14 @@ def batch_leg(cg, torch, stream, n_images=64):
             "one_at_a_time_plain_iters_per_s": total_iters / (ms_plain / 1e3),
             "vs_one_at_a_time_tiled": ms_solo / ms_batch,
             "vs_one_at_a_time_plain": ms_plain / ms_batch,
-            "rounds": st["rounds_launched"], "kernel_launches": st["kernel_launches"]}
+            "px_iter_per_s": px_iter / (ms_batch / 1e3),
+            "algorithmic_GBps": bytes_ / (ms_batch / 1e3) / 1e9,
+            "rounds_per_run": st["rounds_launched"],
+            "kernel_launches_per_run": st["kernel_launches"],
+            "set_up_launches_per_run": n_images,
+            "launches_per_round": (st["kernel_launches"] - n_images) / max(1, st["rounds_launched"]),
+            "note": "per run: one set-up kernel per image, then each round one persistent "
+                    "minor-loop launch over every image's tiles and one feedback launch"}
 
 
 def serve_leg(cg, torch, psf_full, n_jobs=60, loads=(0.7,), seed=1004):
@@ -755,6 +776,7 @@ def main():
     batched = None
     if not args.no_batch:
         batched = batch_leg(cg, torch, stream)
+        batched["frac_of_l2_peak"] = batched["algorithmic_GBps"] / l2_gbs
 
     served = None
     if not args.no_serve:
