@@ -67,6 +67,10 @@ def parse():
     ap.add_argument("--profile", type=int, default=0, metavar="R",
                     help="profiling target: one run of the workload truncated to R rounds "
                          "(no warm-up, no timing, no JSON line)")
+    ap.add_argument("--profile-batch", type=int, default=0, metavar="R",
+                    help="profiling target: the 64-image batch run for R rounds")
+    ap.add_argument("--l2-sweep", action="store_true",
+                    help="the L2 read probe over buffers of 8 MiB to 512 MiB (one JSON line)")
     return ap.parse_args()
 
 
@@ -84,6 +88,47 @@ def run_profile(args):
         plan.run(d_dirty, max_rounds=args.profile)
         torch.cuda.synchronize()
         print(json.dumps({"profile_rounds": args.profile, "components": plan.n_components()}))
+
+
+def run_profile_batch(args):
+    """A bounded target for ncu captures of the batched kernels: the 64-image
+    batch of the batch leg, one run of R rounds."""
+    import torch
+
+    import paper_2501_01461_gb300 as cg
+    cg.lib()
+    jobs = synth.batch_jobs(64)
+    psfs = [torch.from_numpy(j["psf"]).cuda() for j in jobs]
+    dirties = [torch.from_numpy(j["dirty"]).cuda() for j in jobs]
+    spec = [dict(psf=psfs[i], ny=j["n"], nx=j["n"], gain=j["gain"], niter=j["niter"],
+                 threshold=0.0, tiles=j["tiles"], feedback_interval=j["K"])
+            for i, j in enumerate(jobs)]
+    with cg.Batch(spec) as bt:
+        bt.run(dirties, max_rounds=args.profile_batch)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_batch_rounds": args.profile_batch, **bt.stats()}))
+
+
+def run_l2_sweep(args):
+    """The L2 read probe over buffers of 8 to 512 MiB, every form: the
+    bandwidth stays near its L2 value while the buffer fits in L2 and falls
+    to the HBM rate beyond."""
+    import torch
+
+    import paper_2501_01461_gb300 as cg
+    cg.lib()
+    out = {}
+    for mb in (8, 24, 48, 80, 512):
+        buf = torch.ones(mb * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        for name, m, c in (("bulk_copy_1cta", 0, 1), ("bulk_copy_2cta", 0, 2),
+                           ("vector_load_2cta", 1, 2), ("vector_load_4cta", 1, 4)):
+            best = 0.0
+            for _ in range(3):
+                nb, ms = cg.probe_l2_read(buf, passes=max(2, 4800 // mb), method=m, ctas_per_sm=c)
+                best = max(best, nb / (ms / 1e3) / 1e9)
+            out[f"{mb}MiB_{name}"] = round(best, 1)
+        del buf
+    print(json.dumps({"l2_sweep_GBps": out}))
 
 
 def dist_env():
@@ -568,6 +613,12 @@ def main():
         return
     if args.profile > 0:
         run_profile(args)
+        return
+    if args.profile_batch > 0:
+        run_profile_batch(args)
+        return
+    if args.l2_sweep:
+        run_l2_sweep(args)
         return
     if args.sweep:
         run_sweep(args)
