@@ -433,6 +433,21 @@ __device__ __forceinline__ void take_peak(float r, int idx, float& best_a, int& 
 // once per iteration.
 constexpr int kSlabUnroll = 4;
 
+// The running best 4-pixel group: a group replaces it only if its maximum
+// |R| is larger, or equal with a lower base index.  Past the first few groups
+// a new maximum is rare, so the common case is one comparison (m >= best_a)
+// that skips the update.
+__device__ __forceinline__ void keep_group(bool valid, float m, int base, const float4& r,
+                                           float& best_a, int& best_base, float4& best_r) {
+  if (valid && m >= best_a) {
+    if (m > best_a || base < best_base) {
+      best_a = m;
+      best_base = base;
+      best_r = r;
+    }
+  }
+}
+
 // U slabs s, s + 15, ... of one chunk for this lane (rows past r1 masked).
 template <bool RES, int OFF, int U>
 __device__ __forceinline__ void slab_step(const PlanDev& d, float* sRes, int WR, int ya,
@@ -474,13 +489,8 @@ __device__ __forceinline__ void slab_step(const PlanDev& d, float* sRes, int WR,
       else
         *reinterpret_cast<float4*>(d.R + (int64_t)y * d.nx + x) = r;
     }
-    const float m0 = fmaxf(fmaxf(fabsf(r.x), fabsf(r.y)), fmaxf(fabsf(r.z), fabsf(r.w)));
-    const float m = valid ? m0 : -1.f;
-    const int base = y * d.nx + x;
-    const bool better = m > best_a || (m == best_a && base < best_base);
-    best_a = better ? m : best_a;
-    best_base = better ? base : best_base;
-    best_r = better ? r : best_r;
+    const float m = fmaxf(fmaxf(fabsf(r.x), fabsf(r.y)), fmaxf(fabsf(r.z), fabsf(r.w)));
+    keep_group(valid, m, y * d.nx + x, r, best_a, best_base, best_r);
   }
 }
 
@@ -567,11 +577,8 @@ __device__ __forceinline__ void tmem_chunk(const PlanDev& d, uint32_t taddr, boo
     fms2(r.z, r.w, p.z, p.w, f);
     rv[u] = r;
     const float m = fmaxf(fmaxf(fabsf(r.x), fabsf(r.y)), fmaxf(fabsf(r.z), fabsf(r.w)));
-    const int base = (r0 + warp + u * kWarps) * d.nx + c0 + 4 * lane;
-    const bool better = m > best_a || (m == best_a && base < best_base);
-    best_a = better ? m : best_a;
-    best_base = better ? base : best_base;
-    best_r = better ? r : best_r;
+    keep_group(true, m, (r0 + warp + u * kWarps) * d.nx + c0 + 4 * lane, r, best_a, best_base,
+               best_r);
   }
   __syncwarp();
   ptx::tmem_st16(taddr, rv);
