@@ -447,10 +447,12 @@ __device__ __forceinline__ void keep_group(bool valid, float m, int base, const 
 }
 
 // keep_group over the U groups of one step.  Past the first few steps a new
-// maximum is rare, so the step first compares its largest group maximum with
-// the running best once and runs the exact per-group rule only when that
-// reaches it (the result does not depend on the order the groups are
-// considered in).
+// maximum is rare, so the step compares its largest group maximum with the
+// running best once, and the warp runs the exact per-group rule only when
+// one of its lanes reaches its best (a warp-uniform branch; the result does
+// not depend on the order the groups are considered in).  The vote covers
+// the lanes still active (a chunk narrower than the warp's 128 columns leaves
+// some out).
 template <int U>
 __device__ __forceinline__ void keep_groups(const bool (&valid)[U], const float (&m)[U],
                                             const int (&base)[U], const float4 (&r)[U],
@@ -458,7 +460,7 @@ __device__ __forceinline__ void keep_groups(const bool (&valid)[U], const float 
   float mx = -1.f;
 #pragma unroll
   for (int u = 0; u < U; ++u) mx = fmaxf(mx, valid[u] ? m[u] : -1.f);
-  if (mx >= best_a && mx >= 0.f) {
+  if (__any_sync(__activemask(), mx >= best_a && mx >= 0.f)) {
 #pragma unroll
     for (int u = 0; u < U; ++u) keep_group(valid[u], m[u], base[u], r[u], best_a, best_base, best_r);
   }
