@@ -434,7 +434,9 @@ __device__ __forceinline__ void take_peak(float r, int idx, float& best_a, int& 
 constexpr int kSlabUnroll = 4;
 
 // The running best 4-pixel group: a group replaces it only if its maximum
-// |R| is larger, or equal with a lower base index.
+// |R| is larger, or equal with a lower base index.  Past the first few groups
+// a new maximum is rare, so the common case is one comparison (m >= best_a)
+// that skips the update.
 __device__ __forceinline__ void keep_group(bool valid, float m, int base, const float4& r,
                                            float& best_a, int& best_base, float4& best_r) {
   if (valid && m >= best_a) {
@@ -443,26 +445,6 @@ __device__ __forceinline__ void keep_group(bool valid, float m, int base, const 
       best_base = base;
       best_r = r;
     }
-  }
-}
-
-// keep_group over the U groups of one step.  Past the first few steps a new
-// maximum is rare, so the step compares its largest group maximum with the
-// running best once, and the warp runs the exact per-group rule only when
-// one of its lanes reaches its best (a warp-uniform branch; the result does
-// not depend on the order the groups are considered in).  The vote covers
-// the lanes still active (a chunk narrower than the warp's 128 columns leaves
-// some out).
-template <int U>
-__device__ __forceinline__ void keep_groups(const bool (&valid)[U], const float (&m)[U],
-                                            const int (&base)[U], const float4 (&r)[U],
-                                            float& best_a, int& best_base, float4& best_r) {
-  float mx = -1.f;
-#pragma unroll
-  for (int u = 0; u < U; ++u) mx = fmaxf(mx, valid[u] ? m[u] : -1.f);
-  if (__any_sync(__activemask(), mx >= best_a && mx >= 0.f)) {
-#pragma unroll
-    for (int u = 0; u < U; ++u) keep_group(valid[u], m[u], base[u], r[u], best_a, best_base, best_r);
   }
 }
 
@@ -485,13 +467,10 @@ __device__ __forceinline__ void slab_step(const PlanDev& d, float* sRes, int WR,
     rv[u] = RES ? *reinterpret_cast<const float4*>(sRes + (r0 + ly - ya) * WR + (x - x0))
                 : reinterpret_cast<const float4*>(stgR + ly * BW)[g];
   }
-  bool valid[U];
-  float m[U];
-  int base[U];
 #pragma unroll
   for (int u = 0; u < U; ++u) {
     const int y = r0 + (s + u * kWarps) * rps + sub;
-    valid[u] = y < r1;
+    const bool valid = y < r1;
     const float4 a = pa[u];
     float4 p;
     if (OFF == 0) {
@@ -504,17 +483,15 @@ __device__ __forceinline__ void slab_step(const PlanDev& d, float* sRes, int WR,
     float4 r = rv[u];
     fms2(r.x, r.y, p.x, p.y, f);
     fms2(r.z, r.w, p.z, p.w, f);
-    if (valid[u]) {
+    if (valid) {
       if (RES)
         *reinterpret_cast<float4*>(sRes + (y - ya) * WR + (x - x0)) = r;
       else
         *reinterpret_cast<float4*>(d.R + (int64_t)y * d.nx + x) = r;
     }
-    rv[u] = r;
-    m[u] = fmaxf(fmaxf(fabsf(r.x), fabsf(r.y)), fmaxf(fabsf(r.z), fabsf(r.w)));
-    base[u] = y * d.nx + x;
+    const float m = fmaxf(fmaxf(fabsf(r.x), fabsf(r.y)), fmaxf(fabsf(r.z), fabsf(r.w)));
+    keep_group(valid, m, y * d.nx + x, r, best_a, best_base, best_r);
   }
-  keep_groups<U>(valid, m, base, rv, best_a, best_base, best_r);
 }
 
 template <bool RES, int OFF>
@@ -570,9 +547,6 @@ __device__ __forceinline__ void tmem_chunk(const PlanDev& d, uint32_t taddr, boo
   constexpr int kWarps = kPipeConsumers / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float4 rv[kSlabUnroll], pa[kSlabUnroll], pb[kSlabUnroll];
-  const bool valid[kSlabUnroll] = {true, true, true, true};
-  float m[kSlabUnroll];
-  int base[kSlabUnroll];
 #pragma unroll
   for (int u = 0; u < kSlabUnroll; ++u) {
     const float4* rowP4 = reinterpret_cast<const float4*>(stgP + (warp + u * kWarps) * BW);
@@ -602,10 +576,10 @@ __device__ __forceinline__ void tmem_chunk(const PlanDev& d, uint32_t taddr, boo
     fms2(r.x, r.y, p.x, p.y, f);
     fms2(r.z, r.w, p.z, p.w, f);
     rv[u] = r;
-    m[u] = fmaxf(fmaxf(fabsf(r.x), fabsf(r.y)), fmaxf(fabsf(r.z), fabsf(r.w)));
-    base[u] = (r0 + warp + u * kWarps) * d.nx + c0 + 4 * lane;
+    const float m = fmaxf(fmaxf(fabsf(r.x), fabsf(r.y)), fmaxf(fabsf(r.z), fabsf(r.w)));
+    keep_group(true, m, (r0 + warp + u * kWarps) * d.nx + c0 + 4 * lane, r, best_a, best_base,
+               best_r);
   }
-  keep_groups<kSlabUnroll>(valid, m, base, rv, best_a, best_base, best_r);
   __syncwarp();
   ptx::tmem_st16(taddr, rv);
 }
