@@ -34,7 +34,7 @@ using namespace cleangb;
 namespace {
 
 constexpr int64_t kGroupSmemMax = 200 * 1024;  // resident rows per CTA
-constexpr int kMaxUnitG = 16;                   // CTAs per tile in the persistent minor loop
+constexpr int kMaxUnitG = 32;                   // exchange slots per tile (a pair's 2G CTAs)
 // dynamic shared memory floor of the persistent launch: above half an SM, so
 // each SM holds one CTA (units that keep residual chunks in tensor memory
 // take all of its columns)
@@ -55,6 +55,7 @@ struct Job {
   // schedule to its end: the exchange slots of tile t are t G .. t G + G - 1,
   // and the exchange count runs on across rounds (0: not chosen yet)
   int unit_G = 0;
+  bool unit_pair = false;  // tile pairs (fixed with unit_G: the slots are laid out by 2G)
   bool fft = false;  // feedback by FFT convolution (the job's own launches)
   int64_t id = 0;
   int slot = 0;
@@ -176,6 +177,7 @@ int engine_start(clean_engine_s* e, Job& j, const float* d_dirty, cudaStream_t s
   j.dev.round0 = e->round;
   j.finished = false;
   j.unit_G = 0;
+  j.unit_pair = false;
   cudaError_t err = cudaMemsetAsync(j.dev.st, 0, sizeof(DevState), s);
   if (err == cudaSuccess) err = cudaMemsetAsync(j.dev.peak, 0, sizeof(uint64_t) * 2 * j.dev.T, s);
   if (err == cudaSuccess) err = launch_init(j.dev, d_dirty, plan_niter(j.plan), s);
@@ -333,17 +335,58 @@ int engine_rebuild(clean_engine_s* e, cudaStream_t s) {
       // one G for the whole image (its tiles share the exchange slots), the
       // largest any of its tiles asks for, kept while the run lasts
       if (j.unit_G == 0) {
-        int Gi = 1;
+        // tile pairs when the tile count is even and every tile is two chunks
+        // wide: G row bands per tile, each band short enough that a CTA's
+        // full chunks of both tiles sit in tensor memory (4 chunks a tile)
+        int min_w = 1 << 30, max_h = 0, half_w = 0;
         for (int t = 0; t < j.dev.T; ++t) {
           const Rect r = tile_rect(t, j.dev.ny, j.dev.nx, j.dev.ty, j.dev.tx);
-          int g = 1, res = 0, rows = 0;
-          pipe_tile_group(r.y1 - r.y0, r.x1 - r.x0, fast, &g, &res, &rows);
-          Gi = std::max(Gi, g);
+          min_w = std::min(min_w, r.x1 - r.x0);
+          max_h = std::max(max_h, r.y1 - r.y0);
+          half_w = std::max(half_w, ((r.x1 - r.x0) / 2 + 127) / 128 * 128);
         }
-        j.unit_G = Gi;
+        const int per_band = kBatchBoxRows * std::max(1, 4 / std::max(1, half_w / 128));
+        const int Gp = (max_h + per_band - 1) / per_band;
+        if (j.dev.T % 2 == 0 && min_w >= 2 * 128 && 2 * Gp <= kMaxUnitG) {
+          j.unit_pair = true;
+          j.unit_G = Gp;
+        } else {
+          int Gi = 1;
+          for (int t = 0; t < j.dev.T; ++t) {
+            const Rect r = tile_rect(t, j.dev.ny, j.dev.nx, j.dev.ty, j.dev.tx);
+            int g = 1, res = 0, rows = 0;
+            pipe_tile_group(r.y1 - r.y0, r.x1 - r.x0, fast, &g, &res, &rows);
+            Gi = std::max(Gi, g);
+          }
+          j.unit_G = Gi;
+        }
       }
       const int Gi = j.unit_G;
-      for (int t = 0; t < j.dev.T; ++t) {
+      if (j.unit_pair) {
+        for (int pr = 0; pr < j.dev.T / 2; ++pr) {
+          int rows = 0, wd = 0;
+          int64_t px = 0;
+          for (int t = 2 * pr; t <= 2 * pr + 1; ++t) {
+            const Rect r = tile_rect(t, j.dev.ny, j.dev.nx, j.dev.ty, j.dev.tx);
+            rows = std::max(rows, (r.y1 - r.y0 + Gi - 1) / Gi);
+            wd = std::max(wd, r.x1 - r.x0);
+            px += (int64_t)(r.y1 - r.y0) * (r.x1 - r.x0);
+          }
+          BatchUnitItem u{};
+          if (!minor_pipe_batch_geometry(u.cfg, Gi, 0, rows, wd)) return CLEAN_ERR_UNSUPPORTED;
+          u.cfg.sync = CLEAN_SYNC_GRID;
+          u.cfg.G = Gi;
+          u.cfg.pair = 1;
+          u.kind = kUnitPair;
+          u.image = w;
+          u.tile = pr;
+          u.ranks = 2 * Gi;
+          p_smem = std::max(p_smem, u.cfg.smem);
+          uitems.push_back(u);
+          upx.push_back(px);
+        }
+      }
+      for (int t = 0; t < j.dev.T && !j.unit_pair; ++t) {
         const Rect r = tile_rect(t, j.dev.ny, j.dev.nx, j.dev.ty, j.dev.tx);
         const int rows = (r.y1 - r.y0 + Gi - 1) / Gi, wd = r.x1 - r.x0;
         BatchUnitItem u{};
@@ -358,6 +401,7 @@ int engine_rebuild(clean_engine_s* e, cudaStream_t s) {
         u.cfg.G = Gi;
         u.image = w;
         u.tile = t;
+        u.ranks = Gi;
         p_smem = std::max(p_smem, u.cfg.smem);
         uitems.push_back(u);
         upx.push_back((int64_t)(r.y1 - r.y0) * wd);
@@ -479,7 +523,7 @@ int engine_rebuild(clean_engine_s* e, cudaStream_t s) {
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return upx[a] > upx[b]; });
     std::vector<int> used;  // CTAs taken in each wave
     for (int i : order) {
-      const int G = uitems[i].cfg.G;
+      const int G = uitems[i].ranks;
       size_t w = 0;
       while (w < used.size() && used[w] + G > p_grid) ++w;
       if (w == used.size()) {

@@ -198,10 +198,13 @@ int minor_batch_cluster(int want, int resident, int smem);
 
 // One tile of one image in the persistent batched minor loop: its launch
 // configuration (G CTAs with the grid exchange) and the body it takes.
-enum { kUnitResident = 0, kUnitTmem = 1, kUnitStreamed = 2 };
+enum { kUnitResident = 0, kUnitTmem = 1, kUnitStreamed = 2, kUnitPair = 3 };
 struct BatchUnitItem {
   MinorCfg cfg;
-  int32_t image, tile, kind, pad;
+  int32_t image;
+  int32_t tile;   // the tile, or for kUnitPair the pair (tiles 2 tile, 2 tile + 1)
+  int32_t kind;
+  int32_t ranks;  // CTAs of the unit: cfg.G, or 2 cfg.G for a pair
 };
 // CTAs of the persistent launch with `smem` bytes of dynamic shared memory
 // (one per SM; 0 if it cannot be resident).

@@ -1046,7 +1046,8 @@ __device__ __forceinline__ uint64_t pair_poll(const PlanDev& d, const MinorCfg& 
   return abort ? 0ull : kk;
 }
 
-template <bool TM>
+// PERSIST: one unit of the persistent batched launch (as in minor_pipe_body).
+template <bool TM, bool PERSIST = false>
 __device__ __forceinline__ void minor_pair_body(const PlanDev& d, const MinorCfg& c, int parity,
                                                 const CUtensorMap* r_map,
                                                 const CUtensorMap* p_map, int pair, int q) {
@@ -1073,7 +1074,7 @@ __device__ __forceinline__ void minor_pair_body(const PlanDev& d, const MinorCfg
   const uint32_t p_box_bytes = (uint32_t)(BW * BH) * 4u;
   const uint64_t limit = (uint64_t)c.spin_limit_ns;
 
-  if (*(volatile int32_t*)&d.st->status != 0) return;  // uniform, see minor_kernel
+  if (!PERSIST && *(volatile int32_t*)&d.st->status != 0) return;  // uniform, see minor_kernel
 
   // per-tile state in named pairs (selected per step, no local arrays)
   const Piece pc0 = pair_piece(d, 2 * pair, q % G, q / G, G, BH, CW, TM && c.tmem);
@@ -1081,7 +1082,7 @@ __device__ __forceinline__ void minor_pair_body(const PlanDev& d, const MinorCfg
   const bool tm_on = TM && (pc0.n_tm > 0 || pc1.n_tm > 0);
   if (tm_on && warp == 0) {
     ptx::tmem_alloc(&s_tmem, kTmemCols);
-    ptx::tmem_relinquish();
+    if (!PERSIST) ptx::tmem_relinquish();  // a persistent CTA allocates again later
     ptx::tmem_fence_before_sync();
   }
 
@@ -1388,6 +1389,17 @@ __device__ __forceinline__ void minor_pair_body(const PlanDev& d, const MinorCfg
     d.budget[pc1.t] = budget1 - kx1;
     d.gbar[pc1.t] = seq01 + (uint32_t)kx1;
   }
+  if (PERSIST) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int i = 0; i < S; ++i) {
+        ptx::mbar_inval(&full_bar[i]);
+        ptx::mbar_inval(&empty_bar[i]);
+      }
+      ptx::mbar_inval(&key_bar);
+    }
+    __syncthreads();
+  }
 }
 
 template <bool TM>
@@ -1451,6 +1463,9 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
         break;
       case kUnitTmem:
         minor_pipe_body<CLEAN_SYNC_GRID, false, true, true>(d, it.cfg, parity, rm, pm, it.tile, u.y);
+        break;
+      case kUnitPair:  // it.tile: the pair, tiles 2 it.tile and 2 it.tile + 1
+        minor_pair_body<true, true>(d, it.cfg, parity, rm, pm, it.tile, u.y);
         break;
       default:
         minor_pipe_body<CLEAN_SYNC_GRID, false, false, true>(d, it.cfg, parity, rm, pm, it.tile, u.y);
