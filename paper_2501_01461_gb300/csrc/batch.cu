@@ -23,6 +23,8 @@
 // so the host can launch an upper bound of rounds between reads.  If the
 // capture is refused the engine launches the kernels directly.
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -568,8 +570,21 @@ int engine_read(clean_engine_s* e, cudaStream_t s) {
                                     cudaMemcpyDeviceToHost, s);
   if (err == cudaSuccess) err = cudaStreamSynchronize(s);
   if (err != cudaSuccess) return eng_fail(e, CLEAN_ERR_CUDA);
-  for (const Job& j : e->jobs)
-    if (e->h_states[j.slot].status & ST_TIMEOUT) return eng_fail(e, CLEAN_ERR_TIMEOUT);
+  bool timeout = false;
+  for (const Job& j : e->jobs) {
+    const DevState& st = e->h_states[j.slot];
+    if (!(st.status & ST_TIMEOUT)) continue;
+    timeout = true;
+    // CLEANGB_REPORT_TIMEOUT: which job, tile and exchange gave up (stderr)
+    if (std::getenv("CLEANGB_REPORT_TIMEOUT"))
+      std::fprintf(stderr,
+                   "cleangb: timeout in job %lld (%d x %d, %d tiles, %s G %d): tile %lld, "
+                   "iteration %lld\n",
+                   (long long)j.id, j.dev.ny, j.dev.nx, j.dev.T, j.unit_pair ? "pairs" : "units",
+                   j.unit_G, (long long)(st.timeout_where >> 32),
+                   (long long)(st.timeout_where & 0xffffffffll));
+  }
+  if (timeout) return eng_fail(e, CLEAN_ERR_TIMEOUT);
   return CLEAN_OK;
 }
 

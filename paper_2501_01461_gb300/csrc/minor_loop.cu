@@ -959,9 +959,9 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
 //
 // Step s serves tile X = s mod 2 (steps of a finished tile are skipped on
 // both sides alike).  The producer's lane 0 publishes the step's key in
-// s_key (0: the tile is finished) and arrives on key_bar; the consumers wait
-// on key_bar, process the tile's chunks and leave their partial keys in
-// shared memory; the last warp to finish posts the CTA's key to the tile's
+// s_key[n mod 2] (key n; 0: the tile is finished) and arrives on
+// key_bar[n mod 2]; the consumers wait there (phase n / 2), process the
+// tile's chunks and leave their partial keys in shared memory; the last warp to finish posts the CTA's key to the tile's
 // exchange slot with the usual phase mark.  The producer warp reads
 // the exchange of the tile's previous iteration, which every CTA posted one
 // step earlier, so the wait overlaps the other tile's pass.  Exchange g of
@@ -969,6 +969,13 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
 // slots from being overwritten early is the single-tile one.  The last
 // exchange of a launch is posted and never read; the next launch's count
 // continues past it.
+//
+// Keys n and n + 1 can both be posted before the consumers wait for key n:
+// the first key of each tile needs no exchange, and a finished tile's key is
+// posted at once.  On one barrier that is two phases, and a parity wait for
+// the older one would then test the newer, incomplete phase and never
+// return.  Key n + 2 needs the exchange of key n's pass, so with one barrier
+// per buffer no barrier runs more than one phase ahead of its waiters.
 // ---------------------------------------------------------------------------
 struct Piece {
   int t;                 // tile
@@ -1056,7 +1063,7 @@ __device__ __forceinline__ void minor_pair_body(const PlanDev& d, const MinorCfg
   constexpr int kW = kPipeConsumers / 32;
   __shared__ __align__(8) uint64_t full_bar[kPipeMaxStages];
   __shared__ __align__(8) uint64_t empty_bar[kPipeMaxStages];
-  __shared__ __align__(8) uint64_t key_bar;
+  __shared__ __align__(8) uint64_t key_bar[2];  // key n: barrier n mod 2, phase n / 2
   __shared__ int s_arrived[2];  // consumer warps done with the pass, per key buffer
   __shared__ uint64_t s_key[2];
   __shared__ uint64_t s_warp[2][kW];
@@ -1103,7 +1110,8 @@ __device__ __forceinline__ void minor_pair_body(const PlanDev& d, const MinorCfg
       ptx::mbar_init(&full_bar[i], 1);
       ptx::mbar_init(&empty_bar[i], kW);
     }
-    ptx::mbar_init(&key_bar, 1);
+    ptx::mbar_init(&key_bar[0], 1);
+    ptx::mbar_init(&key_bar[1], 1);
     s_arrived[0] = 0;
     s_arrived[1] = 0;
     ptx::fence_barrier_init();
@@ -1160,7 +1168,7 @@ __device__ __forceinline__ void minor_pair_body(const PlanDev& d, const MinorCfg
           s_abort = 1;
         }
         s_key[n_pub & 1u] = active ? key : 0ull;
-        ptx::mbar_arrive(&key_bar);
+        ptx::mbar_arrive(&key_bar[n_pub & 1u]);
       }
       ++n_pub;
       if (!active) {
@@ -1212,7 +1220,8 @@ __device__ __forceinline__ void minor_pair_body(const PlanDev& d, const MinorCfg
     // ---- consumers ----
     // the producer publishes within its own bounded waits (at most two
     // limits), so this wait gets four
-    bool got = pipe_wait(&key_bar, n_pub & 1u, 4 * limit, &s_dead, &d.st->status);
+    bool got = pipe_wait(&key_bar[n_pub & 1u], (n_pub >> 1) & 1u, 4 * limit, &s_dead,
+                         &d.st->status);
     got = __all_sync(0xffffffffu, got);
     const uint64_t key = got ? s_key[n_pub & 1u] : 0ull;
     ++n_pub;
@@ -1396,7 +1405,8 @@ __device__ __forceinline__ void minor_pair_body(const PlanDev& d, const MinorCfg
         ptx::mbar_inval(&full_bar[i]);
         ptx::mbar_inval(&empty_bar[i]);
       }
-      ptx::mbar_inval(&key_bar);
+      ptx::mbar_inval(&key_bar[0]);
+      ptx::mbar_inval(&key_bar[1]);
     }
     __syncthreads();
   }

@@ -47,3 +47,20 @@ def assert_bit_exact(g, o, what=""):
     assert not dr.any(), f"{what}: residual differs at {np.argwhere(dr)[:5].tolist()}"
     dm = g["model"].view(np.uint32) != o.model.view(np.uint32)
     assert not dm.any(), f"{what}: model differs at {np.argwhere(dm)[:5].tolist()}"
+
+
+def one_sided_job(n, n_sources, seed):
+    """An n x n dirty image whose sources all sit in the right half, over a
+    narrow Gaussian PSF (2n x 2n, sigma 1.5 pixels, peak 1 at the centre) and
+    noise of 1 mJy: with a threshold of 10 mJy no left-half tile ever has an
+    iteration, so its key is 0 from the first step while its right-hand
+    neighbour runs."""
+    rng = np.random.default_rng(seed)
+    yy, xx = np.mgrid[-n:n, -n:n].astype(np.float64)
+    psf = np.exp(-(yy * yy + xx * xx) / (2 * 1.5 ** 2)).astype(np.float32)
+    ys = rng.integers(8, n - 8, size=n_sources)
+    xs = rng.choice(np.arange(n // 2 + 8, n - 8), size=n_sources, replace=False)
+    fl = np.exp(rng.uniform(np.log(0.05), np.log(2.1), size=n_sources))
+    import synth
+    dirty = synth.make_dirty(psf, n, ys, xs, fl, 1e-3, rng)
+    return psf, dirty

@@ -159,3 +159,34 @@ def test_batch_streamed_pipeline_groups_equal_solo_runs():
                                   solo["comps"]["flux"].view(np.uint32)), i
             assert np.array_equal(res.cpu().numpy().view(np.uint32),
                                   solo["residual"].view(np.uint32)), i
+
+
+def test_batch_tile_pairs_with_idle_tiles_equal_oracle():
+    """Persistent tile-pair units (512^2 in 2 x 2 tiles: two pairs of
+    256-pixel-wide tiles) beside single-tile units, where every left tile
+    stays under the threshold from the start: each image equals the oracle
+    bit for bit."""
+    import torch
+    from gpu_helpers import one_sided_job
+    cases = [(512, (2, 2), 20, 700, 0.01), (640, (2, 2), 0, 500, 0.01),
+             (512, (1, 1), 15, 300, 0.0)]
+    data = [one_sided_job(n, 10, 500 + i) for i, (n, *_rest) in enumerate(cases)]
+    jobs = [dict(psf=torch.from_numpy(p).cuda(), ny=n, nx=n, gain=0.1, niter=niter,
+                 threshold=thr, tiles=tiles, feedback_interval=K)
+            for (p, _), (n, tiles, K, niter, thr) in zip(data, cases)]
+    dirties = [torch.from_numpy(d).cuda() for _, d in data]
+    with cg.Batch(jobs) as b:
+        for rep in range(2):
+            b.run(dirties)
+            for i, (n, tiles, K, niter, thr) in enumerate(cases):
+                res, mod, comps = b.get(i)
+                o = oracle.clean_f32(data[i][1], data[i][0], 0.1, niter, thr, tiles, K)
+                assert len(comps) == o.n, (i, rep)
+                assert np.array_equal(comps["y"], o.comps["y"]), (i, rep)
+                assert np.array_equal(comps["x"], o.comps["x"]), (i, rep)
+                assert np.array_equal(comps["flux"].view(np.uint32),
+                                      o.comps["flux"].view(np.uint32)), (i, rep)
+                assert np.array_equal(res.cpu().numpy().view(np.uint32),
+                                      o.residual.view(np.uint32)), (i, rep)
+                assert np.array_equal(mod.cpu().numpy().view(np.uint32),
+                                      o.model.view(np.uint32)), (i, rep)

@@ -218,6 +218,23 @@ def test_minor_tile_pairs_bit_exact(case):
         assert_bit_exact(g, o, f"{case} pairs={pr}")
 
 
+def test_tile_pairs_with_an_idle_tile_bit_exact():
+    """Tile pairs whose left tile never has an iteration: its key is 0 from
+    the first step, so the producer posts two keys before the consumers wait
+    for the first (one key barrier per buffer keeps the waits exact)."""
+    from gpu_helpers import one_sided_job
+    psf, dirty = one_sided_job(512, 12, 77)
+    # (tiles, K, G): G row bands a tile, streamed (a 256-wide slab of 256
+    # rows does not fit in shared memory beside the ring)
+    for tiles, K, G in (((1, 2), 10, 2), ((2, 2), 0, 1), ((2, 2), 25, 1)):
+        o = oracle.clean_f32(dirty, psf, 0.1, 800, 0.01, tiles, K)
+        assert 0 < o.n < 800 and set(o.comps["tile"].tolist()) <= {1, 3}
+        g = gpu_clean(dirty, psf, 0.1, 800, 0.01, tiles, K, group_ctas=G,
+                      group_sync=cg.SYNC_GRID, minor_path=2, minor_pair=1)
+        assert g["stats"]["minor_pairs"] == 1 and g["stats"]["resident"] == 0, (tiles, g["stats"])
+        assert_bit_exact(g, o, f"idle left tiles {tiles} K {K}")
+
+
 def test_untiled_grid_256():
     """Plain Hogbom CLEAN on the whole GPU: 256^2 image, 512^2 PSF, 20
     sources, gain 0.1, 2000 iterations, threshold 5 mJy."""
