@@ -584,6 +584,55 @@ __device__ __forceinline__ void tmem_chunk(const PlanDev& d, uint32_t taddr, boo
   ptx::tmem_st16(taddr, rv);
 }
 
+// One streamed chunk of 4 lanes' pixels a row and at most 60 rows (CW = 128):
+// warp w owns rows w, w + 15, w + 30, w + 45 as in tmem_chunk, reads the
+// residual from the staged box and writes it back to global memory.  Rows
+// past the chunk (nrows) and lanes past its right edge (c1) read a valid
+// staged value and neither store nor take part in the peak.  Same
+// arithmetic and peak tracking as slab_step, with the row addresses formed
+// once a chunk.
+template <int OFF>
+__device__ __forceinline__ void stream_chunk(const PlanDev& d, const float* stgR,
+                                             const float* stgP, int BW, int r0, int nrows,
+                                             int c0, int c1, float f, float& best_a,
+                                             int& best_base, float4& best_r) {
+  constexpr int kWarps = kPipeConsumers / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool lane_in = c0 + 4 * lane < c1;
+  float4 rv[kSlabUnroll], pa[kSlabUnroll], pb[kSlabUnroll];
+#pragma unroll
+  for (int u = 0; u < kSlabUnroll; ++u) {
+    const int row = warp + u * kWarps;
+    const int ly = row < nrows ? row : 0;
+    const float4* rowP4 = reinterpret_cast<const float4*>(stgP + ly * BW);
+    pa[u] = rowP4[lane];
+    if (OFF != 0) pb[u] = rowP4[lane + 1];
+    rv[u] = reinterpret_cast<const float4*>(stgR + ly * BW)[lane];
+  }
+  float* out = d.R + (int64_t)(r0 + warp) * d.nx + c0 + 4 * lane;
+  int base = (r0 + warp) * d.nx + c0 + 4 * lane;
+#pragma unroll
+  for (int u = 0; u < kSlabUnroll; ++u) {
+    const bool valid = lane_in && warp + u * kWarps < nrows;
+    const float4 a = pa[u];
+    float4 p;
+    if (OFF == 0) {
+      p = a;
+    } else {
+      const float4 b = pb[u];
+      p = OFF == 1 ? make_float4(a.y, a.z, a.w, b.x)
+                   : OFF == 2 ? make_float4(a.z, a.w, b.x, b.y) : make_float4(a.w, b.x, b.y, b.z);
+    }
+    float4 r = rv[u];
+    fms2(r.x, r.y, p.x, p.y, f);
+    fms2(r.z, r.w, p.z, p.w, f);
+    if (valid) *reinterpret_cast<float4*>(out + (int64_t)u * kWarps * d.nx) = r;
+    const float m = fmaxf(fmaxf(fabsf(r.x), fabsf(r.y)), fmaxf(fabsf(r.z), fabsf(r.w)));
+    keep_group(valid, m, base, r, best_a, best_base, best_r);
+    base += kWarps * d.nx;
+  }
+}
+
 // CTA `rank` of the group serving tile t; r_map and p_map describe the
 // residual and PSF boxes (r_map unused when the rows are resident).
 //
@@ -813,6 +862,21 @@ __device__ __forceinline__ void minor_pipe_body(const PlanDev& d, const MinorCfg
             default:
               tmem_chunk<3>(d, ta, from_box, stgR, stgP, BW, r0, c0, f, best_a, best_base,
                             best_r);
+              break;
+          }
+        } else if (!RES && fast && CW == 128 && BH <= kSlabUnroll * kW) {
+          switch (offP) {
+            case 0:
+              stream_chunk<0>(d, stgR, stgP, BW, r0, r1 - r0, c0, c1, f, best_a, best_base, best_r);
+              break;
+            case 1:
+              stream_chunk<1>(d, stgR, stgP, BW, r0, r1 - r0, c0, c1, f, best_a, best_base, best_r);
+              break;
+            case 2:
+              stream_chunk<2>(d, stgR, stgP, BW, r0, r1 - r0, c0, c1, f, best_a, best_base, best_r);
+              break;
+            default:
+              stream_chunk<3>(d, stgR, stgP, BW, r0, r1 - r0, c0, c1, f, best_a, best_base, best_r);
               break;
           }
         } else if (fast) {
@@ -1279,6 +1343,21 @@ __device__ __forceinline__ void minor_pair_body(const PlanDev& d, const MinorCfg
             break;
           default:
             tmem_chunk<3>(d, ta, from_box, stgR, stgP, BW, r0, c0, f, best_a, best_base, best_r);
+            break;
+        }
+      } else if (fast && CW == 128 && BH <= kSlabUnroll * kW) {
+        switch (offP) {
+          case 0:
+            stream_chunk<0>(d, stgR, stgP, BW, r0, r1 - r0, c0, c1, f, best_a, best_base, best_r);
+            break;
+          case 1:
+            stream_chunk<1>(d, stgR, stgP, BW, r0, r1 - r0, c0, c1, f, best_a, best_base, best_r);
+            break;
+          case 2:
+            stream_chunk<2>(d, stgR, stgP, BW, r0, r1 - r0, c0, c1, f, best_a, best_base, best_r);
+            break;
+          default:
+            stream_chunk<3>(d, stgR, stgP, BW, r0, r1 - r0, c0, c1, f, best_a, best_base, best_r);
             break;
         }
       } else if (fast) {

@@ -235,6 +235,26 @@ def test_tile_pairs_with_an_idle_tile_bit_exact():
         assert_bit_exact(g, o, f"idle left tiles {tiles} K {K}")
 
 
+def test_tile_pairs_with_ties_everywhere_bit_exact():
+    """A delta PSF over an integer-valued image: each iteration changes only
+    the peak pixel, so every later peak is a tie among thousands of pixels of
+    |R| = 3 spread over chunks, lanes, warps and CTAs, and must still be the
+    lowest index (the pair body's per-chunk tracking reads the tied chunks
+    back)."""
+    rng = np.random.default_rng(2024)
+    for (ny, nx), tiles, K, G in (((512, 512), (1, 2), 10, 2), ((512, 512), (2, 2), 0, 1),
+                                  ((520, 1000), (1, 2), 13, 3)):
+        psf = np.zeros((2 * ny, 2 * nx), np.float32)
+        psf[ny, nx] = 1.0
+        dirty = synth.tie_image(ny, nx, rng)
+        o = oracle.clean_f32(dirty, psf, 0.1, 400, 0.0, tiles, K)
+        assert o.n == 400
+        g = gpu_clean(dirty, psf, 0.1, 400, 0.0, tiles, K, group_ctas=G,
+                      group_sync=cg.SYNC_GRID, minor_path=2, minor_pair=1)
+        assert g["stats"]["minor_pairs"] == 1 and g["stats"]["resident"] == 0, g["stats"]
+        assert_bit_exact(g, o, f"ties {ny}x{nx} {tiles} K {K}")
+
+
 def test_untiled_grid_256():
     """Plain Hogbom CLEAN on the whole GPU: 256^2 image, 512^2 PSF, 20
     sources, gain 0.1, 2000 iterations, threshold 5 mJy."""
