@@ -448,6 +448,26 @@ __device__ __forceinline__ void keep_group(bool valid, float m, int base, const 
   }
 }
 
+// One thread's four groups of a chunk (rows w, w + 15, w + 30, w + 45, so in
+// increasing index order) into the running best: the chunk's best group is
+// found as a two-level tournament in which a later group wins only with a
+// strictly larger maximum (the lowest index among equal maxima), then merged
+// once by keep_group.  Same choice as four keep_group calls, with a dependency
+// chain of three steps instead of four.  m < 0 marks a group that takes no
+// part.
+__device__ __forceinline__ void keep_chunk4(const float (&m)[4], const float4 (&r)[4], int base0,
+                                            int row_step, float& best_a, int& best_base,
+                                            float4& best_r) {
+  const bool s01 = m[1] > m[0], s23 = m[3] > m[2];
+  const float m01 = s01 ? m[1] : m[0], m23 = s23 ? m[3] : m[2];
+  const float4 r01 = s01 ? r[1] : r[0], r23 = s23 ? r[3] : r[2];
+  const int u01 = s01 ? 1 : 0, u23 = s23 ? 3 : 2;
+  const bool s = m23 > m01;
+  const float mc = s ? m23 : m01;
+  keep_group(mc >= 0.f, mc, base0 + (s ? u23 : u01) * row_step, s ? r23 : r01, best_a, best_base,
+             best_r);
+}
+
 // U slabs s, s + 15, ... of one chunk for this lane (rows past r1 masked).
 template <bool RES, int OFF, int U>
 __device__ __forceinline__ void slab_step(const PlanDev& d, float* sRes, int WR, int ya,
@@ -547,6 +567,7 @@ __device__ __forceinline__ void tmem_chunk(const PlanDev& d, uint32_t taddr, boo
   constexpr int kWarps = kPipeConsumers / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float4 rv[kSlabUnroll], pa[kSlabUnroll], pb[kSlabUnroll];
+  float m[kSlabUnroll];
 #pragma unroll
   for (int u = 0; u < kSlabUnroll; ++u) {
     const float4* rowP4 = reinterpret_cast<const float4*>(stgP + (warp + u * kWarps) * BW);
@@ -576,10 +597,10 @@ __device__ __forceinline__ void tmem_chunk(const PlanDev& d, uint32_t taddr, boo
     fms2(r.x, r.y, p.x, p.y, f);
     fms2(r.z, r.w, p.z, p.w, f);
     rv[u] = r;
-    const float m = fmaxf(fmaxf(fabsf(r.x), fabsf(r.y)), fmaxf(fabsf(r.z), fabsf(r.w)));
-    keep_group(true, m, (r0 + warp + u * kWarps) * d.nx + c0 + 4 * lane, r, best_a, best_base,
-               best_r);
+    m[u] = fmaxf(fmaxf(fabsf(r.x), fabsf(r.y)), fmaxf(fabsf(r.z), fabsf(r.w)));
   }
+  keep_chunk4(m, rv, (r0 + warp) * d.nx + c0 + 4 * lane, kWarps * d.nx, best_a, best_base,
+              best_r);
   __syncwarp();
   ptx::tmem_st16(taddr, rv);
 }
@@ -600,6 +621,7 @@ __device__ __forceinline__ void stream_chunk(const PlanDev& d, const float* stgR
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const bool lane_in = c0 + 4 * lane < c1;
   float4 rv[kSlabUnroll], pa[kSlabUnroll], pb[kSlabUnroll];
+  float m[kSlabUnroll];
 #pragma unroll
   for (int u = 0; u < kSlabUnroll; ++u) {
     const int row = warp + u * kWarps;
@@ -610,7 +632,6 @@ __device__ __forceinline__ void stream_chunk(const PlanDev& d, const float* stgR
     rv[u] = reinterpret_cast<const float4*>(stgR + ly * BW)[lane];
   }
   float* out = d.R + (int64_t)(r0 + warp) * d.nx + c0 + 4 * lane;
-  int base = (r0 + warp) * d.nx + c0 + 4 * lane;
 #pragma unroll
   for (int u = 0; u < kSlabUnroll; ++u) {
     const bool valid = lane_in && warp + u * kWarps < nrows;
@@ -627,10 +648,11 @@ __device__ __forceinline__ void stream_chunk(const PlanDev& d, const float* stgR
     fms2(r.x, r.y, p.x, p.y, f);
     fms2(r.z, r.w, p.z, p.w, f);
     if (valid) *reinterpret_cast<float4*>(out + (int64_t)u * kWarps * d.nx) = r;
-    const float m = fmaxf(fmaxf(fabsf(r.x), fabsf(r.y)), fmaxf(fabsf(r.z), fabsf(r.w)));
-    keep_group(valid, m, base, r, best_a, best_base, best_r);
-    base += kWarps * d.nx;
+    rv[u] = r;
+    m[u] = valid ? fmaxf(fmaxf(fabsf(r.x), fabsf(r.y)), fmaxf(fabsf(r.z), fabsf(r.w))) : -1.f;
   }
+  keep_chunk4(m, rv, (r0 + warp) * d.nx + c0 + 4 * lane, kWarps * d.nx, best_a, best_base,
+              best_r);
 }
 
 // CTA `rank` of the group serving tile t; r_map and p_map describe the
