@@ -605,6 +605,11 @@ __device__ __forceinline__ void tmem_chunk(const PlanDev& d, uint32_t taddr, boo
   ptx::tmem_st16(taddr, rv);
 }
 
+template <int N>
+struct IntTag {
+  static constexpr int value = N;
+};
+
 // One streamed chunk of 4 lanes' pixels a row and at most 60 rows (CW = 128):
 // warp w owns rows w, w + 15, w + 30, w + 45 as in tmem_chunk, reads the
 // residual from the staged box and writes it back to global memory.  Rows
@@ -1330,8 +1335,59 @@ __device__ __forceinline__ void minor_pair_body(const PlanDev& d, const MinorCfg
       __syncwarp();
       ptx::tmem_wait_st();
     }
+    // 128-wide chunks with the window inside the PSF: every chunk is a
+    // tensor-memory or a streamed one, and the PSF realignment (c0 + dx) mod 4
+    // is the same for every chunk of the pass (chunk columns step by 128), so
+    // the pass is specialised on it once instead of switching per chunk.  A
+    // wait whose producer gave up returns false from its bounded slow path.
+    auto fast_pass = [&](auto off) {
+      constexpr int OFF = decltype(off)::value;
+      int rb = 0, cb = 0;
+      for (int ch = 0; ch < P.nch; ++ch) {
+        const int st = c_st;
+        bool ok = pipe_wait(&full_bar[st], c_ph, limit, &s_dead, &d.st->status);
+        if (TM) ok = __all_sync(0xffffffffu, ok);
+        if (!ok) break;
+        if (++c_st == S) {
+          c_st = 0;
+          c_ph ^= 1u;
+        }
+        const int r0 = P.ya + rb * BH, r1 = min(P.yb, r0 + BH);
+        const int c0 = P.x0 + cb * CW, c1 = min(P.x1, c0 + CW);
+        if (++cb == P.ncb) {
+          cb = 0;
+          ++rb;
+        }
+        const float* stgR = sStage + (size_t)st * stage_floats;
+        const float* stgP = stgR + box_floats;
+        if (TM && ch < P.n_tm)
+          tmem_chunk<OFF>(d, tm_base + (uint32_t)(X * 64 + ch * 16), kX == 0, stgR, stgP, BW, r0,
+                          c0, f, best_a, best_base, best_r);
+        else
+          stream_chunk<OFF>(d, stgR, stgP, BW, r0, r1 - r0, c0, c1, f, best_a, best_base, best_r);
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(&empty_bar[st]);
+      }
+    };
+    const bool lean = fast && CW == 128 && BH <= kSlabUnroll * kW;
+    if (lean) {
+      switch ((P.x0 + dx) & 3) {
+        case 0:
+          fast_pass(IntTag<0>{});
+          break;
+        case 1:
+          fast_pass(IntTag<1>{});
+          break;
+        case 2:
+          fast_pass(IntTag<2>{});
+          break;
+        default:
+          fast_pass(IntTag<3>{});
+          break;
+      }
+    }
     int rb = 0, cb = 0;
-    for (int ch = 0; ch < P.nch; ++ch) {
+    for (int ch = 0; ch < P.nch && !lean; ++ch) {
       const int st = c_st;
       bool ok = !*(volatile int*)&s_dead &&
                 pipe_wait(&full_bar[st], c_ph, limit, &s_dead, &d.st->status);
