@@ -848,7 +848,57 @@ __device__ __forceinline__ void minor_pipe_body(const PlanDev& d, const MinorCfg
         __syncwarp();
         ptx::tmem_wait_st();
       }
-      for (int ch = 0; ch < nch; ++ch) {
+      // streamed 128-wide chunks with the window inside the PSF: the pass is
+      // specialised once on the PSF realignment, which every chunk shares (as
+      // in the tile-pair body)
+      auto fast_pass = [&](auto off) {
+        constexpr int OFF = decltype(off)::value;
+        int rb = 0, cb = 0;
+        for (int ch = 0; ch < nch; ++ch) {
+          const int st = c_st;
+          bool ok = pipe_wait(&full_bar[st], c_ph, limit, &s_dead, &d.st->status);
+          if (TM) ok = __all_sync(0xffffffffu, ok);
+          if (!ok) break;
+          if (++c_st == S) {
+            c_st = 0;
+            c_ph ^= 1u;
+          }
+          const int r0 = ya + rb * BH, r1 = min(yb, r0 + BH);
+          const int c0 = x0 + cb * CW, c1 = min(x1, c0 + CW);
+          if (++cb == ncb) {
+            cb = 0;
+            ++rb;
+          }
+          const float* stgR = sStage + (size_t)st * stage_floats;
+          const float* stgP = stgR + box_floats;
+          if (TM && ch < n_tm)
+            tmem_chunk<OFF>(d, tm_base + (uint32_t)ch * 16u, k == 0, stgR, stgP, BW, r0, c0, f,
+                            best_a, best_base, best_r);
+          else
+            stream_chunk<OFF>(d, stgR, stgP, BW, r0, r1 - r0, c0, c1, f, best_a, best_base,
+                              best_r);
+          __syncwarp();
+          if (lane == 0) ptx::mbar_arrive(&empty_bar[st]);
+        }
+      };
+      const bool lean = !RES && fast && CW == 128 && BH <= kSlabUnroll * kW;
+      if (lean) {
+        switch ((x0 + dx) & 3) {
+          case 0:
+            fast_pass(IntTag<0>{});
+            break;
+          case 1:
+            fast_pass(IntTag<1>{});
+            break;
+          case 2:
+            fast_pass(IntTag<2>{});
+            break;
+          default:
+            fast_pass(IntTag<3>{});
+            break;
+        }
+      }
+      for (int ch = 0; ch < nch && !lean; ++ch) {
         const int st = c_st;
         bool ok = !*(volatile int*)&s_dead &&
                   pipe_wait(&full_bar[st], c_ph, limit, &s_dead, &d.st->status);
