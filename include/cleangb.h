@@ -48,6 +48,10 @@
  *   - Every call returns a clean_status.  After CLEAN_ERR_CUDA or
  *     CLEAN_ERR_TIMEOUT a plan is poisoned: every later call on it returns
  *     the same code.  No call aborts the process.
+ *   - Diagnostics: with the environment variable CLEANGB_REPORT_TIMEOUT set,
+ *     the batch and server entry points print to stderr, for each job whose
+ *     bounded wait expired, its shape, its unit layout and the tile and
+ *     exchange where the wait gave up.
  */
 #ifndef CLEANGB_H
 #define CLEANGB_H
