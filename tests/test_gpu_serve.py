@@ -160,3 +160,29 @@ def test_serving_stream_non_power_of_two_jobs_equal_solo_runs():
     st = serve.serve_one_at_a_time(jobs, run)
     assert ran == sorted(ran) and st["jobs"] == len(jobs)
     assert all(j.finished >= j.admitted >= j.arrival - 1e-9 for j in jobs)
+
+
+def test_saturated_stream_of_tile_pair_jobs_equals_solo_runs():
+    """Jobs whose tiles run as pairs in the persistent minor-loop launch
+    (even tile counts, tiles at least 256 pixels wide), all arriving at once
+    under a memory budget that admits a few at a time: the others join as
+    jobs finish, so the pair units of new jobs run beside those of jobs in
+    later rounds.  In one job the left tiles never have an iteration (their
+    keys are 0 from the first step).  Each result equals its solo run bit
+    for bit."""
+    import torch
+    from gpu_helpers import one_sided_job
+    specs = [(576, (2, 2), 900, 0.0), (768, (2, 2), 1200, 0.0), (1088, (4, 4), 1600, 0.0),
+             (640, (2, 2), 700, 0.0), (1024, (2, 2), 1000, 0.0), (1536, (4, 4), 1600, 0.0)]
+    data = [_data(n, 300 + i, n_src=25) for i, (n, *_r) in enumerate(specs)]
+    specs.append((512, (2, 2), 600, 0.01))
+    data.append(one_sided_job(512, 10, 901))
+    jobs = [serve.Job(psf=torch.from_numpy(p).cuda(), dirty=torch.from_numpy(d).cuda(), niter=nit,
+                      threshold=thr, tiles=tiles, feedback_interval=50, arrival=0.0)
+            for (p, d), (n, tiles, nit, thr) in zip(data, specs)]
+    fp = sorted(j.footprint() for j in jobs)
+    st = serve.serve(jobs, budget_bytes=1.1 * (fp[-1] + fp[-2]), rounds_per_step=2)
+    assert st["jobs"] == len(jobs)
+    assert max(j.admitted for j in jobs) >= min(j.finished for j in jobs)  # later jobs joined
+    for j, (p, d), (n, tiles, nit, thr) in zip(jobs, data, specs):
+        _same(j.result, gpu_clean(d, p, 0.1, nit, thr, tiles, 50))
