@@ -1102,10 +1102,11 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
 // both sides alike).  The producer's lane 0 publishes the step's key in
 // s_key[n mod 2] (key n; 0: the tile is finished) and arrives on
 // key_bar[n mod 2]; the consumers wait there (phase n / 2), process the
-// tile's chunks and leave their partial keys in shared memory; the last warp to finish posts the CTA's key to the tile's
-// exchange slot with the usual phase mark.  The producer warp reads
-// the exchange of the tile's previous iteration, which every CTA posted one
-// step earlier, so the wait overlaps the other tile's pass.  Exchange g of
+// tile's chunks and leave their partial keys in shared memory; the last warp
+// to finish posts the CTA's key to the tile's exchange slot with the usual
+// phase mark.  The producer warp reads the exchange of the tile's previous
+// iteration, which every CTA posted one step earlier, so the wait overlaps
+// the other tile's pass.  Exchange g of
 // tile t is posted after reading exchange g - 1, so the argument that keeps
 // slots from being overwritten early is the single-tile one.  The last
 // exchange of a launch is posted and never read; the next launch's count
