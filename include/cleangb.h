@@ -75,7 +75,7 @@ typedef enum {
   CLEAN_ERR_OOM = 3,         /* device allocation failed */
   CLEAN_ERR_CUDA = 4,        /* a CUDA call failed (plan poisoned) */
   CLEAN_ERR_TIMEOUT = 5,     /* a bounded device wait expired (plan poisoned) */
-  CLEAN_ERR_UNSUPPORTED = 6  /* valid request this build cannot serve */
+  CLEAN_ERR_UNSUPPORTED = 6  /* valid request the library cannot serve */
 } clean_status;
 
 /* feedback_mode.  The environment variable CLEANGB_FORCE_FEEDBACK

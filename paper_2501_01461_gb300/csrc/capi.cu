@@ -1277,7 +1277,7 @@ const char* clean_strerror(int status) {
     case CLEAN_ERR_OOM: return "out of device memory";
     case CLEAN_ERR_CUDA: return "CUDA error";
     case CLEAN_ERR_TIMEOUT: return "bounded device wait expired";
-    case CLEAN_ERR_UNSUPPORTED: return "unsupported by this build";
+    case CLEAN_ERR_UNSUPPORTED: return "unsupported by the library";
     default: return "unknown status";
   }
 }
