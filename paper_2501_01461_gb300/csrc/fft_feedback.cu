@@ -192,6 +192,33 @@ __device__ __forceinline__ void fft_stage(float2* buf, int L, int Ns, const floa
   __syncthreads();
 }
 
+// The same stage reading `in` and writing `out` (another buffer): each
+// butterfly goes through registers alone (one at a time per thread), and the
+// stage needs one barrier, after its stores.
+template <int R>
+__device__ __forceinline__ void fft_stage_pp(const float2* in, float2* out, int L, int Ns,
+                                             const float2* __restrict__ tw,
+                                             const float2* __restrict__ tws, bool inv) {
+  const int nb = L / R;
+#pragma unroll 1
+  for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+    const int k = j % Ns;
+    float2 v[R];
+    v[0] = in[fpad(j)];
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      float2 w = __ldg(&tws[r * Ns + k]);
+      if (inv) w.y = -w.y;
+      v[r] = cmul(in[fpad(j + r * nb)], w);
+    }
+    Dft<R>::run(v, inv, tw, L);
+    const int base = (j - k) * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) out[fpad(base + r * Ns)] = v[r];
+  }
+  __syncthreads();
+}
+
 // ---- power-of-two lengths 2048 .. 8192: radix-16 stages, L / 16 threads --------
 // Each thread holds one 16-point butterfly per stage in registers; all index
 // arithmetic is compile-time.  A stage's twiddles w^r (w = e^(-2 pi i k /
@@ -360,9 +387,38 @@ __device__ __forceinline__ void fft_p2_io(float2* buf, const FftAxis& ax,
 // other.
 template <bool P2>
 __device__ __forceinline__ void fft_1d(float2* buf, const FftAxis& ax,
-                                       const float2* __restrict__ tw, bool inv) {
+                                       const float2* __restrict__ tw, bool inv,
+                                       float2* tmp = nullptr) {
   if constexpr (P2) {
     fft_p2_io(buf, ax, tw, inv, BufIO{buf}, BufIO{buf});
+    return;
+  }
+  if (tmp) {
+    // mixed radix with a scratch buffer: stages alternate between the two,
+    // and the result comes back to buf if it ends in tmp
+    float2* a = buf;
+    float2* b = tmp;
+    int Ns = 1;
+    for (int s = 0; s < ax.nrad; ++s) {
+      const int R = ax.rad[s];
+      const float2* tws = tw + ax.tw_off[s];
+      switch (R) {
+        case 8: fft_stage_pp<8>(a, b, ax.L, Ns, tw, tws, inv); break;
+        case 4: fft_stage_pp<4>(a, b, ax.L, Ns, tw, tws, inv); break;
+        case 2: fft_stage_pp<2>(a, b, ax.L, Ns, tw, tws, inv); break;
+        case 3: fft_stage_pp<3>(a, b, ax.L, Ns, tw, tws, inv); break;
+        case 5: fft_stage_pp<5>(a, b, ax.L, Ns, tw, tws, inv); break;
+        default: fft_stage_pp<7>(a, b, ax.L, Ns, tw, tws, inv); break;
+      }
+      float2* t = a;
+      a = b;
+      b = t;
+      Ns *= R;
+    }
+    if (a != buf) {
+      for (int i = threadIdx.x; i < ax.L; i += blockDim.x) buf[fpad(i)] = a[fpad(i)];
+      __syncthreads();
+    }
     return;
   }
   int Ns = 1;
@@ -405,7 +461,7 @@ __global__ void __launch_bounds__(kFftMaxThreads, 1) fft_psf_rows_kernel(PlanDev
     fbuf[fpad(mx)] = make_float2(kernel_image(d, Ly, Lx, 2 * a, mx),
                                  kernel_image(d, Ly, Lx, 2 * a + 1, mx));
   __syncthreads();
-  fft_1d<P2>(fbuf, ax, twx, false);
+  fft_1d<P2>(fbuf, ax, twx, false, P2 ? nullptr : fbuf + fpad(Lx) + 2);
   for (int k = threadIdx.x; k <= Lx / 2; k += blockDim.x) {
     const float2 z1 = fbuf[fpad(k)];
     const float2 z = fbuf[fpad(k == 0 ? 0 : Lx - k)];
@@ -427,7 +483,7 @@ __global__ void __launch_bounds__(kFftMaxThreads, 1) fft_psf_cols_kernel(FftAxis
   float2* col = Kspec + (int64_t)blockIdx.x * Ly;
   for (int i = threadIdx.x; i < Ly; i += blockDim.x) fbuf[fpad(i)] = col[i];
   __syncthreads();
-  fft_1d<P2>(fbuf, ay, twy, false);
+  fft_1d<P2>(fbuf, ay, twy, false, P2 ? nullptr : fbuf + fpad(Ly) + 2);
   for (int i = threadIdx.x; i < Ly; i += blockDim.x) {
     const float2 v = fbuf[fpad(i)];
     col[i] = make_float2(v.x * scale, v.y * scale);
@@ -541,6 +597,7 @@ __global__ void __launch_bounds__(kFftMaxThreads, 1)
   float2* kst = reinterpret_cast<float2*>(fsm);  // the spectrum column, Ly
   float2* fbuf = kst + Ly;                        // the transform, padded
   float2* rowv = fbuf + fpad(Ly) + 2;             // radix-16 path: the component rows' inputs
+  float2* scratch = rowv;                         // mixed radix: the transforms' second buffer
   __shared__ __align__(8) uint64_t kbar;
   __shared__ int s_abort;
   const uint32_t kbytes = (uint32_t)Ly * (uint32_t)sizeof(float2);
@@ -605,7 +662,7 @@ __global__ void __launch_bounds__(kFftMaxThreads, 1)
       continue;
     }
     __syncthreads();
-    fft_1d<P2>(fbuf, ay, twy, false);
+    fft_1d<P2>(fbuf, ay, twy, false, scratch);
     // the spectrum column: every thread waits (bounded) for the bulk copy
     if (!ptx::mbar_wait_bounded(&kbar, phase, limit_ns)) {
       atomicOr(&d.st->status, ST_TIMEOUT);
@@ -626,7 +683,7 @@ __global__ void __launch_bounds__(kFftMaxThreads, 1)
       ptx::mbar_arrive_expect_tx(&kbar, kbytes);
       bulk_load(kst, Kspec + (int64_t)(k + gridDim.x) * Ly, kbytes, &kbar);
     }
-    fft_1d<P2>(fbuf, ay, twy, true);
+    fft_1d<P2>(fbuf, ay, twy, true, scratch);
     // pair-major: row q's bin k at ((q / 2) ncols + k) 2 + q % 2, so a pair
     // of rows is one contiguous run for the row pass
 #pragma unroll
@@ -923,14 +980,14 @@ cudaError_t fft_build_psf_spectrum(const PlanDev& d, const FftAxis& ay, const Ff
   if (ax.p2)
     fft_psf_rows_kernel<true><<<ay.L / 2, ax.nthr, fft_smem_bytes(ax.L), s>>>(d, ax, ay.L, twx, Kspec);
   else
-    fft_psf_rows_kernel<false><<<ay.L / 2, ax.nthr, fft_smem_bytes(ax.L), s>>>(d, ax, ay.L, twx, Kspec);
+    fft_psf_rows_kernel<false><<<ay.L / 2, ax.nthr, 2 * fft_smem_bytes(ax.L), s>>>(d, ax, ay.L, twx, Kspec);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const float scale = (float)(1.0 / ((double)ay.L * (double)ax.L));
   if (ay.p2)
     fft_psf_cols_kernel<true><<<ax.L / 2 + 1, ay.nthr, fft_smem_bytes(ay.L), s>>>(ay, twy, Kspec, scale);
   else
-    fft_psf_cols_kernel<false><<<ax.L / 2 + 1, ay.nthr, fft_smem_bytes(ay.L), s>>>(ay, twy, Kspec, scale);
+    fft_psf_cols_kernel<false><<<ax.L / 2 + 1, ay.nthr, 2 * fft_smem_bytes(ay.L), s>>>(ay, twy, Kspec, scale);
   return cudaGetLastError();
 }
 
@@ -947,8 +1004,10 @@ cudaError_t fft_feedback_round(const PlanDev& d, const FftAxis& ay, const FftAxi
   if (e != cudaSuccess) return e;
   const int ncols = ax.L / 2 + 1;
   const int grid = std::min(ncols, fft_sm_count());
+  // the spectrum column, the transform, then the radix-16 path's component
+  // rows or the mixed-radix path's second buffer
   const size_t cs = sizeof(float2) * (size_t)ay.L + fft_smem_bytes(ay.L) +
-                    sizeof(float2) * (size_t)d.ny;
+                    (ay.p2 ? sizeof(float2) * (size_t)d.ny : fft_smem_bytes(ay.L));
   if (ay.p2)
     fft_cols_kernel<true><<<grid, ay.nthr, cs, s>>>(d, ay, ax.L, comps, lead, twx, twy, Kspec, Y,
                                                     kFftWaitNs);
