@@ -743,7 +743,7 @@ template <bool P2>
 __global__ void __launch_bounds__(kFftMaxThreads, 1)
     fft_rows_kernel(PlanDev d, FftAxis ax, const float2* __restrict__ twx,
                     const float2* __restrict__ Y, float* __restrict__ R0, int parity,
-                    uint64_t limit_ns) {
+                    uint64_t limit_ns, int scratch) {
   extern __shared__ __align__(128) unsigned char fsm[];
   const int Lx = ax.L, ncols = Lx / 2 + 1, nx = d.nx, ny = d.ny;
   const int npairs = (ny + 1) / 2;
@@ -752,6 +752,11 @@ __global__ void __launch_bounds__(kFftMaxThreads, 1)
   float2* fbuf = reinterpret_cast<float2*>(rstg + 2 * ((nx + 3) & ~3));
   int32_t* s_cnt = reinterpret_cast<int32_t*>(fbuf + fpad(Lx) + 1);
   int32_t* s_pre = s_cnt + d.T;
+  // mixed radix, when the launch made room: the transform's second buffer
+  float2* tmp = nullptr;
+  if (!P2 && scratch)
+    tmp = reinterpret_cast<float2*>(
+        (reinterpret_cast<uintptr_t>(s_pre + d.T + 1) + 15) & ~static_cast<uintptr_t>(15));
   __shared__ uint64_t s_warp[2][32];
   __shared__ __align__(8) uint64_t ybar, rbar;
   __shared__ int s_abort;
@@ -806,7 +811,7 @@ __global__ void __launch_bounds__(kFftMaxThreads, 1)
     }
     if (!P2) {
       __syncthreads();
-      fft_1d<P2>(fbuf, ax, twx, true);
+      fft_1d<P2>(fbuf, ax, twx, true, tmp);
       // R <- R0 - S; the results back into fbuf as (row q0, row q1)
       if (bulk_r && !ptx::mbar_wait_bounded(&rbar, phase, limit_ns)) {
         atomicOr(&d.st->status, ST_TIMEOUT);
@@ -1018,13 +1023,32 @@ cudaError_t fft_feedback_round(const PlanDev& d, const FftAxis& ay, const FftAxi
   if (e != cudaSuccess) return e;
   const int npairs = (d.ny + 1) / 2;
   const int rgrid = std::min(npairs, fft_sm_count());
-  const size_t smem = sizeof(float2) * 2 * (size_t)((ncols + 1) & ~1) +
-                      sizeof(float) * 2 * (size_t)((d.nx + 3) & ~3) + fft_smem_bytes(ax.L) +
-                      sizeof(int32_t) * (2 * (size_t)d.T + 1);
-  if (ax.p2)
-    fft_rows_kernel<true><<<rgrid, ax.nthr, smem, s>>>(d, ax, twx, Y, R0, parity, kFftWaitNs);
-  else
-    fft_rows_kernel<false><<<rgrid, ax.nthr, smem, s>>>(d, ax, twx, Y, R0, parity, kFftWaitNs);
+  size_t smem = sizeof(float2) * 2 * (size_t)((ncols + 1) & ~1) +
+                sizeof(float) * 2 * (size_t)((d.nx + 3) & ~3) + fft_smem_bytes(ax.L) +
+                sizeof(int32_t) * (2 * (size_t)d.T + 1);
+  if (ax.p2) {
+    fft_rows_kernel<true><<<rgrid, ax.nthr, smem, s>>>(d, ax, twx, Y, R0, parity, kFftWaitNs, 0);
+    return cudaGetLastError();
+  }
+  // mixed radix: a second transform buffer after the counters when it fits
+  // under the device's per-block limit (all but the largest lengths)
+  int scratch = 0;
+  {
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa;
+    const size_t need = ((smem + 15) & ~(size_t)15) + fft_smem_bytes(ax.L);
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) ==
+            cudaSuccess &&
+        cudaFuncGetAttributes(&fa, (const void*)fft_rows_kernel<false>) == cudaSuccess &&
+        need + fa.sharedSizeBytes <= (size_t)optin) {
+      smem = need;
+      scratch = 1;
+    }
+    cudaGetLastError();
+  }
+  fft_rows_kernel<false><<<rgrid, ax.nthr, smem, s>>>(d, ax, twx, Y, R0, parity, kFftWaitNs,
+                                                      scratch);
   return cudaGetLastError();
 }
 
