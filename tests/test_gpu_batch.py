@@ -190,3 +190,38 @@ def test_batch_tile_pairs_with_idle_tiles_equal_oracle():
                                       o.residual.view(np.uint32)), (i, rep)
                 assert np.array_equal(mod.cpu().numpy().view(np.uint32),
                                       o.model.view(np.uint32)), (i, rep)
+
+
+def test_batch_non_square_tile_pairs_equal_solo_runs():
+    """Non-square images whose tiles run as pairs in the persistent launch
+    (a 1 x 2 grid of 500-pixel-wide tiles: ragged column halves; 2 x 2 of
+    384 x 256 tiles; 3 x 2 of ragged 233/234-row tiles), beside a
+    single-tile image: each equals its solo run bit for bit."""
+    import torch
+    cases = [(520, 1000, (1, 2), 13, 700), (512, 768, (2, 2), 25, 900),
+             (700, 600, (3, 2), 12, 900), (300, 200, (1, 1), 20, 300)]
+    data = []
+    for i, (ny, nx, tiles, K, niter) in enumerate(cases):
+        rng = np.random.default_rng(700 + i)
+        psf = synth.make_psf(2 * ny, 2 * nx)
+        n = min(ny, nx)
+        ys, xs, fl = synth.make_sky(n, 12, 0.05, 2.1, rng)
+        d = synth.make_dirty(psf[ny - n:ny + n, nx - n:nx + n], n, ys, xs, fl, 1e-3, rng)
+        dirty = synth.random_image(ny, nx, rng, 1e-3)
+        dirty[:n, :n] += d
+        data.append((psf, dirty))
+    jobs = [dict(psf=torch.from_numpy(p).cuda(), ny=ny, nx=nx, gain=0.1, niter=niter,
+                 threshold=0.0, tiles=tiles, feedback_interval=K)
+            for (p, _), (ny, nx, tiles, K, niter) in zip(data, cases)]
+    with cg.Batch(jobs) as b:
+        b.run([torch.from_numpy(d).cuda() for _, d in data])
+        for i, (ny, nx, tiles, K, niter) in enumerate(cases):
+            res, mod, comps = b.get(i)
+            solo = gpu_clean(data[i][1], data[i][0], 0.1, niter, 0.0, tiles, K)
+            assert len(comps) == solo["n"] == niter, i
+            assert np.array_equal(comps["flux"].view(np.uint32),
+                                  solo["comps"]["flux"].view(np.uint32)), i
+            assert np.array_equal(res.cpu().numpy().view(np.uint32),
+                                  solo["residual"].view(np.uint32)), i
+            assert np.array_equal(mod.cpu().numpy().view(np.uint32),
+                                  solo["model"].view(np.uint32)), i
